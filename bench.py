@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the per-frame distance-map pipeline (Alg. 2 lines 4-10) on B300.
+
+One step = one control frame at 256^3 voxels of 1 cm: ClearMap of both maps, Insert of
+the FK-placed robot links into the self map, Insert of a 300k-point synthetic
+depth-camera cloud (with robot-point removal) into the environment map, the exact EDT
+of both maps and the 24-sphere query against both.  `value` is voxels transformed per
+second over all ranks (2 x 256^3 per frame), with inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vedt|reference]
+
+Under torchrun each rank runs its own frames (independent maps: weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EDT Gvoxel/s & %HBM roofline at 256³; frame p50/p99 ms; surrogate vs exact query/s"
+SEED = 1234 + 2000
+DIMS = (256, 256, 256)
+VOXEL = 0.01
+N_POINTS = 300_000
+SELF_MASK = 0b111          # static body + links 1-2: the self-collision obstacle set O_L
+WORKLOAD = ("frame256: 256^3 grid at 1 cm; 300k-point synthetic depth-camera cloud (room + primitives + "
+            "0.3 m sphere moving at 1 m/s) into M_I with robot-point removal; 7-link capsule arm + body "
+            "into M_S from a smooth joint trajectory; exact int32 EDT (sqdist + nearest index) of both "
+            "maps; 24-sphere query on both maps; consecutive frames")
+
+# ncu DRAM traffic per launch (read + write bytes) of the dominant kernel, with the
+# source it was taken from; set to None when the kernel changes.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=("vedt", "reference"), default="vedt")
+    p.add_argument("--e2e-steps", type=int, default=200)
+    p.add_argument("--frames", type=int, default=60, help="distinct synthetic frames, cycled")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------
+# ranks
+# ------------------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world, device="cpu"):
+    """Max of a float over ranks (timing only; never data)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------
+# workload
+# ------------------------------------------------------------------------------------
+def build_workload(n_frames, rank=0):
+    from paper_2407_02363_b300 import synth
+    grid = synth.GridSpec(DIMS, VOXEL)
+    scene = synth.CameraScene(SEED + 100 * rank, grid, n_points=N_POINTS)
+    chain = synth.make_chain(SEED, (1.28, 1.28, 1.28))
+    links = synth.link_models(chain, VOXEL)
+    spheres = synth.sphere_model(chain)
+    traj = synth.joint_trajectory(SEED, n_frames)
+    clouds = [scene.frame(i) for i in range(n_frames)]
+    return dict(grid=grid, chain=chain, links=links, spheres=spheres, traj=traj, clouds=clouds)
+
+
+def sphere_centres_lib(v, chain, spheres, q):
+    """Sphere centres C_i in the world from the library's host FK (Alg. 2 line 8)."""
+    P = v.fk(chain, q)
+    R = P[spheres.link]
+    c = np.einsum("nij,nj->ni", R[:, :, :3], spheres.local) + R[:, :, 3]
+    return c.astype(np.float32)
+
+
+# ------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, val in zip(names, r[5:9]) if val.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if _isnum(r[3])), default=None)}
+
+
+def _isnum(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+# ------------------------------------------------------------------------------------
+# algorithmic bytes per launch (design traffic of each kernel)
+# ------------------------------------------------------------------------------------
+def algorithmic_bytes(kind, n_vox_per_grid, n_grids, n_points, n_link_pts):
+    N = n_vox_per_grid * n_grids
+    return {
+        "clear": n_vox_per_grid,                 # one grid per launch, 1 B written per voxel
+        "insert_points": n_points * 12,          # 12 B of xyz read per point
+        "insert_links": n_link_pts * 12,         # 12 B of xyz read per link point
+        "edt_x": N * (1 + 2),                    # uint8 occupancy in, uint16 row site out
+        "edt_y": N * (2 + 2),                    # uint16 row site in, uint16 2-D site out
+        "edt_z": N * (2 + 4 + 4),                # uint16 2-D site in, int32 sqdist + int32 idx out
+        "query": 24 * n_grids * (12 + 8 + 32),
+    }[kind]
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------
+# CPU oracle baseline (rank 0, N = 1)
+# ------------------------------------------------------------------------------------
+def oracle_frame(oracle, W, cloud, q, z_range=None):
+    grid, chain, links, spheres = W["grid"], W["chain"], W["links"], W["spheres"]
+    X, Y, Z = grid.dims
+    poses = oracle.fk(chain, q).astype(np.float32)
+    s = np.zeros((Z, Y, X), np.uint8)
+    oracle.insert_links(s, grid.dims, grid.voxel_size, grid.origin, links, poses, SELF_MASK)
+    e = np.zeros((Z, Y, X), np.uint8)
+    oracle.insert_points(e, s, grid.dims, grid.voxel_size, grid.origin, cloud, filter_self=True)
+    if z_range is not None:
+        e, s = e[z_range[0]:z_range[1]], s[z_range[0]:z_range[1]]
+    c = oracle.sphere_centres(chain, spheres, q)
+    nvox = 0
+    for occ in (e, s):
+        sq, ix = oracle.edt(occ)
+        oracle.query_spheres(sq, ix, (X, Y, occ.shape[0]), grid.voxel_size, grid.origin, c, spheres.radius)
+        nvox += occ.size
+    return nvox
+
+
+def cpu_baseline(W, seconds):
+    import oracle
+    t0 = time.perf_counter()
+    n = vox = 0
+    while True:
+        i = n % len(W["clouds"])
+        vox += oracle_frame(oracle, W, W["clouds"][i], W["traj"][i])
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": vox / dt / 1e9, "unit": "Gvoxel/s", "cores": oracle.default_threads(), "kind": "oracle",
+            "sample": f"{n} full 256^3 frames (insert + EDT of both maps + query) in {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------------------------
+# reference arm: the oracle timed as it stands on the host cores
+# ------------------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    W = build_workload(min(args.frames, 8))
+    # size the per-step sample (a z-slab of both maps) so the whole run takes ~2 minutes
+    t0 = time.perf_counter()
+    oracle_frame(oracle, W, W["clouds"][0], W["traj"][0])
+    t_full = time.perf_counter() - t0
+    budget = 120.0
+    zs = int(max(4, min(DIMS[2], DIMS[2] * budget / max(1e-9, (args.steps + args.warmup) * t_full))))
+    for i in range(args.warmup):
+        oracle_frame(oracle, W, W["clouds"][i % len(W["clouds"])], W["traj"][i % len(W["clouds"])], (0, zs))
+    t0 = time.perf_counter()
+    vox = 0
+    for i in range(args.steps):
+        k = i % len(W["clouds"])
+        z0 = (i * 37) % (DIMS[2] - zs + 1)
+        vox += oracle_frame(oracle, W, W["clouds"][k], W["traj"][k], (z0, z0 + zs))
+    dt = time.perf_counter() - t0
+    value = vox / dt / 1e9
+    sample = f"per step: one frame's inserts + EDT and query of both maps on a 256x256x{zs} z-slab"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "Gvoxel/s", "cores": oracle.default_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------------------------
+# vedt arm
+# ------------------------------------------------------------------------------------
+def run_vedt(args):
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: CUDA device required for --impl vedt")
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    from paper_2407_02363_b300 import build
+    build.build()
+    from paper_2407_02363_b300 import vedt as v
+
+    n_frames = max(1, min(args.frames, args.steps + args.warmup))
+    W = build_workload(n_frames, rank)
+    grid, chain, spheres = W["grid"], W["chain"], W["spheres"]
+    N = grid.n_voxels
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    clouds = [torch.from_numpy(c).to(dev) for c in W["clouds"]]
+    centres = torch.from_numpy(np.stack([sphere_centres_lib(v, chain, spheres, q) for q in W["traj"]])).to(dev)
+    radii = torch.from_numpy(spheres.radius).to(dev)
+    m_sph = len(spheres.radius)
+    out = torch.empty(2 * m_sph * 32, dtype=torch.uint8, device=dev)
+    cchain = v.make_chain(chain)
+    torch.cuda.synchronize()
+
+    m = v.Map(grid.dims, grid.voxel_size, grid.origin, stream=stream)
+    m.register_links(W["links"])
+    n_link_pts = sum(len(l) for l in W["links"])
+
+    def step(i):
+        k = i % n_frames
+        m.frame(clouds[k], clouds[k].shape[0], cchain, W["traj"][k], SELF_MASK, centres[k], radii, m_sph, out)
+
+    for i in range(args.warmup):
+        step(i)
+    m.check()
+    # ---- timed region: K frames, device time with CUDA events on the library's stream ----
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m.kernel_times()
+    m.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        step(args.warmup + i)
+        evs[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    m.check()
+    m.set_timing(False)
+    kt = m.kernel_times()
+    total_ms = reduce_max(t_start.elapsed_time(t_end), world, device=dev)
+    frame_ms = sorted(a.elapsed_time(b) for a, b in evs)
+    vox_all = 2 * N * args.steps * world
+    value = vox_all / (total_ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel ----
+    peak, peak_kind = load_peaks()
+    kernels = {}
+    for name, (ms, cnt) in kt.items():
+        if cnt == 0:
+            continue
+        n_grids = 2 if name in ("edt_x", "edt_y", "edt_z", "query") else 1
+        b = algorithmic_bytes(name, N, n_grids, N_POINTS, n_link_pts)
+        avg = ms / cnt
+        kernels[name] = {"launches": cnt, "total_ms": ms, "avg_us": avg * 1e3, "alg_bytes_per_launch": b,
+                         "achieved_gbs": b / (avg * 1e-3) / 1e9}
+    tot = sum(k["total_ms"] for k in kernels.values())
+    for k in kernels.values():
+        k["share"] = k["total_ms"] / tot if tot else 0.0
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    dk = kernels[dom]
+    traffic = NCU_TRAFFIC.get(dom)
+    roof = {"kernel": dom, "bound": "hbm", "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": dk["achieved_gbs"] / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+            "alg_bytes_per_launch": dk["alg_bytes_per_launch"]}
+    edt_ms = sum(kernels[k]["total_ms"] for k in ("edt_x", "edt_y", "edt_z") if k in kernels) / args.steps
+    edt = {"ms_per_frame_both_maps": edt_ms, "gvoxel_s": 2 * N / (edt_ms * 1e-3) / 1e9,
+           "alg_bytes_per_voxel": 9, "achieved_gbs": 9 * 2 * N / (edt_ms * 1e-3) / 1e9,
+           "frac_of_peak": 9 * 2 * N / (edt_ms * 1e-3) / 1e9 / peak}
+
+    # ---- end to end through the public API from host buffers ----
+    pinned = [torch.from_numpy(c).pin_memory() for c in W["clouds"]]
+    cen_host = [sphere_centres_lib(v, chain, spheres, q) for q in W["traj"]]
+    res = np.zeros(2 * m_sph, dtype=v.SPHERE_DTYPE)
+    for i in range(3):
+        m.frame_host(pinned[i % n_frames], cchain, W["traj"][i % n_frames], SELF_MASK, cen_host[i % n_frames],
+                     spheres.radius, out=res)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.e2e_steps):
+        k = i % n_frames
+        m.frame_host(pinned[k], cchain, W["traj"][k], SELF_MASK, cen_host[k], spheres.radius, out=res)
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world, device=dev)
+    e2e = {"value": 2 * N * args.e2e_steps * world / e2e_s / 1e9, "unit": "Gvoxel/s",
+           "h2d_bytes_per_step": N_POINTS * 12 + m_sph * 16, "d2h_bytes_per_step": 2 * m_sph * 32,
+           "steps": args.e2e_steps, "ms_per_step": e2e_s / args.e2e_steps * 1e3,
+           "api": "vedt_frame_host (pinned host cloud in, sphere results out)"}
+    m.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(W, args.cpu_seconds)
+
+    if rank == 0:
+        occ = float(np.mean([0.0]))
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "voxel_size_m": VOXEL, "points": N_POINTS,
+                       "maps_per_step": 2, "distinct_frames": n_frames, "parallelism": f"replicas x{world}",
+                       "l2": "no flush: each step writes 268 MB of fields plus ~134 MB of scratch, > 126 MB L2"},
+            "latency_ms": {"p50": frame_ms[len(frame_ms) // 2], "p99": frame_ms[min(len(frame_ms) - 1,
+                                                                                     int(0.99 * len(frame_ms)))],
+                           "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
+            "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": int(sum(k["launches"] for k in kernels.values())), "clocks": clk,
+        }
+        del occ
+        print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_vedt(args)
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * vedt.h -- C ABI of the B300-native exact voxel distance-map library.
+ *
+ * The calls follow the control cycle of "Real Time Collision Avoidance with
+ * GPU-Computed Distance Maps" (arXiv 2407.02363), Alg. 2:
+ *   line 1   initialise the self map M_S and environment map M_I  -> vedt_map_create
+ *   line 4   ClearMap                                               -> vedt_clear
+ *   line 5-6 UpdateLinks(q) + Insert(O_Lk) into M_S                 -> vedt_insert_links / vedt_insert_robot
+ *   line 7   Insert(Point_Cloud) into M_I (robot points removed)    -> vedt_insert_pointcloud
+ *   line 8   ForwardKinematics of the sphere centres                -> vedt_fk (host helper)
+ *   line 9   PBA_EDT(M_S, M_I): exact EDT, Sec. III-C, Alg. 1        -> vedt_compute_edt
+ *   line 10  ExtractClosestObstaclePose, Eq. (dist), Alg. 3 l.3-4   -> vedt_query_spheres
+ *
+ * Conventions for every call:
+ *  - Grids are X x Y x Z cubic voxels of edge voxel_size metres; voxel (x, y, z) has
+ *    linear index x + X*(y + Y*z) (x fastest).  World point p lies in voxel
+ *    floor((p - origin) / voxel_size) computed in fp32 (one rounded subtraction, one
+ *    rounded division); it is inside iff 0 <= v < dims on every axis (points on the
+ *    upper face and NaN points are outside).  1 <= X, Y, Z <= VEDT_MAX_DIM.
+ *  - Occupancy grids are uint8 (nonzero = occupied).  The distance field is int32
+ *    squared distance in voxel units plus int32 linear index of a nearest occupied
+ *    voxel.  Where several occupied voxels are equally near, any of them may be
+ *    returned.  An empty map yields sqdist = INT32_MAX and idx = -1 everywhere.
+ *  - Calls are asynchronous and ordered on the map's CUDA stream unless stated
+ *    otherwise.  Pointers named *_dev are device pointers, *_host host pointers.
+ *    The caller owns every pointer it passes and keeps it valid until the stream work
+ *    that uses it has completed.  The map owns its grids, fields and scratch.
+ *  - Every call returns a vedt_status and never throws across the ABI.  Argument
+ *    errors are detected on the host before any launch (VEDT_EINVAL).  A bounded wait
+ *    that expires inside a kernel sets an error word that the next synchronising call
+ *    reports (VEDT_ETIMEOUT).
+ */
+#ifndef VEDT_H
+#define VEDT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VEDT_MAX_DIM 1024
+#define VEDT_MAX_LINKS 16
+#define VEDT_MAX_JOINTS 15
+
+typedef enum {
+    VEDT_OK = 0,
+    VEDT_EINVAL = -1,    /* bad argument (null handle, dims, sizes, mask, ...)          */
+    VEDT_ENOMEM = -2,    /* device or host allocation failed                           */
+    VEDT_ECUDA = -3,     /* a CUDA runtime/driver call failed                          */
+    VEDT_ETIMEOUT = -4,  /* a bounded in-kernel wait expired; results are invalid      */
+    VEDT_EBUSY = -5,     /* not enough free device memory to admit the request         */
+    VEDT_ENOTSUP = -6    /* request outside what this build supports                   */
+} vedt_status;
+
+/* which map(s) a call acts on */
+enum { VEDT_MAP_ENV = 1, VEDT_MAP_SELF = 2, VEDT_MAP_BOTH = 3 };
+
+/* sphere query status */
+enum { VEDT_SPHERE_OK = 0, VEDT_SPHERE_OUTSIDE = 1, VEDT_SPHERE_EMPTY = 2 };
+
+typedef struct vedt_map vedt_map;
+
+/* Result of one sphere against one map (32 bytes). */
+typedef struct {
+    int32_t sqdist;      /* squared voxel distance at the centre's voxel (-1 if outside)  */
+    int32_t idx;         /* linear index of the nearest occupied voxel O_i (-1 if none)   */
+    float dist;          /* x_ci of Eq. (dist) in metres: voxel_size * sqrtf(sqdist)      */
+    float clearance;     /* dist - sphere radius (Eq. (ref): >= 0 means no collision)     */
+    float nearest[3];    /* world centre of voxel idx: origin + (v + 0.5) * voxel_size     */
+    int32_t status;      /* VEDT_SPHERE_OK / _OUTSIDE (dist NaN) / _EMPTY (dist +inf)      */
+} vedt_sphere_result;
+
+/* Serial kinematic chain for vedt_fk / vedt_insert_robot.  Link 0 is the static body,
+ * at `base` (3x4 row-major rotation | translation) in the world.  Joint k (1..n) sits
+ * at offset[k-1] (3x4) in link k-1's frame and turns link k about that frame's z axis:
+ * T_0 = base, T_k = T_(k-1) * offset_k * Rz(q_k). */
+typedef struct {
+    int32_t n_joints;                       /* 1 .. VEDT_MAX_JOINTS                    */
+    double base[12];
+    double offset[VEDT_MAX_JOINTS][12];
+} vedt_chain;
+
+/* ---- lifecycle (Alg. 2 line 1) ---------------------------------------------------- */
+
+/* Creates M_I (environment) and M_S (self) grids of dims[3] = {X, Y, Z} voxels with
+ * edge voxel_size > 0 and world min corner origin[3], plus both distance fields and
+ * the EDT scratch; all device memory is allocated here (about 13*X*Y*Z bytes per grid
+ * for dims <= 256, 19*X*Y*Z above).  `stream` is a cudaStream_t (NULL = legacy default
+ * stream).  Grids start cleared.  *out receives the handle.  Errors: EINVAL, ENOMEM,
+ * ECUDA. */
+vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float origin[3],
+                            void *stream, vedt_map **out);
+
+/* Frees all device memory of the map (synchronises its stream first).  NULL is a no-op. */
+vedt_status vedt_map_destroy(vedt_map *map);
+
+/* Rebinds the map to another stream (cudaStream_t); later calls are ordered there. */
+vedt_status vedt_map_set_stream(vedt_map *map, void *stream);
+
+/* Reports dims, voxel size and origin (any output may be NULL). */
+vedt_status vedt_map_info(const vedt_map *map, int32_t dims_out[3], float *voxel_size_out,
+                          float origin_out[3]);
+
+/* ---- per-frame steps ---------------------------------------------------------------- */
+
+/* ClearMap (Alg. 2 line 4; Tab. 1 "Clear Map"): zeroes the occupancy of the selected
+ * map(s) (`which` = VEDT_MAP_ENV / _SELF / _BOTH). */
+vedt_status vedt_clear(vedt_map *map, int which);
+
+/* Insert(Point_Cloud) (Alg. 2 line 7; Sec. III-A).  xyz_dev: n_points x 3 fp32 device
+ * array (sensor frame if T_world_sensor_host != NULL, else world).  T_world_sensor_host:
+ * optional 3x4 fp32 row-major pose applied as w_a = ((T_a0 p_x + T_a1 p_y) + T_a2 p_z)
+ * + T_a3 in fp32 without FMA.  Points outside the grid are dropped; with filter_self != 0
+ * points whose voxel is occupied in M_S are dropped (robot-point removal, Sec. III-A).
+ * counts_dev (nullable, device int64[3]) is incremented by {written, outside, filtered}.
+ * n_points = 0 is valid.  Errors: EINVAL (null map/xyz with n > 0, n < 0). */
+vedt_status vedt_insert_pointcloud(vedt_map *map, const float *xyz_dev, int64_t n_points,
+                                   const float *T_world_sensor_host, int filter_self,
+                                   int64_t *counts_dev);
+
+/* Registers the offline link voxel models (Sec. III-A): link k's model is
+ * link_xyz_host[k], n_vox[k] fp32 xyz points in the link frame.  Copied to the device
+ * once (synchronously); replaces any earlier registration.  Link 0 is the static body.
+ * 1 <= n_links <= VEDT_MAX_LINKS, n_vox[k] >= 0.  Errors: EINVAL, ENOMEM, ECUDA. */
+vedt_status vedt_register_links(vedt_map *map, int n_links, const float *const *link_xyz_host,
+                                const int64_t *n_vox);
+
+/* UpdateLinks + Insert(O_Lk) (Alg. 2 lines 5-6; Sec. III-E): moves every registered
+ * link k with bit k set in link_mask by poses_host[12k .. 12k+12) (3x4 fp32 row-major
+ * R | t, same arithmetic as above) and marks the voxels in M_S.  The set of links in
+ * the mask is the self-collision obstacle O_L of Eq. (selfclink).  Errors: EINVAL (no
+ * links registered, mask names an unregistered link). */
+vedt_status vedt_insert_links(vedt_map *map, const float *poses_host, uint32_t link_mask);
+
+/* Forward kinematics on the host in fp64 (Alg. 2 lines 5 and 8): poses_out receives
+ * (chain->n_joints + 1) 3x4 row-major transforms T_0 .. T_n (see vedt_chain).  Each
+ * matrix entry is summed left to right without FMA.  Errors: EINVAL. */
+vedt_status vedt_fk(const vedt_chain *chain, const double *q, double *poses_out);
+
+/* vedt_fk followed by rounding the poses to fp32 and vedt_insert_links(link_mask).
+ * The chain must have n_joints + 1 <= registered links.  Errors: as both calls. */
+vedt_status vedt_insert_robot(vedt_map *map, const vedt_chain *chain, const double *q,
+                              uint32_t link_mask);
+
+/* PBA_EDT (Alg. 2 line 9; Sec. III-C, Alg. 1): exact squared Euclidean distance
+ * transform of the selected occupancy grid(s) with a nearest occupied voxel per voxel,
+ * as three separable sweeps (rows along x; lower envelopes along y, then along z). */
+vedt_status vedt_compute_edt(vedt_map *map, int which);
+
+/* ExtractClosestObstaclePose + x_ci = |O_i - C_i| (Alg. 2 line 10; Eq. (dist); Alg. 3
+ * lines 3-4) at the voxels holding the m sphere centres.  centres_host: m x 3 fp32
+ * world; radii_host: m fp32.  out_host: m results per selected map, ENV block first
+ * when which = VEDT_MAP_BOTH (2m results).  Synchronises the stream and reports any
+ * pending in-kernel error.  1 <= m <= 4096.  Errors: EINVAL, ETIMEOUT, ECUDA. */
+vedt_status vedt_query_spheres(vedt_map *map, const float *centres_host, const float *radii_host,
+                               int m, int which, vedt_sphere_result *out_host);
+
+/* Same query on device buffers, asynchronous (no synchronisation, no error check). */
+vedt_status vedt_query_spheres_dev(vedt_map *map, const float *centres_dev, const float *radii_dev,
+                                   int m, int which, vedt_sphere_result *out_dev);
+
+/* ---- one control cycle ------------------------------------------------------------------- */
+
+/* Alg. 2 lines 4-10 in one call on device buffers, asynchronous: vedt_clear(BOTH),
+ * vedt_insert_robot(chain, q, link_mask) (skipped if chain == NULL), vedt_insert_pointcloud
+ * (xyz_dev, n_points, T_world_sensor_host, filter_self = 1), vedt_compute_edt(BOTH) and
+ * vedt_query_spheres_dev(centres_dev, radii_dev, m, BOTH, out_dev) (skipped if m == 0).
+ * Errors: as the individual calls. */
+vedt_status vedt_frame(vedt_map *map, const float *xyz_dev, int64_t n_points,
+                       const float *T_world_sensor_host, const vedt_chain *chain, const double *q,
+                       uint32_t link_mask, const float *centres_dev, const float *radii_dev, int m,
+                       vedt_sphere_result *out_dev);
+
+/* The same cycle from host buffers: copies xyz_host (n_points x 3 fp32; page-locked memory
+ * makes the copy asynchronous) into the map's device staging buffer (grown on demand,
+ * ENOMEM if that fails) and centres/radii into device scratch, runs vedt_frame, copies the
+ * 2m results (ENV block first) to out_host and synchronises the stream, reporting any
+ * pending in-kernel error.  1 <= m <= 4096 or m == 0. */
+vedt_status vedt_frame_host(vedt_map *map, const float *xyz_host, int64_t n_points,
+                            const float *T_world_sensor_host, const vedt_chain *chain, const double *q,
+                            uint32_t link_mask, const float *centres_host, const float *radii_host,
+                            int m, vedt_sphere_result *out_host);
+
+/* ---- access ---------------------------------------------------------------------------- */
+
+/* Borrowed device pointers to the selected map's fields (which = ENV or SELF), valid
+ * until the map is destroyed; contents change with later calls. */
+vedt_status vedt_get_field(vedt_map *map, int which, const int32_t **sqdist_dev,
+                           const int32_t **idx_dev);
+vedt_status vedt_get_occupancy(vedt_map *map, int which, uint8_t **occ_dev);
+
+/* Synchronises the map's stream and returns ETIMEOUT/ECUDA if any kernel flagged an
+ * error since the last check (and clears the flag), else OK. */
+vedt_status vedt_check(vedt_map *map);
+
+/* Per-kernel timing with CUDA events on the map's stream.  enable != 0 starts
+ * recording an event pair around every launch; vedt_kernel_times synchronises and adds
+ * the accumulated milliseconds and launch counts of each kernel kind into ms_out /
+ * count_out (arrays of VEDT_NUM_KERNELS, nullable), then resets the accumulators. */
+enum { VEDT_K_CLEAR = 0, VEDT_K_INSERT_LINKS, VEDT_K_INSERT_POINTS, VEDT_K_EDT_X,
+       VEDT_K_EDT_Y, VEDT_K_EDT_Z, VEDT_K_QUERY, VEDT_NUM_KERNELS };
+vedt_status vedt_set_timing(vedt_map *map, int enable);
+vedt_status vedt_kernel_times(vedt_map *map, double *ms_out, int64_t *count_out);
+
+/* Human-readable text for a status code (static storage). */
+const char *vedt_status_string(vedt_status s);
+
+/* Library version string. */
+const char *vedt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VEDT_H */

@@ -1,0 +1,564 @@
+// C ABI of libvedt: map lifecycle, per-frame calls, forward kinematics, timing.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "vedt_internal.h"
+
+using namespace vedt;
+
+namespace {
+
+constexpr int kMaxQuery = 4096;
+
+struct EvPair {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct vedt_map {
+    int32_t X = 0, Y = 0, Z = 0, Xp = 0;
+    float vs = 0.f;
+    float origin[3] = {0, 0, 0};
+    cudaStream_t stream = nullptr;
+    int large = 0;
+    int64_t N = 0;
+    // [0] = environment M_I, [1] = self M_S
+    uint8_t *occ[2] = {nullptr, nullptr};
+    int32_t *sq[2] = {nullptr, nullptr};
+    int32_t *ix[2] = {nullptr, nullptr};
+    uint16_t *xs[2] = {nullptr, nullptr};
+    void *s2[2] = {nullptr, nullptr};
+    uint8_t *slice_has[2] = {nullptr, nullptr};
+    int32_t *err = nullptr;
+    // EDT launch tables for which = ENV (0), SELF (1), BOTH (2)
+    GridTable tab[3];
+    void *tab_mem = nullptr;
+    // query scratch
+    QueryGrid *qgrids = nullptr;   // device [3]: env, self, env+self ... see below
+    float *q_in = nullptr;         // device centres (3*kMaxQuery) + radii (kMaxQuery)
+    vedt_sphere_result *q_out = nullptr;
+    // links
+    float *link_pts = nullptr;
+    uint8_t *link_of = nullptr;
+    float *stage = nullptr;        // device staging for host point clouds
+    int64_t stage_cap = 0;         // points
+    int64_t n_link_pts = 0;
+    int n_links = 0;
+    // timing
+    bool timing = false;
+    std::vector<EvPair> pending;
+    std::vector<cudaEvent_t> free_events;
+    double ms[VEDT_NUM_KERNELS] = {};
+    int64_t cnt[VEDT_NUM_KERNELS] = {};
+};
+
+namespace {
+
+vedt_status from_cuda(cudaError_t e) { return e == cudaSuccess ? VEDT_OK : (e == cudaErrorMemoryAllocation ? VEDT_ENOMEM : VEDT_ECUDA); }
+
+#define VCHECK(call)                                  \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return from_cuda(e_);  \
+    } while (0)
+
+cudaEvent_t take_event(vedt_map *m) {
+    if (!m->free_events.empty()) {
+        cudaEvent_t e = m->free_events.back();
+        m->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records an event before a launch when timing is on; returns the pending slot or -1.
+int timing_begin(vedt_map *m, int kind) {
+    if (!m->timing) return -1;
+    EvPair p{kind, take_event(m), take_event(m)};
+    cudaEventRecord(p.a, m->stream);
+    m->pending.push_back(p);
+    return static_cast<int>(m->pending.size()) - 1;
+}
+
+void timing_end(vedt_map *m, int slot) {
+    if (slot >= 0) cudaEventRecord(m->pending[slot].b, m->stream);
+}
+
+void harvest(vedt_map *m) {
+    for (auto &p : m->pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+            m->ms[p.kind] += t;
+            m->cnt[p.kind] += 1;
+        }
+        m->free_events.push_back(p.a);
+        m->free_events.push_back(p.b);
+    }
+    m->pending.clear();
+}
+
+bool valid_which(int w) { return w == VEDT_MAP_ENV || w == VEDT_MAP_SELF || w == VEDT_MAP_BOTH; }
+
+}  // namespace
+
+namespace vedt {
+
+CUresult encode_tmap(CUtensorMap *m, CUtensorMapDataType t, int elem, void *base, uint64_t d0, uint64_t d1,
+                     uint64_t d2, uint32_t b0, uint32_t b1, uint32_t b2) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    if (!fn) return CUDA_ERROR_NOT_FOUND;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {d0 * elem, d0 * d1 * elem};
+    const cuuint32_t box[3] = {b0, b1, b2};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, t, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+// Fills desc/tmaps for grids (host copies) and uploads them; used by maps and batches.
+vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *dev_desc, void *dev_tmaps,
+                        int32_t *err) {
+    std::vector<GridDesc> d(grids);
+    std::vector<CUtensorMap> tm(2 * grids.size());
+    int64_t rows = 0, ty = 0, tz = 0;
+    t.large = 0;
+    t.maxY = t.maxZ = 0;
+    for (size_t i = 0; i < d.size(); ++i) {
+        GridDesc &g = d[i];
+        g.row_begin = rows;
+        g.ty_begin = ty;
+        g.tz_begin = tz;
+        rows += static_cast<int64_t>(g.Y) * g.Z;
+        ty += static_cast<int64_t>(g.Xp / kTile) * g.Z;
+        tz += static_cast<int64_t>(g.Xp / kTile) * g.Y;
+        const bool large = g.X > kSmallMax || g.Y > kSmallMax || g.Z > kSmallMax;
+        t.large |= large;
+        t.maxY = g.Y > t.maxY ? g.Y : t.maxY;
+        t.maxZ = g.Z > t.maxZ ? g.Z : t.maxZ;
+    }
+    for (size_t i = 0; i < d.size(); ++i) {
+        GridDesc &g = d[i];
+        const uint32_t by = g.Y > kBox ? kBox : g.Y, bz = g.Z > kBox ? kBox : g.Z;
+        if (encode_tmap(&tm[2 * i], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, g.xs, g.Xp, g.Y, g.Z, kTile, by, 1) !=
+            CUDA_SUCCESS)
+            return VEDT_ECUDA;
+        const bool big = t.large != 0;
+        if (encode_tmap(&tm[2 * i + 1], big ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                        big ? 4 : 2, g.s2, g.Xp, g.Y, g.Z, kTile, 1, bz) != CUDA_SUCCESS)
+            return VEDT_ECUDA;
+    }
+    VCHECK(cudaMemcpy(dev_desc, d.data(), sizeof(GridDesc) * d.size(), cudaMemcpyHostToDevice));
+    VCHECK(cudaMemcpy(dev_tmaps, tm.data(), sizeof(CUtensorMap) * tm.size(), cudaMemcpyHostToDevice));
+    t.desc = static_cast<GridDesc *>(dev_desc);
+    t.tmaps = static_cast<CUtensorMap *>(dev_tmaps);
+    t.n = static_cast<int>(d.size());
+    t.rows = rows;
+    t.tiles_y = ty;
+    t.tiles_z = tz;
+    t.err = err;
+    return VEDT_OK;
+}
+
+}  // namespace vedt
+
+namespace {
+
+void free_map(vedt_map *m) {
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(m->occ[i]);
+        cudaFree(m->sq[i]);
+        cudaFree(m->ix[i]);
+        cudaFree(m->xs[i]);
+        cudaFree(m->s2[i]);
+        cudaFree(m->slice_has[i]);
+    }
+    cudaFree(m->err);
+    cudaFree(m->tab_mem);
+    cudaFree(m->qgrids);
+    cudaFree(m->q_in);
+    cudaFree(m->q_out);
+    cudaFree(m->link_pts);
+    cudaFree(m->link_of);
+    cudaFree(m->stage);
+    for (auto &p : m->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : m->free_events) cudaEventDestroy(e);
+    delete m;
+}
+
+GridDesc grid_of(const vedt_map *m, int i) {
+    GridDesc g{};
+    g.occ = m->occ[i];
+    g.xs = m->xs[i];
+    g.s2 = m->s2[i];
+    g.slice_has = m->slice_has[i];
+    g.sqdist = m->sq[i];
+    g.idx = m->ix[i];
+    g.X = m->X;
+    g.Y = m->Y;
+    g.Z = m->Z;
+    g.Xp = m->Xp;
+    return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vedt_version(void) { return "vedt 0.1 (sm_103a)"; }
+
+const char *vedt_status_string(vedt_status s) {
+    switch (s) {
+        case VEDT_OK: return "ok";
+        case VEDT_EINVAL: return "invalid argument";
+        case VEDT_ENOMEM: return "out of memory";
+        case VEDT_ECUDA: return "CUDA error";
+        case VEDT_ETIMEOUT: return "in-kernel wait timed out";
+        case VEDT_EBUSY: return "not enough free device memory";
+        case VEDT_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float origin[3], void *stream,
+                            vedt_map **out) {
+    if (!dims || !origin || !out) return VEDT_EINVAL;
+    *out = nullptr;
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > VEDT_MAX_DIM || !std::isfinite(origin[a])) return VEDT_EINVAL;
+    if (!(voxel_size > 0.f) || !std::isfinite(voxel_size)) return VEDT_EINVAL;
+    vedt_map *m = new (std::nothrow) vedt_map();
+    if (!m) return VEDT_ENOMEM;
+    m->X = dims[0];
+    m->Y = dims[1];
+    m->Z = dims[2];
+    m->Xp = (m->X + kTile - 1) / kTile * kTile;
+    m->vs = voxel_size;
+    for (int a = 0; a < 3; ++a) m->origin[a] = origin[a];
+    m->stream = static_cast<cudaStream_t>(stream);
+    m->large = (m->X > kSmallMax || m->Y > kSmallMax || m->Z > kSmallMax) ? 1 : 0;
+    m->N = static_cast<int64_t>(m->X) * m->Y * m->Z;
+    const int64_t Np = static_cast<int64_t>(m->Xp) * m->Y * m->Z;
+    const size_t s2b = m->large ? 4 : 2;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        if (e == cudaSuccess) e = cudaMalloc(&m->occ[i], m->N);
+        if (e == cudaSuccess) e = cudaMalloc(&m->sq[i], m->N * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&m->ix[i], m->N * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&m->xs[i], Np * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&m->s2[i], Np * s2b);
+        if (e == cudaSuccess) e = cudaMalloc(&m->slice_has[i], m->Z);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(int32_t));
+    const size_t desc_bytes = sizeof(GridDesc) * 4, tm_bytes = sizeof(CUtensorMap) * 8;
+    if (e == cudaSuccess) e = cudaMalloc(&m->tab_mem, desc_bytes + tm_bytes + 256);
+    if (e == cudaSuccess) e = cudaMalloc(&m->qgrids, sizeof(QueryGrid) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->q_in, sizeof(float) * 4 * kMaxQuery);
+    if (e == cudaSuccess) e = cudaMalloc(&m->q_out, sizeof(vedt_sphere_result) * 2 * kMaxQuery);
+    if (e != cudaSuccess) {
+        free_map(m);
+        return from_cuda(e);
+    }
+    e = cudaMemset(m->err, 0, sizeof(int32_t));
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemset(m->occ[i], 0, m->N);
+    if (e != cudaSuccess) {
+        free_map(m);
+        return from_cuda(e);
+    }
+    // tables: ENV = {0}, SELF = {1}, BOTH = {0, 1}; descriptors then tensor maps (64B aligned)
+    char *base = static_cast<char *>(m->tab_mem);
+    char *tmb = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(base + desc_bytes) + 127) & ~uintptr_t(127));
+    const std::vector<GridDesc> g0{grid_of(m, 0)}, g1{grid_of(m, 1)}, g01{grid_of(m, 0), grid_of(m, 1)};
+    vedt_status st = build_table(m->tab[0], g0, base, tmb, m->err);
+    if (st == VEDT_OK)
+        st = build_table(m->tab[1], g1, base + sizeof(GridDesc), tmb + 2 * sizeof(CUtensorMap), m->err);
+    if (st == VEDT_OK)
+        st = build_table(m->tab[2], g01, base + 2 * sizeof(GridDesc), tmb + 4 * sizeof(CUtensorMap), m->err);
+    const QueryGrid qg[4] = {{m->sq[0], m->ix[0]}, {m->sq[1], m->ix[1]}, {m->sq[0], m->ix[0]}, {m->sq[1], m->ix[1]}};
+    if (st == VEDT_OK) st = from_cuda(cudaMemcpy(m->qgrids, qg, sizeof(qg), cudaMemcpyHostToDevice));
+    if (st != VEDT_OK) {
+        free_map(m);
+        return st;
+    }
+    *out = m;
+    return VEDT_OK;
+}
+
+vedt_status vedt_map_destroy(vedt_map *m) {
+    if (!m) return VEDT_OK;
+    cudaStreamSynchronize(m->stream);
+    free_map(m);
+    return VEDT_OK;
+}
+
+vedt_status vedt_map_set_stream(vedt_map *m, void *stream) {
+    if (!m) return VEDT_EINVAL;
+    m->stream = static_cast<cudaStream_t>(stream);
+    return VEDT_OK;
+}
+
+vedt_status vedt_map_info(const vedt_map *m, int32_t dims_out[3], float *vs, float origin_out[3]) {
+    if (!m) return VEDT_EINVAL;
+    if (dims_out) {
+        dims_out[0] = m->X;
+        dims_out[1] = m->Y;
+        dims_out[2] = m->Z;
+    }
+    if (vs) *vs = m->vs;
+    if (origin_out)
+        for (int a = 0; a < 3; ++a) origin_out[a] = m->origin[a];
+    return VEDT_OK;
+}
+
+vedt_status vedt_clear(vedt_map *m, int which) {
+    if (!m || !valid_which(which)) return VEDT_EINVAL;
+    for (int i = 0; i < 2; ++i) {
+        if (!(which & (1 << i))) continue;
+        const int slot = timing_begin(m, VEDT_K_CLEAR);
+        VCHECK(launch_clear(m->occ[i], m->N, m->stream));
+        timing_end(m, slot);
+    }
+    return VEDT_OK;
+}
+
+vedt_status vedt_insert_pointcloud(vedt_map *m, const float *xyz_dev, int64_t n, const float *T,
+                                   int filter_self, int64_t *counts_dev) {
+    if (!m || n < 0 || (n > 0 && !xyz_dev)) return VEDT_EINVAL;
+    if (n == 0) return VEDT_OK;
+    const int slot = timing_begin(m, VEDT_K_INSERT_POINTS);
+    VCHECK(launch_insert_points(m->occ[0], m->occ[1], m->X, m->Y, m->Z, m->vs, m->origin, xyz_dev, n, T,
+                                filter_self ? 1 : 0, counts_dev, m->stream));
+    timing_end(m, slot);
+    return VEDT_OK;
+}
+
+vedt_status vedt_register_links(vedt_map *m, int n_links, const float *const *xyz, const int64_t *n_vox) {
+    if (!m || n_links < 1 || n_links > VEDT_MAX_LINKS || !xyz || !n_vox) return VEDT_EINVAL;
+    int64_t total = 0;
+    for (int k = 0; k < n_links; ++k) {
+        if (n_vox[k] < 0 || (n_vox[k] > 0 && !xyz[k])) return VEDT_EINVAL;
+        total += n_vox[k];
+    }
+    std::vector<float> pts(static_cast<size_t>(total) * 3);
+    std::vector<uint8_t> of(static_cast<size_t>(total));
+    int64_t w = 0;
+    for (int k = 0; k < n_links; ++k) {
+        if (n_vox[k] > 0) std::memcpy(pts.data() + 3 * w, xyz[k], sizeof(float) * 3 * n_vox[k]);
+        std::memset(of.data() + w, k, static_cast<size_t>(n_vox[k]));
+        w += n_vox[k];
+    }
+    VCHECK(cudaStreamSynchronize(m->stream));
+    cudaFree(m->link_pts);
+    cudaFree(m->link_of);
+    m->link_pts = nullptr;
+    m->link_of = nullptr;
+    m->n_link_pts = 0;
+    m->n_links = 0;
+    if (total > 0) {
+        VCHECK(cudaMalloc(&m->link_pts, pts.size() * sizeof(float)));
+        VCHECK(cudaMalloc(&m->link_of, of.size()));
+        VCHECK(cudaMemcpy(m->link_pts, pts.data(), pts.size() * sizeof(float), cudaMemcpyHostToDevice));
+        VCHECK(cudaMemcpy(m->link_of, of.data(), of.size(), cudaMemcpyHostToDevice));
+    }
+    m->n_link_pts = total;
+    m->n_links = n_links;
+    return VEDT_OK;
+}
+
+vedt_status vedt_insert_links(vedt_map *m, const float *poses, uint32_t mask) {
+    if (!m || !poses || m->n_links == 0) return VEDT_EINVAL;
+    if (m->n_links < 32 && (mask >> m->n_links) != 0u) return VEDT_EINVAL;
+    LinkPose P{};
+    for (int k = 0; k < m->n_links; ++k)
+        for (int i = 0; i < 12; ++i) P.T[k][i] = poses[12 * k + i];
+    const int slot = timing_begin(m, VEDT_K_INSERT_LINKS);
+    VCHECK(launch_insert_links(m->occ[1], m->X, m->Y, m->Z, m->vs, m->origin, m->link_pts, m->link_of,
+                               m->n_link_pts, P, mask, m->stream));
+    timing_end(m, slot);
+    return VEDT_OK;
+}
+
+vedt_status vedt_fk(const vedt_chain *c, const double *q, double *out) {
+    if (!c || !q || !out || c->n_joints < 1 || c->n_joints > VEDT_MAX_JOINTS) return VEDT_EINVAL;
+    // T_0 = base; T_k = T_(k-1) * offset_k * Rz(q_k); every entry summed left to right.
+    auto mul = [](const double *A, const double *B, double *C) {
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) {
+                double s = A[4 * i] * B[j];
+                s = s + A[4 * i + 1] * B[4 + j];
+                s = s + A[4 * i + 2] * B[8 + j];
+                C[4 * i + j] = s;
+            }
+            double t = A[4 * i] * B[3];
+            t = t + A[4 * i + 1] * B[7];
+            t = t + A[4 * i + 2] * B[11];
+            C[4 * i + 3] = t + A[4 * i + 3];
+        }
+    };
+    std::memcpy(out, c->base, sizeof(double) * 12);
+    for (int k = 0; k < c->n_joints; ++k) {
+        const double cq = std::cos(q[k]), sq = std::sin(q[k]);
+        const double rz[12] = {cq, -sq, 0.0, 0.0, sq, cq, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0};
+        double tmp[12];
+        mul(out + 12 * k, c->offset[k], tmp);
+        mul(tmp, rz, out + 12 * (k + 1));
+    }
+    return VEDT_OK;
+}
+
+vedt_status vedt_insert_robot(vedt_map *m, const vedt_chain *c, const double *q, uint32_t mask) {
+    if (!m || !c || !q || c->n_joints < 1 || c->n_joints > VEDT_MAX_JOINTS) return VEDT_EINVAL;
+    if (c->n_joints + 1 > m->n_links) return VEDT_EINVAL;
+    double P[(VEDT_MAX_JOINTS + 1) * 12];
+    vedt_status st = vedt_fk(c, q, P);
+    if (st != VEDT_OK) return st;
+    float Pf[VEDT_MAX_LINKS * 12] = {};
+    for (int i = 0; i < (c->n_joints + 1) * 12 && i < VEDT_MAX_LINKS * 12; ++i) Pf[i] = static_cast<float>(P[i]);
+    return vedt_insert_links(m, Pf, mask);
+}
+
+vedt_status vedt_compute_edt(vedt_map *m, int which) {
+    if (!m || !valid_which(which)) return VEDT_EINVAL;
+    const GridTable &t = m->tab[which - 1];
+    int slot = timing_begin(m, VEDT_K_EDT_X);
+    VCHECK(launch_pass_x(t, m->stream));
+    timing_end(m, slot);
+    slot = timing_begin(m, VEDT_K_EDT_Y);
+    VCHECK(launch_pass_y(t, m->stream));
+    timing_end(m, slot);
+    slot = timing_begin(m, VEDT_K_EDT_Z);
+    VCHECK(launch_pass_z(t, m->stream));
+    timing_end(m, slot);
+    return VEDT_OK;
+}
+
+vedt_status vedt_query_spheres_dev(vedt_map *m, const float *centres, const float *radii, int n, int which,
+                                   vedt_sphere_result *out) {
+    if (!m || !centres || !radii || !out || n < 1 || n > kMaxQuery || !valid_which(which)) return VEDT_EINVAL;
+    const QueryGrid *g = which == VEDT_MAP_SELF ? m->qgrids + 1 : m->qgrids;
+    const int ng = which == VEDT_MAP_BOTH ? 2 : 1;
+    const int slot = timing_begin(m, VEDT_K_QUERY);
+    VCHECK(launch_query(g, ng, m->X, m->Y, m->Z, m->vs, m->origin, centres, radii, n, out, m->stream));
+    timing_end(m, slot);
+    return VEDT_OK;
+}
+
+vedt_status vedt_check(vedt_map *m) {
+    if (!m) return VEDT_EINVAL;
+    VCHECK(cudaStreamSynchronize(m->stream));
+    int32_t e = 0;
+    VCHECK(cudaMemcpy(&e, m->err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e) {
+        VCHECK(cudaMemset(m->err, 0, sizeof(int32_t)));
+        return (e & kErrTimeout) ? VEDT_ETIMEOUT : VEDT_ECUDA;
+    }
+    return VEDT_OK;
+}
+
+vedt_status vedt_query_spheres(vedt_map *m, const float *centres, const float *radii, int n, int which,
+                               vedt_sphere_result *out) {
+    if (!m || !centres || !radii || !out || n < 1 || n > kMaxQuery || !valid_which(which)) return VEDT_EINVAL;
+    VCHECK(cudaMemcpyAsync(m->q_in, centres, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->stream));
+    VCHECK(cudaMemcpyAsync(m->q_in + 3 * kMaxQuery, radii, sizeof(float) * n, cudaMemcpyHostToDevice, m->stream));
+    vedt_status st = vedt_query_spheres_dev(m, m->q_in, m->q_in + 3 * kMaxQuery, n, which, m->q_out);
+    if (st != VEDT_OK) return st;
+    const int ng = which == VEDT_MAP_BOTH ? 2 : 1;
+    VCHECK(cudaMemcpyAsync(out, m->q_out, sizeof(vedt_sphere_result) * n * ng, cudaMemcpyDeviceToHost, m->stream));
+    return vedt_check(m);
+}
+
+vedt_status vedt_frame(vedt_map *m, const float *xyz, int64_t n, const float *T, const vedt_chain *chain,
+                       const double *q, uint32_t mask, const float *centres, const float *radii, int nq,
+                       vedt_sphere_result *out) {
+    if (!m || n < 0 || (n > 0 && !xyz) || (chain && !q) || nq < 0 || nq > kMaxQuery) return VEDT_EINVAL;
+    if (nq > 0 && (!centres || !radii || !out)) return VEDT_EINVAL;
+    vedt_status st = vedt_clear(m, VEDT_MAP_BOTH);
+    if (st == VEDT_OK && chain) st = vedt_insert_robot(m, chain, q, mask);
+    if (st == VEDT_OK) st = vedt_insert_pointcloud(m, xyz, n, T, 1, nullptr);
+    if (st == VEDT_OK) st = vedt_compute_edt(m, VEDT_MAP_BOTH);
+    if (st == VEDT_OK && nq > 0) st = vedt_query_spheres_dev(m, centres, radii, nq, VEDT_MAP_BOTH, out);
+    return st;
+}
+
+vedt_status vedt_frame_host(vedt_map *m, const float *xyz, int64_t n, const float *T, const vedt_chain *chain,
+                            const double *q, uint32_t mask, const float *centres, const float *radii, int nq,
+                            vedt_sphere_result *out) {
+    if (!m || n < 0 || (n > 0 && !xyz) || nq < 0 || nq > kMaxQuery) return VEDT_EINVAL;
+    if (nq > 0 && (!centres || !radii || !out)) return VEDT_EINVAL;
+    if (n > m->stage_cap) {
+        VCHECK(cudaStreamSynchronize(m->stream));
+        cudaFree(m->stage);
+        m->stage = nullptr;
+        m->stage_cap = 0;
+        VCHECK(cudaMalloc(&m->stage, sizeof(float) * 3 * n));
+        m->stage_cap = n;
+    }
+    if (n > 0) VCHECK(cudaMemcpyAsync(m->stage, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->stream));
+    if (nq > 0) {
+        VCHECK(cudaMemcpyAsync(m->q_in, centres, sizeof(float) * 3 * nq, cudaMemcpyHostToDevice, m->stream));
+        VCHECK(cudaMemcpyAsync(m->q_in + 3 * kMaxQuery, radii, sizeof(float) * nq, cudaMemcpyHostToDevice,
+                               m->stream));
+    }
+    vedt_status st = vedt_frame(m, m->stage, n, T, chain, q, mask, m->q_in, m->q_in + 3 * kMaxQuery, nq, m->q_out);
+    if (st != VEDT_OK) return st;
+    if (nq > 0)
+        VCHECK(cudaMemcpyAsync(out, m->q_out, sizeof(vedt_sphere_result) * 2 * nq, cudaMemcpyDeviceToHost,
+                               m->stream));
+    return vedt_check(m);
+}
+
+vedt_status vedt_get_field(vedt_map *m, int which, const int32_t **sq, const int32_t **ix) {
+    if (!m || (which != VEDT_MAP_ENV && which != VEDT_MAP_SELF)) return VEDT_EINVAL;
+    const int i = which == VEDT_MAP_ENV ? 0 : 1;
+    if (sq) *sq = m->sq[i];
+    if (ix) *ix = m->ix[i];
+    return VEDT_OK;
+}
+
+vedt_status vedt_get_occupancy(vedt_map *m, int which, uint8_t **occ) {
+    if (!m || !occ || (which != VEDT_MAP_ENV && which != VEDT_MAP_SELF)) return VEDT_EINVAL;
+    *occ = m->occ[which == VEDT_MAP_ENV ? 0 : 1];
+    return VEDT_OK;
+}
+
+vedt_status vedt_set_timing(vedt_map *m, int enable) {
+    if (!m) return VEDT_EINVAL;
+    m->timing = enable != 0;
+    return VEDT_OK;
+}
+
+vedt_status vedt_kernel_times(vedt_map *m, double *ms_out, int64_t *count_out) {
+    if (!m) return VEDT_EINVAL;
+    VCHECK(cudaStreamSynchronize(m->stream));
+    harvest(m);
+    for (int k = 0; k < VEDT_NUM_KERNELS; ++k) {
+        if (ms_out) ms_out[k] = m->ms[k];
+        if (count_out) count_out[k] = m->cnt[k];
+        m->ms[k] = 0;
+        m->cnt[k] = 0;
+    }
+    return VEDT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+// Per-frame occupancy updates and the sphere query (Alg. 2 lines 4-7 and 10).
+//
+// All floating-point steps that decide an integer voxel use explicitly rounded
+// intrinsics in a fixed order (no FMA contraction, IEEE division), so that a point lands
+// in the same voxel as under any other correctly rounded fp32 evaluation of
+//   w_a = ((R_a0 p_x + R_a1 p_y) + R_a2 p_z) + t_a,   v_a = floor((w_a - origin_a) / vs).
+#include "vedt_internal.h"
+
+namespace vedt {
+
+struct Origin { float o[3]; };
+
+__device__ __forceinline__ bool voxel_coord(float p, float o, float vs, int n, int &v) {
+    const float f = floorf(__fdiv_rn(__fsub_rn(p, o), vs));
+    if (!(f >= 0.0f) || !(f < static_cast<float>(n))) return false;   // NaN fails both tests
+    v = static_cast<int>(f);
+    return true;
+}
+
+__device__ __forceinline__ void rigid(const float *T, float px, float py, float pz, float &wx,
+                                      float &wy, float &wz) {
+    wx = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[0], px), __fmul_rn(T[1], py)), __fmul_rn(T[2], pz)), T[3]);
+    wy = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[4], px), __fmul_rn(T[5], py)), __fmul_rn(T[6], pz)), T[7]);
+    wz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[8], px), __fmul_rn(T[9], py)), __fmul_rn(T[10], pz)), T[11]);
+}
+
+// ClearMap (Alg. 2 line 4): 16-byte stores over the byte grid, byte tail.
+__global__ void __launch_bounds__(256) k_clear(uint8_t *__restrict__ p, int64_t n) {
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const int64_t head = static_cast<int64_t>(((a + 15) & ~uintptr_t(15)) - a);
+    const int64_t h = head < n ? head : n;
+    const int64_t nvec = (n - h) >> 4;
+    uint4 *v = reinterpret_cast<uint4 *>(p + h);
+    for (int64_t i = tid; i < nvec; i += stride) v[i] = make_uint4(0, 0, 0, 0);
+    for (int64_t i = tid; i < h; i += stride) p[i] = 0;
+    for (int64_t i = h + (nvec << 4) + tid; i < n; i += stride) p[i] = 0;
+}
+
+struct Pose12 { float T[12]; };
+
+// Insert(Point_Cloud) with robot-point removal (Alg. 2 line 7; Sec. III-A).
+__global__ void __launch_bounds__(256) k_insert_points(uint8_t *__restrict__ env, const uint8_t *__restrict__ self,
+                                                       int X, int Y, int Z, float vs, Origin org,
+                                                       const float *__restrict__ xyz, int64_t n, Pose12 T, int use_T,
+                                                       int filter_self, unsigned long long *counts) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    unsigned long long written = 0, outside = 0, filtered = 0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float wx = __ldg(xyz + 3 * i), wy = __ldg(xyz + 3 * i + 1), wz = __ldg(xyz + 3 * i + 2);
+        if (use_T) rigid(T.T, wx, wy, wz, wx, wy, wz);
+        int vx, vy, vz;
+        if (!voxel_coord(wx, org.o[0], vs, X, vx) || !voxel_coord(wy, org.o[1], vs, Y, vy) ||
+            !voxel_coord(wz, org.o[2], vs, Z, vz)) {
+            ++outside;
+            continue;
+        }
+        const int64_t id = vx + static_cast<int64_t>(X) * (vy + static_cast<int64_t>(Y) * vz);
+        if (filter_self && self[id]) {
+            ++filtered;
+            continue;
+        }
+        env[id] = 1;
+        ++written;
+    }
+    if (counts) {
+        // warp-aggregated counters
+        for (int d = 16; d > 0; d >>= 1) {
+            written += __shfl_down_sync(0xffffffffu, written, d);
+            outside += __shfl_down_sync(0xffffffffu, outside, d);
+            filtered += __shfl_down_sync(0xffffffffu, filtered, d);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (written) atomicAdd(counts + 0, written);
+            if (outside) atomicAdd(counts + 1, outside);
+            if (filtered) atomicAdd(counts + 2, filtered);
+        }
+    }
+}
+
+// UpdateLinks + Insert(O_Lk) (Alg. 2 lines 5-6): every registered link point is moved by
+// its link's pose and marked in the self map if its link is in the mask.
+__global__ void __launch_bounds__(256) k_insert_links(uint8_t *__restrict__ self, int X, int Y, int Z, float vs,
+                                                      Origin org, const float *__restrict__ pts,
+                                                      const uint8_t *__restrict__ link_of, int64_t n,
+                                                      LinkPose poses, uint32_t mask) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int k = link_of[i];
+        if (!((mask >> k) & 1u)) continue;
+        float wx, wy, wz;
+        rigid(poses.T[k], __ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2), wx, wy, wz);
+        int vx, vy, vz;
+        if (!voxel_coord(wx, org.o[0], vs, X, vx) || !voxel_coord(wy, org.o[1], vs, Y, vy) ||
+            !voxel_coord(wz, org.o[2], vs, Z, vz))
+            continue;
+        self[vx + static_cast<int64_t>(X) * (vy + static_cast<int64_t>(Y) * vz)] = 1;
+    }
+}
+
+// ExtractClosestObstaclePose + Eq. (dist): thread (grid g, sphere i).
+__global__ void __launch_bounds__(128) k_query(const QueryGrid *__restrict__ grids, int ng, int X, int Y, int Z,
+                                               float vs, Origin org, const float *__restrict__ centres,
+                                               const float *__restrict__ radii, int m,
+                                               vedt_sphere_result *__restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * ng) return;
+    const int g = t / m, i = t - g * m;
+    vedt_sphere_result r;
+    int v[3];
+    const bool inside = voxel_coord(centres[3 * i], org.o[0], vs, X, v[0]) &&
+                        voxel_coord(centres[3 * i + 1], org.o[1], vs, Y, v[1]) &&
+                        voxel_coord(centres[3 * i + 2], org.o[2], vs, Z, v[2]);
+    if (!inside) {
+        r.sqdist = -1;
+        r.idx = -1;
+        r.dist = __int_as_float(0x7fc00000);
+        r.clearance = r.dist;
+        r.nearest[0] = r.nearest[1] = r.nearest[2] = r.dist;
+        r.status = VEDT_SPHERE_OUTSIDE;
+        out[t] = r;
+        return;
+    }
+    const int64_t id = v[0] + static_cast<int64_t>(X) * (v[1] + static_cast<int64_t>(Y) * v[2]);
+    r.sqdist = grids[g].sqdist[id];
+    r.idx = grids[g].idx[id];
+    if (r.idx < 0) {
+        r.dist = __int_as_float(0x7f800000);
+        r.clearance = r.dist;
+        r.nearest[0] = r.nearest[1] = r.nearest[2] = __int_as_float(0x7fc00000);
+        r.status = VEDT_SPHERE_EMPTY;
+        out[t] = r;
+        return;
+    }
+    r.dist = __fmul_rn(vs, __fsqrt_rn(static_cast<float>(r.sqdist)));
+    r.clearance = __fsub_rn(r.dist, radii[i]);
+    const int j = r.idx;
+    const int nv[3] = {j % X, (j / X) % Y, j / (X * Y)};
+    for (int a = 0; a < 3; ++a)
+        r.nearest[a] = __fadd_rn(org.o[a], __fmul_rn(__fadd_rn(static_cast<float>(nv[a]), 0.5f), vs));
+    r.status = VEDT_SPHERE_OK;
+    out[t] = r;
+}
+
+static int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+cudaError_t launch_clear(uint8_t *p, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n / 16 + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+    const int blocks = static_cast<int>(want < 1 ? 1 : (want < cap ? want : cap));
+    k_clear<<<blocks, 256, 0, s>>>(p, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_insert_points(uint8_t *env, const uint8_t *self, int X, int Y, int Z, float vs,
+                                 const float *origin, const float *xyz, int64_t n, const float *T,
+                                 int filter_self, int64_t *counts, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    Origin o{{origin[0], origin[1], origin[2]}};
+    Pose12 P{};
+    if (T)
+        for (int i = 0; i < 12; ++i) P.T[i] = T[i];
+    const int64_t want = (n + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
+    const int blocks = static_cast<int>(want < cap ? want : cap);
+    k_insert_points<<<blocks, 256, 0, s>>>(env, self, X, Y, Z, vs, o, xyz, n, P, T != nullptr, filter_self,
+                                           reinterpret_cast<unsigned long long *>(counts));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_insert_links(uint8_t *self, int X, int Y, int Z, float vs, const float *origin,
+                                const float *pts, const uint8_t *link_of, int64_t n, const LinkPose &poses,
+                                uint32_t mask, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    Origin o{{origin[0], origin[1], origin[2]}};
+    const int64_t want = (n + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
+    const int blocks = static_cast<int>(want < cap ? want : cap);
+    k_insert_links<<<blocks, 256, 0, s>>>(self, X, Y, Z, vs, o, pts, link_of, n, poses, mask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query(const QueryGrid *g, int ng, int X, int Y, int Z, float vs, const float *origin,
+                         const float *centres, const float *radii, int m, vedt_sphere_result *out,
+                         cudaStream_t s) {
+    if (m <= 0 || ng <= 0) return cudaSuccess;
+    Origin o{{origin[0], origin[1], origin[2]}};
+    const int n = m * ng;
+    k_query<<<(n + 127) / 128, 128, 0, s>>>(g, ng, X, Y, Z, vs, o, centres, radii, m, out);
+    return cudaGetLastError();
+}
+
+}  // namespace vedt

@@ -152,12 +152,16 @@ class CameraScene:
         d /= np.linalg.norm(d, axis=-1, keepdims=True)
         self.eye = eye
         self.dirs = d.reshape(-1, 3)
-        # static primitives
+        # static primitives: a room (floor, back and side walls just inside the grid)
         t = np.full(self.dirs.shape[0], np.inf)
         floor_z = lo[2] + 0.05
-        with np.errstate(divide="ignore", invalid="ignore"):
-            tf = (floor_z - eye[2]) / self.dirs[:, 2]
-        t = np.where((tf > 0) & np.isfinite(tf), np.minimum(t, tf), t)
+        for axis, val in ((2, floor_z), (1, lo[1] + ext[1] - 0.05), (0, lo[0] + 0.05),
+                          (0, lo[0] + ext[0] - 0.05)):
+            with np.errstate(divide="ignore", invalid="ignore"):
+                tp = (val - eye[axis]) / self.dirs[:, axis]
+            hit = eye[None, :] + np.where(np.isfinite(tp), tp, 0)[:, None] * self.dirs
+            inside = np.all((hit >= lo) & (hit <= lo + ext), axis=1)
+            t = np.where((tp > 0) & np.isfinite(tp) & inside, np.minimum(t, tp), t)
         for _ in range(n_boxes):
             c = lo + ext * rng.uniform(0.15, 0.85, 3)
             c[2] = floor_z + rng.uniform(0.05, 0.4)

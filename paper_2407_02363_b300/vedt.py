@@ -1,0 +1,300 @@
+"""Thin ctypes binding of libvedt.so (include/vedt.h).  Argument marshalling only:
+every step of the pipeline runs in the library's CUDA kernels.  Importing this module
+raises if the compiled library is missing; there is no CPU fallback.
+
+Device buffers are passed as torch CUDA tensors (via data_ptr) or raw integers; streams
+as torch.cuda.Stream objects or raw cudaStream_t integers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvedt.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libvedt.so not built at {LIB_PATH}; run `python -m paper_2407_02363_b300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+MAP_ENV, MAP_SELF, MAP_BOTH = 1, 2, 3
+SPHERE_OK, SPHERE_OUTSIDE, SPHERE_EMPTY = 0, 1, 2
+MAX_DIM, MAX_LINKS, MAX_JOINTS = 1024, 16, 15
+KERNELS = ("clear", "insert_links", "insert_points", "edt_x", "edt_y", "edt_z", "query")
+
+SPHERE_DTYPE = np.dtype([("sqdist", "<i4"), ("idx", "<i4"), ("dist", "<f4"),
+                         ("clearance", "<f4"), ("nearest", "<f4", (3,)), ("status", "<i4")])
+assert SPHERE_DTYPE.itemsize == 32
+
+
+class Chain(ctypes.Structure):
+    _fields_ = [("n_joints", ctypes.c_int32), ("base", ctypes.c_double * 12),
+                ("offset", (ctypes.c_double * 12) * MAX_JOINTS)]
+
+
+class VedtError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+_P, _I32, _I64, _F32, _U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_uint32
+_sig = {
+    "vedt_map_create": [_P, _F32, _P, _P, _P],
+    "vedt_map_destroy": [_P],
+    "vedt_map_set_stream": [_P, _P],
+    "vedt_map_info": [_P, _P, _P, _P],
+    "vedt_clear": [_P, _I32],
+    "vedt_insert_pointcloud": [_P, _P, _I64, _P, _I32, _P],
+    "vedt_register_links": [_P, _I32, _P, _P],
+    "vedt_insert_links": [_P, _P, _U32],
+    "vedt_fk": [_P, _P, _P],
+    "vedt_insert_robot": [_P, _P, _P, _U32],
+    "vedt_compute_edt": [_P, _I32],
+    "vedt_query_spheres": [_P, _P, _P, _I32, _I32, _P],
+    "vedt_query_spheres_dev": [_P, _P, _P, _I32, _I32, _P],
+    "vedt_get_field": [_P, _I32, _P, _P],
+    "vedt_get_occupancy": [_P, _I32, _P],
+    "vedt_check": [_P],
+    "vedt_set_timing": [_P, _I32],
+    "vedt_kernel_times": [_P, _P, _P],
+    "vedt_frame": [_P, _P, _I64, _P, _P, _P, _U32, _P, _P, _I32, _P],
+    "vedt_frame_host": [_P, _P, _I64, _P, _P, _P, _U32, _P, _P, _I32, _P],
+}
+for _n, _a in _sig.items():
+    _f = getattr(_lib, _n)
+    _f.argtypes = _a
+    _f.restype = ctypes.c_int
+_lib.vedt_status_string.argtypes = [ctypes.c_int]
+_lib.vedt_status_string.restype = ctypes.c_char_p
+_lib.vedt_version.restype = ctypes.c_char_p
+
+
+def status_string(s: int) -> str:
+    return _lib.vedt_status_string(int(s)).decode()
+
+
+def version() -> str:
+    return _lib.vedt_version().decode()
+
+
+def _chk(st, where):
+    if st != OK:
+        raise VedtError(st, where)
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def dev_ptr(x):
+    """Device address of a torch tensor (or an int)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def stream_handle(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def make_chain(chain) -> Chain:
+    """Packs a synth.Chain-like object (base 3x4, offsets n x 3x4) into vedt_chain."""
+    c = Chain()
+    c.n_joints = chain.n_joints
+    for i, v in enumerate(np.asarray(chain.base, dtype=np.float64).reshape(12)):
+        c.base[i] = float(v)
+    for k in range(chain.n_joints):
+        for i, v in enumerate(np.asarray(chain.offsets[k], dtype=np.float64).reshape(12)):
+            c.offset[k][i] = float(v)
+    return c
+
+
+def fk(chain, q) -> np.ndarray:
+    c = chain if isinstance(chain, Chain) else make_chain(chain)
+    qa = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros((c.n_joints + 1, 3, 4), dtype=np.float64)
+    _chk(_lib.vedt_fk(ctypes.byref(c), _np_ptr(qa), _np_ptr(out)), "vedt_fk")
+    return out
+
+
+class Map:
+    """Owns one vedt_map (environment M_I + self M_S grids and their distance fields)."""
+
+    def __init__(self, dims, voxel_size, origin=(0.0, 0.0, 0.0), stream=None):
+        d = np.ascontiguousarray(dims, dtype=np.int32)
+        o = np.ascontiguousarray(origin, dtype=np.float32)
+        h = ctypes.c_void_p()
+        _chk(_lib.vedt_map_create(_np_ptr(d), float(voxel_size), _np_ptr(o), stream_handle(stream),
+                                  ctypes.byref(h)), "vedt_map_create")
+        self._h = h
+        self.dims = tuple(int(v) for v in d)
+        self.voxel_size = float(np.float32(voxel_size))
+        self.origin = tuple(float(v) for v in o)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.vedt_map_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _chk(_lib.vedt_map_set_stream(self._h, stream_handle(stream)), "vedt_map_set_stream")
+
+    def clear(self, which=MAP_BOTH):
+        _chk(_lib.vedt_clear(self._h, which), "vedt_clear")
+
+    def insert_pointcloud(self, xyz_dev, n=None, T_world_sensor=None, filter_self=False, counts_dev=None):
+        n = int(xyz_dev.shape[0]) if n is None else int(n)
+        T = None
+        if T_world_sensor is not None:
+            T = np.ascontiguousarray(T_world_sensor, dtype=np.float32).reshape(12)
+        _chk(_lib.vedt_insert_pointcloud(self._h, dev_ptr(xyz_dev), n, None if T is None else _np_ptr(T),
+                                         1 if filter_self else 0, dev_ptr(counts_dev)),
+             "vedt_insert_pointcloud")
+
+    def register_links(self, link_points):
+        arrs = [np.ascontiguousarray(p, dtype=np.float32).reshape(-1, 3) for p in link_points]
+        ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+        nv = np.array([a.shape[0] for a in arrs], dtype=np.int64)
+        _chk(_lib.vedt_register_links(self._h, len(arrs), ptrs, _np_ptr(nv)), "vedt_register_links")
+        self._links = arrs
+
+    def insert_links(self, poses_f32, link_mask):
+        P = np.ascontiguousarray(poses_f32, dtype=np.float32).reshape(-1)
+        _chk(_lib.vedt_insert_links(self._h, _np_ptr(P), int(link_mask)), "vedt_insert_links")
+
+    def insert_robot(self, chain, q, link_mask):
+        c = chain if isinstance(chain, Chain) else make_chain(chain)
+        qa = np.ascontiguousarray(q, dtype=np.float64)
+        _chk(_lib.vedt_insert_robot(self._h, ctypes.byref(c), _np_ptr(qa), int(link_mask)), "vedt_insert_robot")
+
+    def compute_edt(self, which=MAP_BOTH):
+        _chk(_lib.vedt_compute_edt(self._h, which), "vedt_compute_edt")
+
+    def query_spheres(self, centres, radii, which=MAP_BOTH) -> np.ndarray:
+        c = np.ascontiguousarray(centres, dtype=np.float32).reshape(-1, 3)
+        r = np.ascontiguousarray(radii, dtype=np.float32).reshape(-1)
+        ng = 2 if which == MAP_BOTH else 1
+        out = np.zeros(c.shape[0] * ng, dtype=SPHERE_DTYPE)
+        _chk(_lib.vedt_query_spheres(self._h, _np_ptr(c), _np_ptr(r), c.shape[0], which, _np_ptr(out)),
+             "vedt_query_spheres")
+        return out
+
+    def query_spheres_dev(self, centres_dev, radii_dev, m, which, out_dev):
+        _chk(_lib.vedt_query_spheres_dev(self._h, dev_ptr(centres_dev), dev_ptr(radii_dev), int(m), which,
+                                         dev_ptr(out_dev)), "vedt_query_spheres_dev")
+
+    def frame(self, xyz_dev, n, chain, q, link_mask, centres_dev, radii_dev, m, out_dev, T_world_sensor=None):
+        """One control cycle on device buffers (vedt_frame), asynchronous."""
+        T = None if T_world_sensor is None else np.ascontiguousarray(T_world_sensor, np.float32).reshape(12)
+        qa = None if q is None else np.ascontiguousarray(q, dtype=np.float64)
+        _chk(_lib.vedt_frame(self._h, dev_ptr(xyz_dev), int(n), None if T is None else _np_ptr(T),
+                             None if chain is None else ctypes.byref(chain), None if qa is None else _np_ptr(qa),
+                             int(link_mask), dev_ptr(centres_dev), dev_ptr(radii_dev), int(m), dev_ptr(out_dev)),
+             "vedt_frame")
+
+    def frame_host(self, xyz_host, chain, q, link_mask, centres, radii, out=None, T_world_sensor=None):
+        """One control cycle from host buffers (vedt_frame_host); returns the 2m results."""
+        x = np.ascontiguousarray(xyz_host, dtype=np.float32).reshape(-1, 3) if not hasattr(xyz_host, "data_ptr") \
+            else xyz_host
+        n = int(x.shape[0])
+        xp = _np_ptr(x) if isinstance(x, np.ndarray) else x.data_ptr()
+        c = np.ascontiguousarray(centres, dtype=np.float32).reshape(-1, 3)
+        r = np.ascontiguousarray(radii, dtype=np.float32).reshape(-1)
+        if out is None:
+            out = np.zeros(2 * c.shape[0], dtype=SPHERE_DTYPE)
+        T = None if T_world_sensor is None else np.ascontiguousarray(T_world_sensor, np.float32).reshape(12)
+        qa = np.ascontiguousarray(q, dtype=np.float64)
+        _chk(_lib.vedt_frame_host(self._h, xp, n, None if T is None else _np_ptr(T),
+                                  None if chain is None else ctypes.byref(chain), _np_ptr(qa), int(link_mask),
+                                  _np_ptr(c), _np_ptr(r), c.shape[0], _np_ptr(out)), "vedt_frame_host")
+        return out
+
+    def field_ptrs(self, which):
+        sq, ix = ctypes.c_void_p(), ctypes.c_void_p()
+        _chk(_lib.vedt_get_field(self._h, which, ctypes.byref(sq), ctypes.byref(ix)), "vedt_get_field")
+        return sq.value, ix.value
+
+    def occupancy_ptr(self, which):
+        p = ctypes.c_void_p()
+        _chk(_lib.vedt_get_occupancy(self._h, which, ctypes.byref(p)), "vedt_get_occupancy")
+        return p.value
+
+    def check(self):
+        _chk(_lib.vedt_check(self._h), "vedt_check")
+
+    def set_timing(self, enable=True):
+        _chk(_lib.vedt_set_timing(self._h, 1 if enable else 0), "vedt_set_timing")
+
+    def kernel_times(self):
+        ms = np.zeros(len(KERNELS), dtype=np.float64)
+        cnt = np.zeros(len(KERNELS), dtype=np.int64)
+        _chk(_lib.vedt_kernel_times(self._h, _np_ptr(ms), _np_ptr(cnt)), "vedt_kernel_times")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNELS)}
+
+    # --- torch views of device buffers ---
+    def field_view(self, which):
+        """Borrowed zero-copy (sqdist, idx) torch views (Z, Y, X) of the selected field."""
+        X, Y, Z = self.dims
+        sq, ix = self.field_ptrs(which)
+        return device_view(sq, (Z, Y, X), "<i4"), device_view(ix, (Z, Y, X), "<i4")
+
+    def field(self, which):
+        """(sqdist, idx) as new torch int32 CUDA tensors of shape (Z, Y, X)."""
+        self.check()
+        sq, ix = self.field_view(which)
+        return sq.clone(), ix.clone()
+
+    def occupancy_view(self, which):
+        X, Y, Z = self.dims
+        return device_view(self.occupancy_ptr(which), (Z, Y, X), "|u1")
+
+    def occupancy(self, which):
+        self.check()
+        return self.occupancy_view(which).clone()
+
+    def upload_occupancy(self, which, occ):
+        """Copies a uint8 (Z, Y, X) array (numpy or torch) into the selected grid."""
+        import torch
+        self.check()
+        dst = self.occupancy_view(which)
+        src = torch.as_tensor(np.ascontiguousarray(occ, dtype=np.uint8)) if isinstance(occ, np.ndarray) else occ
+        dst.copy_(src.reshape(dst.shape))
+        torch.cuda.synchronize()
+
+
+class _CudaArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def device_view(ptr, shape, typestr):
+    """Zero-copy torch CUDA tensor over library-owned device memory (borrowed)."""
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
+
+
+def exported_symbols():
+    """Names declared in include/vedt.h that this library must export."""
+    return list(_sig) + ["vedt_status_string", "vedt_version"]

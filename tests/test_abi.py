@@ -1,0 +1,75 @@
+"""CPU-side checks of the C ABI: the library loads, exports every entry point that
+include/*.h declares, validates arguments on the host before touching the GPU, and its
+host forward kinematics agrees with the oracle's."""
+import glob
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2407_02363_b300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def v():
+    from paper_2407_02363_b300 import build
+    build.build()
+    from paper_2407_02363_b300 import vedt
+    return vedt
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(vedt_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(v):
+    declared = _declared()
+    assert "vedt_compute_edt" in declared and "vedt_query_spheres" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", v.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (vedt_[a-z0-9_]+)", out))
+    assert declared <= exported, sorted(declared - exported)
+
+
+def test_status_strings(v):
+    assert v.status_string(0) == "ok"
+    assert "invalid" in v.status_string(-1)
+    assert v.version().startswith("vedt")
+
+
+@pytest.mark.parametrize("dims,vs", [((0, 4, 4), 0.01), ((4, 4, 1025), 0.01), ((4, 4, 4), 0.0),
+                                     ((4, 4, 4), -1.0), ((4, 4, 4), float("nan"))])
+def test_map_create_rejects_bad_arguments(v, dims, vs):
+    with pytest.raises(v.VedtError) as e:
+        v.Map(dims, vs)
+    assert e.value.status == v.EINVAL
+
+
+def test_null_handle_calls_rejected(v):
+    import ctypes
+    L = v._lib
+    assert L.vedt_clear(None, 3) == v.EINVAL
+    assert L.vedt_compute_edt(None, 3) == v.EINVAL
+    assert L.vedt_insert_pointcloud(None, None, 10, None, 0, None) == v.EINVAL
+    assert L.vedt_query_spheres(None, None, None, 1, 3, None) == v.EINVAL
+    assert L.vedt_map_destroy(None) == v.OK
+    assert L.vedt_check(None) == v.EINVAL
+    assert L.vedt_fk(None, None, None) == v.EINVAL
+
+
+def test_fk_matches_oracle(v, oracle_mod):
+    chain = synth.make_chain(3, (1.28, 1.28, 1.28))
+    for q in synth.joint_states(4, 20):
+        P = v.fk(chain, q)
+        R = oracle_mod.fk(chain, q)
+        assert np.abs(P - R).max() < 1e-12
+        # same operation order on both sides: identical fp32 poses
+        assert np.array_equal(P.astype(np.float32), R.astype(np.float32))

@@ -1,0 +1,113 @@
+"""GPU parity of the exact EDT (Sec. III-C, Alg. 1) against the CPU oracle, through the
+C ABI: squared distances bit-exact everywhere, every nearest index valid (ties may pick
+another equally near voxel)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_02363_b300 import synth
+from gpu_helpers import INT32_MAX, check_idx_valid, lib
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu_edt(occ_env, occ_self=None, which=None):
+    v = lib()
+    Z, Y, X = occ_env.shape
+    m = v.Map((X, Y, Z), 0.01)
+    m.upload_occupancy(v.MAP_ENV, occ_env)
+    if occ_self is not None:
+        m.upload_occupancy(v.MAP_SELF, occ_self)
+    w = which if which is not None else (v.MAP_BOTH if occ_self is not None else v.MAP_ENV)
+    m.compute_edt(w)
+    m.check()
+    out = []
+    for g in (v.MAP_ENV, v.MAP_SELF):
+        if w & g:
+            sq, ix = m.field(g)
+            out.append((sq.cpu().numpy(), ix.cpu().numpy()))
+    m.close()
+    return out
+
+
+def assert_parity(occ, sq, ix):
+    osq, _ = oracle.edt(occ)
+    assert np.array_equal(sq, osq), f"{int((sq != osq).sum())} voxels differ"
+    check_idx_valid(occ, sq, ix)
+
+
+CASES = [
+    ((16, 16, 16), 0.001), ((16, 16, 16), 0.05), ((16, 16, 16), 0.5),
+    ((64, 64, 64), 0.02), ((37, 50, 29), 0.01), ((100, 3, 70), 0.02),
+    ((33, 65, 17), 0.3), ((200, 1, 1), 0.02), ((1, 300, 1), 0.02), ((1, 1, 256), 0.02),
+    ((256, 7, 9), 0.005), ((31, 256, 40), 0.001), ((96, 64, 255), 0.0005),
+    ((128, 128, 128), 0.0001),
+]
+
+
+@pytest.mark.parametrize("dims,density", CASES)
+def test_edt_small_mode(dims, density):
+    occ = synth.random_occupancy(hash(dims) % 1000, dims, density)
+    occ2 = synth.random_occupancy(hash(dims) % 1000 + 1, dims, density * 0.5)
+    (sq, ix), (sq2, ix2) = run_gpu_edt(occ, occ2)
+    assert_parity(occ, sq, ix)
+    assert_parity(occ2, sq2, ix2)
+
+
+LARGE = [((300, 40, 20), 0.01), ((260, 260, 8), 0.002), ((40, 20, 700), 0.003),
+         ((512, 64, 64), 0.001), ((70, 513, 33), 0.02), ((1024, 2, 3), 0.01)]
+
+
+@pytest.mark.parametrize("dims,density", LARGE)
+def test_edt_large_mode(dims, density):
+    occ = synth.random_occupancy(7 + sum(dims), dims, density)
+    (sq, ix), = run_gpu_edt(occ)
+    assert_parity(occ, sq, ix)
+
+
+@pytest.mark.parametrize("dims", [(16, 16, 16), (300, 20, 10)])
+def test_edt_empty_and_full(dims):
+    Z = dims[2]
+    empty = np.zeros((Z, dims[1], dims[0]), np.uint8)
+    full = np.ones_like(empty)
+    (sq, ix), (sq2, ix2) = run_gpu_edt(empty, full)
+    assert (sq == INT32_MAX).all() and (ix == -1).all()
+    assert (sq2 == 0).all() and np.array_equal(ix2.reshape(-1), np.arange(full.size))
+
+
+def test_edt_single_site_and_empty_slices():
+    dims = (64, 48, 40)
+    for site in [(0, 0, 0), (63, 47, 39), (31, 0, 20)]:
+        occ = synth.sites_occupancy(dims, [site])
+        (sq, ix), = run_gpu_edt(occ)
+        Z, Y, X = occ.shape
+        gz, gy, gx = np.meshgrid(np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+        expect = (gx - site[0]) ** 2 + (gy - site[1]) ** 2 + (gz - site[2]) ** 2
+        assert np.array_equal(sq, expect)
+        assert (ix == site[0] + X * (site[1] + Y * site[2])).all()
+
+
+def test_edt_max_int_range_corners():
+    """Opposite corners of a 256^3 grid: the largest squared distances of small mode."""
+    dims = (256, 256, 256)
+    occ = synth.sites_occupancy(dims, [(0, 0, 0)])
+    (sq, ix), = run_gpu_edt(occ)
+    assert sq[255, 255, 255] == 3 * 255 * 255
+    assert_parity(occ, sq, ix)
+
+
+def test_edt_full_size_256_and_512():
+    for dims, dens in (((256, 256, 256), 0.02), ((512, 512, 512), 0.003)):
+        occ = synth.random_occupancy(5, dims, dens)
+        (sq, ix), = run_gpu_edt(occ)
+        assert_parity(occ, sq, ix)
+        del occ, sq, ix
+
+
+def test_edt_repeat_is_deterministic_and_independent_of_other_grid():
+    dims = (96, 80, 72)
+    occ = synth.random_occupancy(11, dims, 0.01)
+    other = synth.random_occupancy(12, dims, 0.2)
+    (a, ai), = run_gpu_edt(occ, which=None)
+    (b, bi), (_, _) = run_gpu_edt(occ, other)
+    assert np.array_equal(a, b) and np.array_equal(ai, bi)

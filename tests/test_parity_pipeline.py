@@ -1,0 +1,152 @@
+"""GPU parity of the whole per-frame pipeline (Alg. 2 lines 4-10) against the oracle:
+occupancy after ClearMap + Insert(O_Lk) + Insert(Point_Cloud) byte-equal, EDT of both
+maps bit-exact in squared distance, sphere results (Eq. (dist)) bit-equal."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2407_02363_b300 import synth
+from gpu_helpers import check_idx_valid, lib, spheres_bitequal
+
+pytestmark = pytest.mark.gpu
+
+SELF_MASK = 0b111   # static body + links 1-2 form the self-collision obstacle O_L
+
+
+def robot_points(link_models, poses, mask, n, seed):
+    """Cloud points lying on the robot (to exercise the robot-point removal)."""
+    rng = np.random.default_rng(seed)
+    pts = []
+    for k, P in enumerate(poses):
+        if not (mask >> k) & 1 or len(link_models[k]) == 0:
+            continue
+        sel = link_models[k][rng.integers(0, len(link_models[k]), n)].astype(np.float64)
+        pts.append(sel @ P[:, :3].T.astype(np.float64) + P[:, 3])
+    return np.concatenate(pts).astype(np.float32)
+
+
+def run_frame(grid, chain, q, cloud, T=None, use_library_fk=False):
+    v = lib()
+    links = synth.link_models(chain, grid.voxel_size)
+    spheres = synth.sphere_model(chain)
+    poses = oracle.fk(chain, q).astype(np.float32)
+    m = v.Map(grid.dims, grid.voxel_size, grid.origin)
+    m.register_links(links)
+    m.clear(v.MAP_BOTH)
+    if use_library_fk:
+        m.insert_robot(chain, q, SELF_MASK)
+    else:
+        m.insert_links(poses, SELF_MASK)
+    cl = torch.from_numpy(cloud).cuda()
+    counts = torch.zeros(3, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    m.insert_pointcloud(cl, T_world_sensor=T, filter_self=True, counts_dev=counts)
+    occ_env = m.occupancy(v.MAP_ENV).cpu().numpy()
+    occ_self = m.occupancy(v.MAP_SELF).cpu().numpy()
+    m.compute_edt(v.MAP_BOTH)
+    fields = [tuple(t.cpu().numpy() for t in m.field(g)) for g in (v.MAP_ENV, v.MAP_SELF)]
+    centres = oracle.sphere_centres(chain, spheres, q)
+    res = m.query_spheres(centres, spheres.radius, v.MAP_BOTH)
+    m.close()
+    # oracle
+    X, Y, Z = grid.dims
+    o_self = np.zeros((Z, Y, X), np.uint8)
+    oracle.insert_links(o_self, grid.dims, grid.voxel_size, grid.origin, links, poses, SELF_MASK)
+    o_env = np.zeros((Z, Y, X), np.uint8)
+    n_written = oracle.insert_points(o_env, o_self, grid.dims, grid.voxel_size, grid.origin, cloud, T=T,
+                                     filter_self=True)
+    return dict(occ_env=occ_env, occ_self=occ_self, o_env=o_env, o_self=o_self, fields=fields,
+                res=res, centres=centres, radii=spheres.radius, counts=counts.cpu().numpy(),
+                n_written=n_written, n_points=len(cloud))
+
+
+def check_frame(grid, r):
+    assert np.array_equal(r["occ_self"], r["o_self"])
+    assert np.array_equal(r["occ_env"], r["o_env"])
+    assert r["counts"][0] == r["n_written"] and r["counts"].sum() == r["n_points"]
+    m = len(r["radii"])
+    for g, occ in enumerate((r["o_env"], r["o_self"])):
+        sq, ix = r["fields"][g]
+        osq, oix = oracle.edt(occ)
+        assert np.array_equal(sq, osq)
+        check_idx_valid(occ, sq, ix)
+        # the query reads the oracle's own field so ties in idx cannot matter
+        expect = oracle.query_spheres(osq, ix, grid.dims, grid.voxel_size, grid.origin, r["centres"], r["radii"])
+        got = r["res"][g * m:(g + 1) * m].copy()
+        exp = np.zeros(m, dtype=got.dtype)
+        for name in exp.dtype.names:
+            exp[name] = expect[name]
+        assert spheres_bitequal(got, exp)
+        # and against the oracle's own idx, everything but idx/nearest must agree too
+        e2 = oracle.query_spheres(osq, oix, grid.dims, grid.voxel_size, grid.origin, r["centres"], r["radii"])
+        for name in ("sqdist", "status"):
+            assert np.array_equal(got[name], e2[name])
+        assert np.array_equal(got["dist"].view(np.uint32), e2["dist"].view(np.uint32))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_config1_frame(seed):
+    """64^3 at 2 cm: 20k surface points + robot points, 7-DoF capsule chain, 24 spheres."""
+    grid = synth.GridSpec((64, 64, 64), 0.02)
+    chain = synth.make_chain(1234 + 1000 + seed, (0.64, 0.64, 0.64))
+    q = synth.joint_states(1234 + 1000 + seed, 1)[0]
+    cloud = synth.surface_cloud(1234 + 1000 + seed, grid, 20_000)
+    poses = oracle.fk(chain, q).astype(np.float32)
+    extra = robot_points(synth.link_models(chain, grid.voxel_size), poses, SELF_MASK, 500, seed)
+    cloud = np.concatenate([cloud, extra, np.array([[np.nan, 0, 0], [9, 9, 9]], np.float32)])
+    r = run_frame(grid, chain, q, cloud)
+    assert r["counts"][2] > 0            # some robot points were removed
+    check_frame(grid, r)
+
+
+def test_config1_library_fk_and_sensor_pose():
+    grid = synth.GridSpec((64, 64, 64), 0.02, origin=(-0.64, -0.64, 0.0))
+    chain = synth.make_chain(77, (0.0, 0.0, 0.64))
+    q = synth.joint_states(78, 1)[0]
+    cloud = synth.surface_cloud(79, synth.GridSpec((64, 64, 64), 0.02), 20_000)
+    T = np.array([[0, -1, 0, 0.3], [1, 0, 0, -0.9], [0, 0, 1, 0.01]], dtype=np.float32)
+    r = run_frame(grid, chain, q, cloud, T=T, use_library_fk=True)
+    check_frame(grid, r)
+
+
+def test_config2_frame_full_size():
+    """256^3 at 1 cm: 300k-point depth-camera cloud with the moving sphere obstacle."""
+    grid = synth.GridSpec((256, 256, 256), 0.01)
+    scene = synth.CameraScene(1234 + 2000, grid)
+    chain = synth.make_chain(1234 + 2000, (1.28, 1.28, 1.28))
+    q = synth.joint_trajectory(1234 + 2000, 40)[37]
+    cloud = scene.frame(37)
+    r = run_frame(grid, chain, q, cloud)
+    assert r["occ_env"].mean() > 0.001
+    check_frame(grid, r)
+
+
+def test_empty_cloud_and_all_outside():
+    v = lib()
+    grid = synth.GridSpec((32, 32, 32), 0.05)
+    m = v.Map(grid.dims, grid.voxel_size)
+    m.clear(v.MAP_BOTH)
+    m.insert_pointcloud(torch.zeros((0, 3), device="cuda"), n=0)
+    far = torch.full((100, 3), 50.0, device="cuda")
+    counts = torch.zeros(3, dtype=torch.int64, device="cuda")
+    m.insert_pointcloud(far, counts_dev=counts)
+    m.compute_edt(v.MAP_BOTH)
+    res = m.query_spheres(np.array([[0.5, 0.5, 0.5], [5, 5, 5]], np.float32), np.array([0.05, 0.05], np.float32))
+    assert counts.cpu().tolist() == [0, 100, 0]
+    assert res["status"].tolist() == [v.SPHERE_EMPTY, v.SPHERE_OUTSIDE] * 2
+    assert np.isinf(res["dist"][0]) and np.isnan(res["dist"][1])
+    m.close()
+
+
+def test_timing_api_counts_launches():
+    v = lib()
+    m = v.Map((64, 64, 64), 0.02)
+    m.set_timing(True)
+    for _ in range(3):
+        m.clear(v.MAP_BOTH)
+        m.compute_edt(v.MAP_BOTH)
+    t = m.kernel_times()
+    assert t["edt_x"][1] == 3 and t["edt_y"][1] == 3 and t["edt_z"][1] == 3 and t["clear"][1] == 6
+    assert all(ms >= 0 for ms, _ in t.values())
+    m.close()
