@@ -356,6 +356,37 @@ def run_vedt(args):
            "frac_of_peak": 9 * 2 * N / (edt_ms * 1e-3) / 1e9 / peak}
 
     # ---- end to end through the public API from host buffers ----
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = run_e2e(args, v, m, W, n_frames, cchain, world, dev)
+    m.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(W, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "voxel_size_m": VOXEL, "points": N_POINTS,
+                       "maps_per_step": 2, "distinct_frames": n_frames, "parallelism": f"replicas x{world}",
+                       "l2": "no flush: each step writes 268 MB of fields plus ~134 MB of scratch, > 126 MB L2"},
+            "latency_ms": {"p50": frame_ms[len(frame_ms) // 2], "p99": frame_ms[min(len(frame_ms) - 1,
+                                                                                     int(0.99 * len(frame_ms)))],
+                           "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
+            "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": int(sum(k["launches"] for k in kernels.values())), "clocks": clk,
+        }
+        print(json.dumps(line))
+
+
+def run_e2e(args, v, m, W, n_frames, cchain, world, dev):
+    import torch
+    chain, spheres = W["chain"], W["spheres"]
+    N = W["grid"].n_voxels
+    m_sph = len(spheres.radius)
     pinned = [torch.from_numpy(c).pin_memory() for c in W["clouds"]]
     cen_host = [sphere_centres_lib(v, chain, spheres, q) for q in W["traj"]]
     res = np.zeros(2 * m_sph, dtype=v.SPHERE_DTYPE)
@@ -374,29 +405,7 @@ def run_vedt(args):
            "h2d_bytes_per_step": N_POINTS * 12 + m_sph * 16, "d2h_bytes_per_step": 2 * m_sph * 32,
            "steps": args.e2e_steps, "ms_per_step": e2e_s / args.e2e_steps * 1e3,
            "api": "vedt_frame_host (pinned host cloud in, sphere results out)"}
-    m.close()
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(W, args.cpu_seconds)
-
-    if rank == 0:
-        occ = float(np.mean([0.0]))
-        line = {
-            "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dims": list(DIMS), "voxel_size_m": VOXEL, "points": N_POINTS,
-                       "maps_per_step": 2, "distinct_frames": n_frames, "parallelism": f"replicas x{world}",
-                       "l2": "no flush: each step writes 268 MB of fields plus ~134 MB of scratch, > 126 MB L2"},
-            "latency_ms": {"p50": frame_ms[len(frame_ms) // 2], "p99": frame_ms[min(len(frame_ms) - 1,
-                                                                                     int(0.99 * len(frame_ms)))],
-                           "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
-            "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
-            "gpu_launches": int(sum(k["launches"] for k in kernels.values())), "clocks": clk,
-        }
-        del occ
-        print(json.dumps(line))
+    return e2e
 
 
 def main():

@@ -85,8 +85,8 @@ typedef struct {
 
 /* Creates M_I (environment) and M_S (self) grids of dims[3] = {X, Y, Z} voxels with
  * edge voxel_size > 0 and world min corner origin[3], plus both distance fields and
- * the EDT scratch; all device memory is allocated here (about 13*X*Y*Z bytes per grid
- * for dims <= 256, 19*X*Y*Z above).  `stream` is a cudaStream_t (NULL = legacy default
+ * the EDT scratch; all device memory is allocated here (about 12*X*Y*Z bytes per grid
+ * for dims <= 256, 15*X*Y*Z above).  `stream` is a cudaStream_t (NULL = legacy default
  * stream).  Grids start cleared.  *out receives the handle.  Errors: EINVAL, ENOMEM,
  * ECUDA. */
 vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float origin[3],

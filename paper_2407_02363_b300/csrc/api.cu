@@ -34,7 +34,8 @@ struct vedt_map {
     uint8_t *occ[2] = {nullptr, nullptr};
     int32_t *sq[2] = {nullptr, nullptr};
     int32_t *ix[2] = {nullptr, nullptr};
-    uint16_t *xs[2] = {nullptr, nullptr};
+    void *xs[2] = {nullptr, nullptr};
+    uint8_t *row_has[2] = {nullptr, nullptr};
     void *s2[2] = {nullptr, nullptr};
     uint8_t *slice_has[2] = {nullptr, nullptr};
     int32_t *err = nullptr;
@@ -141,29 +142,30 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
     std::vector<CUtensorMap> tm(2 * grids.size());
     int64_t rows = 0, ty = 0, tz = 0;
     t.large = 0;
-    t.maxY = t.maxZ = 0;
+    t.maxY = t.maxZ = t.maxXp = 0;
     for (size_t i = 0; i < d.size(); ++i) {
         GridDesc &g = d[i];
         g.row_begin = rows;
         g.ty_begin = ty;
         g.tz_begin = tz;
         rows += static_cast<int64_t>(g.Y) * g.Z;
-        ty += static_cast<int64_t>(g.Xp / kTile) * g.Z;
-        tz += static_cast<int64_t>(g.Xp / kTile) * g.Y;
+        ty += static_cast<int64_t>(g.Xp / kEnvCols) * g.Z;
+        tz += static_cast<int64_t>(g.Xp / kEnvCols) * g.Y;
         const bool large = g.X > kSmallMax || g.Y > kSmallMax || g.Z > kSmallMax;
         t.large |= large;
         t.maxY = g.Y > t.maxY ? g.Y : t.maxY;
         t.maxZ = g.Z > t.maxZ ? g.Z : t.maxZ;
+        t.maxXp = g.Xp > t.maxXp ? g.Xp : t.maxXp;
     }
     for (size_t i = 0; i < d.size(); ++i) {
         GridDesc &g = d[i];
         const uint32_t by = g.Y > kBox ? kBox : g.Y, bz = g.Z > kBox ? kBox : g.Z;
-        if (encode_tmap(&tm[2 * i], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, g.xs, g.Xp, g.Y, g.Z, kTile, by, 1) !=
-            CUDA_SUCCESS)
-            return VEDT_ECUDA;
         const bool big = t.large != 0;
+        if (encode_tmap(&tm[2 * i], big ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                        big ? 2 : 1, g.xs, g.Xp, g.Y, g.Z, kEnvCols, by, 1) != CUDA_SUCCESS)
+            return VEDT_ECUDA;
         if (encode_tmap(&tm[2 * i + 1], big ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
-                        big ? 4 : 2, g.s2, g.Xp, g.Y, g.Z, kTile, 1, bz) != CUDA_SUCCESS)
+                        big ? 4 : 2, g.s2, g.Xp, g.Y, g.Z, kEnvCols, 1, bz) != CUDA_SUCCESS)
             return VEDT_ECUDA;
     }
     VCHECK(cudaMemcpy(dev_desc, d.data(), sizeof(GridDesc) * d.size(), cudaMemcpyHostToDevice));
@@ -188,6 +190,7 @@ void free_map(vedt_map *m) {
         cudaFree(m->sq[i]);
         cudaFree(m->ix[i]);
         cudaFree(m->xs[i]);
+        cudaFree(m->row_has[i]);
         cudaFree(m->s2[i]);
         cudaFree(m->slice_has[i]);
     }
@@ -211,6 +214,7 @@ GridDesc grid_of(const vedt_map *m, int i) {
     GridDesc g{};
     g.occ = m->occ[i];
     g.xs = m->xs[i];
+    g.row_has = m->row_has[i];
     g.s2 = m->s2[i];
     g.slice_has = m->slice_has[i];
     g.sqdist = m->sq[i];
@@ -266,7 +270,8 @@ vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float
         if (e == cudaSuccess) e = cudaMalloc(&m->occ[i], m->N);
         if (e == cudaSuccess) e = cudaMalloc(&m->sq[i], m->N * 4);
         if (e == cudaSuccess) e = cudaMalloc(&m->ix[i], m->N * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&m->xs[i], Np * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&m->xs[i], Np * (m->large ? 2 : 1));
+        if (e == cudaSuccess) e = cudaMalloc(&m->row_has[i], static_cast<int64_t>(m->Y) * m->Z);
         if (e == cudaSuccess) e = cudaMalloc(&m->s2[i], Np * s2b);
         if (e == cudaSuccess) e = cudaMalloc(&m->slice_has[i], m->Z);
     }

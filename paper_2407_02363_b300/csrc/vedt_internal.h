@@ -8,7 +8,8 @@
 
 namespace vedt {
 
-constexpr int kTile = 32;            // columns per EDT tile (one warp, one lane per column)
+constexpr int kTile = 32;            // lanes per warp
+constexpr int kEnvCols = 32;         // columns per pass-Y/Z tile (two warps: lower / upper half)
 constexpr int kBox = 256;            // max TMA box extent along one dimension
 constexpr uint16_t kNoX = 0xFFFF;    // pass-X "row has no site"
 constexpr int kSmallMax = 256;       // all dims <= 256: 16-bit packed 2-D sites, 8-bit links
@@ -21,7 +22,9 @@ constexpr int kErrBounds = 2;
 // every tile is whole and every TMA row stride is a multiple of 16 bytes.
 struct GridDesc {
     const uint8_t *occ;     // [Z][Y][X] occupancy
-    uint16_t *xs;           // [Z][Y][Xp] pass-X nearest site x (kNoX if the row is empty)
+    void *xs;               // [Z][Y][Xp] pass-X nearest site x: small uint8 (valid iff
+                            // row_has), large uint16 (kNoX if the row is empty)
+    uint8_t *row_has;       // [Z][Y] small mode: 1 iff row (y, z) has an occupied voxel
     void *s2;               // [Z][Y][Xp] pass-Y 2-D site: small x | y << 8, large x | y << 16
     uint8_t *slice_has;     // [Z] 1 iff slice z has an occupied voxel
     int32_t *sqdist;        // [Z][Y][X]
@@ -30,7 +33,6 @@ struct GridDesc {
     int64_t row_begin;      // prefix over rows (Y*Z) of the grids before this one
     int64_t ty_begin;       // prefix over pass-Y tiles ((Xp/32)*Z)
     int64_t tz_begin;       // prefix over pass-Z tiles ((Xp/32)*Y)
-    int32_t pad[2];
 };
 
 struct GridTable {
@@ -38,7 +40,7 @@ struct GridTable {
     CUtensorMap *tmaps;          // device array [2n]: {xs box (32, by, 1), s2 box (32, 1, bz)}
     int n;
     int large;                   // 0: every grid has dims <= 256
-    int maxY, maxZ;
+    int maxY, maxZ, maxXp;
     int64_t rows, tiles_y, tiles_z;
     int32_t *err;                // device error word
 };
