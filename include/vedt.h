@@ -203,6 +203,25 @@ enum { VEDT_K_CLEAR = 0, VEDT_K_INSERT_LINKS, VEDT_K_INSERT_POINTS, VEDT_K_EDT_X
 vedt_status vedt_set_timing(vedt_map *map, int enable);
 vedt_status vedt_kernel_times(vedt_map *map, double *ms_out, int64_t *count_out);
 
+/* ---- EDT without device allocation -------------------------------------------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers that must not allocate
+ * device memory once running: a hard real-time control loop (cudaMalloc may synchronise
+ * the device and has no latency bound) or a process whose device memory is already
+ * reserved by another allocator.  It computes the same exact EDT as vedt_compute_edt for
+ * one grid: occ_dev (X*Y*Z uint8, layout as above) in, sqdist_dev and idx_dev (X*Y*Z
+ * int32 each) out, all caller-owned device memory, asynchronously on `stream`
+ * (cudaStream_t, NULL = legacy default stream).  Scratch comes from one fixed array of
+ * about 6.4 MB that the library keeps in every GPU's memory until the process exits: each
+ * dimension must be <= 256 and ceil(X/32)*32*Y*Z <= 2^21 (a 128^3 grid fits), otherwise
+ * the call returns VEDT_ENOTSUP without doing anything.  The first call on a device looks
+ * the array up (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Calls share the array and leave their scratch in it; calls that may overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the caller.
+ * Errors: EINVAL (null pointer, dims < 1), ENOTSUP (grid larger than the scratch), ECUDA. */
+vedt_status vedt_edt_noalloc(const uint8_t *occ_dev, int32_t X, int32_t Y, int32_t Z,
+                             int32_t *sqdist_dev, int32_t *idx_dev, void *stream);
+
 /* Human-readable text for a status code (static storage). */
 const char *vedt_status_string(vedt_status s);
 

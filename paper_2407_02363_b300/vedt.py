@@ -64,6 +64,7 @@ _sig = {
     "vedt_kernel_times": [_P, _P, _P],
     "vedt_frame": [_P, _P, _I64, _P, _P, _P, _U32, _P, _P, _I32, _P],
     "vedt_frame_host": [_P, _P, _I64, _P, _P, _P, _U32, _P, _P, _I32, _P],
+    "vedt_edt_noalloc": [_P, _I32, _I32, _I32, _P, _P, _P],
 }
 for _n, _a in _sig.items():
     _f = getattr(_lib, _n)
@@ -106,6 +107,14 @@ def stream_handle(s):
     if isinstance(s, int):
         return s
     return s.cuda_stream
+
+
+def edt_noalloc(occ_dev, dims, sqdist_dev, idx_dev, stream=None):
+    """Exact EDT of one grid into caller-provided device buffers using the library's
+    fixed static scratch (no device allocation; see vedt_edt_noalloc in include/vedt.h)."""
+    X, Y, Z = (int(v) for v in dims)
+    _chk(_lib.vedt_edt_noalloc(dev_ptr(occ_dev), X, Y, Z, dev_ptr(sqdist_dev), dev_ptr(idx_dev),
+                               stream_handle(stream)), "vedt_edt_noalloc")
 
 
 def make_chain(chain) -> Chain:
