@@ -182,6 +182,58 @@ vedt_status vedt_frame_host(vedt_map *map, const float *xyz_host, int64_t n_poin
                             uint32_t link_mask, const float *centres_host, const float *radii_host,
                             int m, vedt_sphere_result *out_host);
 
+/* ---- batches of maps ---------------------------------------------------------------------- */
+
+/* A batch runs the per-frame pipeline of Alg. 2 (lines 4-10) for many independent maps of
+ * uneven extents at once: each step is one launch over all maps, and the EDT of every
+ * grid in the batch is one persistent launch whose work items (rows for the row sweep,
+ * 32-column tiles for the two envelope sweeps) are handed out in order, each envelope
+ * tile waiting (bounded) only for its own grid's previous sweep.  Maps with a dimension
+ * > 256 form a second persistent launch.  The batch references (does not own) its maps;
+ * they must outlive it.  All batch calls are ordered on the batch's stream. */
+typedef struct vedt_batch vedt_batch;
+
+vedt_status vedt_batch_create(vedt_map *const *maps, int n_maps, void *stream, vedt_batch **out);
+vedt_status vedt_batch_destroy(vedt_batch *batch);
+
+/* Launch-shape knobs explored by the autotuner: ctas_per_sm (0 = occupancy maximum) and
+ * rows_per_item (pass-X rows per work item) of the persistent EDT, or persistent = 0 for
+ * three plain launches (one per sweep) over all grids.  Results never depend on them.
+ * Drops a recorded graph. */
+vedt_status vedt_batch_set_tuning(vedt_batch *batch, int ctas_per_sm, int rows_per_item, int persistent);
+
+/* PBA_EDT (Alg. 2 line 9) of both grids of every map in the batch. */
+vedt_status vedt_batch_compute_edt(vedt_batch *batch);
+
+/* Offline link models shared by every map of the batch (same robot, own joint states);
+ * as vedt_register_links. */
+vedt_status vedt_batch_register_links(vedt_batch *batch, int n_links, const float *const *link_xyz_host,
+                                      const int64_t *n_vox);
+
+/* Inputs of the next frame.  xyz_dev: world-frame fp32 points of all maps, map i owning
+ * points [offsets_host[i], offsets_host[i+1]) (offsets_host[0] = 0, n_maps + 1 entries).
+ * poses_host: n_maps x n_links x 12 fp32 link poses.  centres_dev: n_maps x m x 3 fp32
+ * sphere centres, radii_dev: m fp32 radii, out_dev: n_maps x 2 x m results (per map the
+ * environment block, then the self block).  Device pointers are kept, not copied; poses
+ * and offsets are copied to the device before the call returns.  Once a graph is recorded
+ * the device pointers, m, link_mask must stay the same and no map may exceed the point
+ * count it had at recording (EINVAL otherwise). */
+vedt_status vedt_batch_set_frame(vedt_batch *batch, const float *xyz_dev, const int64_t *offsets_host,
+                                 const float *poses_host, uint32_t link_mask, const float *centres_dev,
+                                 const float *radii_dev, int m, vedt_sphere_result *out_dev);
+
+/* One frame for every map: clear both grids, insert links (link_mask) into M_S, insert
+ * the points into M_I with robot-point removal, EDT of all grids, sphere query. */
+vedt_status vedt_batch_run(vedt_batch *batch);
+
+/* Records vedt_batch_run as a CUDA graph (needs a non-default stream); vedt_batch_replay
+ * launches it, reading the frame inputs current at replay time. */
+vedt_status vedt_batch_capture(vedt_batch *batch);
+vedt_status vedt_batch_replay(vedt_batch *batch);
+
+/* Synchronises the batch's stream; ETIMEOUT if an in-kernel wait expired. */
+vedt_status vedt_batch_check(vedt_batch *batch);
+
 /* ---- access ---------------------------------------------------------------------------- */
 
 /* Borrowed device pointers to the selected map's fields (which = ENV or SELF), valid

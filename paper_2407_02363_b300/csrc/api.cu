@@ -14,55 +14,6 @@ using namespace vedt;
 
 namespace {
 
-constexpr int kMaxQuery = 4096;
-
-struct EvPair {
-    int kind;
-    cudaEvent_t a, b;
-};
-
-}  // namespace
-
-struct vedt_map {
-    int32_t X = 0, Y = 0, Z = 0, Xp = 0;
-    float vs = 0.f;
-    float origin[3] = {0, 0, 0};
-    cudaStream_t stream = nullptr;
-    int large = 0;
-    int64_t N = 0;
-    // [0] = environment M_I, [1] = self M_S
-    uint8_t *occ[2] = {nullptr, nullptr};
-    int32_t *sq[2] = {nullptr, nullptr};
-    int32_t *ix[2] = {nullptr, nullptr};
-    void *xs[2] = {nullptr, nullptr};
-    uint8_t *row_has[2] = {nullptr, nullptr};
-    void *s2[2] = {nullptr, nullptr};
-    uint8_t *slice_has[2] = {nullptr, nullptr};
-    int32_t *err = nullptr;
-    // EDT launch tables for which = ENV (0), SELF (1), BOTH (2)
-    GridTable tab[3];
-    void *tab_mem = nullptr;
-    // query scratch
-    QueryGrid *qgrids = nullptr;   // device [3]: env, self, env+self ... see below
-    float *q_in = nullptr;         // device centres (3*kMaxQuery) + radii (kMaxQuery)
-    vedt_sphere_result *q_out = nullptr;
-    // links
-    float *link_pts = nullptr;
-    uint8_t *link_of = nullptr;
-    float *stage = nullptr;        // device staging for host point clouds
-    int64_t stage_cap = 0;         // points
-    int64_t n_link_pts = 0;
-    int n_links = 0;
-    // timing
-    bool timing = false;
-    std::vector<EvPair> pending;
-    std::vector<cudaEvent_t> free_events;
-    double ms[VEDT_NUM_KERNELS] = {};
-    int64_t cnt[VEDT_NUM_KERNELS] = {};
-};
-
-namespace {
-
 vedt_status from_cuda(cudaError_t e) { return e == cudaSuccess ? VEDT_OK : (e == cudaErrorMemoryAllocation ? VEDT_ENOMEM : VEDT_ECUDA); }
 
 #define VCHECK(call)                                  \

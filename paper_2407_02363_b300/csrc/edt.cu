@@ -38,83 +38,86 @@ namespace vedt {
 // pass X
 // ------------------------------------------------------------------------------------
 template <int S, bool SMALL>
-__global__ void __launch_bounds__(256) k_pass_x(const GridDesc *__restrict__ gd, int ng, int64_t rows_total) {
+__device__ __forceinline__ void pass_x_row(const GridDesc &G, int64_t lr, int lane) {
     constexpr int kNoLeft = -4096, kNoRight = 8192;
+    const int x0 = S * lane;
+    const int X = G.X, Xp = G.Xp;
+    const uint8_t *row = G.occ + lr * X;
+    uint32_t m = 0;
+    if ((X & 3) == 0 && x0 + S <= X) {
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(row + x0);
+#pragma unroll
+        for (int q = 0; q < S / 4; ++q) {
+            const uint32_t nz = __vcmpne4(__ldg(w + q), 0u) & 0x08040201u;
+            m |= ((nz * 0x01010101u) >> 24) << (4 * q);
+        }
+    } else {
+        for (int i = 0; i < S; ++i) {
+            const int x = x0 + i;
+            if (x < X && row[x]) m |= 1u << i;
+        }
+    }
+    int lastp = m ? x0 + 31 - __clz(m) : kNoLeft;
+    int firstp = m ? x0 + __ffs(m) - 1 : kNoRight;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, lastp, d);
+        const int u = __shfl_down_sync(0xffffffffu, firstp, d);
+        if (lane >= d) lastp = max(lastp, t);
+        if (lane + d < 32) firstp = min(firstp, u);
+    }
+    const bool any = __shfl_sync(0xffffffffu, lastp, 31) >= 0;
+    int L = __shfl_up_sync(0xffffffffu, lastp, 1);
+    int R = __shfl_down_sync(0xffffffffu, firstp, 1);
+    if (lane == 0) L = kNoLeft;
+    if (lane == 31) R = kNoRight;
+    int left[S], best[S];
+    int cur = L;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        if ((m >> i) & 1u) cur = x0 + i;
+        left[i] = cur;
+    }
+    cur = R;
+#pragma unroll
+    for (int i = S - 1; i >= 0; --i) {
+        if ((m >> i) & 1u) cur = x0 + i;
+        const int x = x0 + i;
+        best[i] = (x - left[i] <= cur - x) ? left[i] : cur;
+    }
+    if (x0 < Xp) {
+        if (SMALL) {
+            uint32_t wv[S / 4];
+#pragma unroll
+            for (int q = 0; q < S / 4; ++q)
+                wv[q] = (best[4 * q] & 0xFF) | ((best[4 * q + 1] & 0xFF) << 8) | ((best[4 * q + 2] & 0xFF) << 16) |
+                        (static_cast<uint32_t>(best[4 * q + 3]) << 24);
+            uint32_t *o = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(G.xs) + lr * Xp + x0);
+#pragma unroll
+            for (int q = 0; q < S / 4; q += 2) *reinterpret_cast<uint2 *>(o + q) = make_uint2(wv[q], wv[q + 1]);
+            if (lane == 0) G.row_has[lr] = any ? 1 : 0;
+        } else {
+            uint32_t wv[S / 2];
+#pragma unroll
+            for (int q = 0; q < S / 2; ++q)
+                wv[q] = any ? ((best[2 * q] & 0xFFFF) | (static_cast<uint32_t>(best[2 * q + 1]) << 16)) : 0xFFFFFFFFu;
+            uint32_t *o = reinterpret_cast<uint32_t *>(static_cast<uint16_t *>(G.xs) + lr * Xp + x0);
+#pragma unroll
+            for (int q = 0; q < S / 2; q += 4)
+                *reinterpret_cast<uint4 *>(o + q) = make_uint4(wv[q], wv[q + 1], wv[q + 2], wv[q + 3]);
+        }
+    }
+}
+
+template <int S, bool SMALL>
+__global__ void __launch_bounds__(256) k_pass_x(const GridDesc *__restrict__ gd, int ng, int64_t rows_total) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    const int x0 = S * lane;
     int g = 0;
     for (int64_t r = warp; r < rows_total; r += nwarps) {
         while (g + 1 < ng && gd[g + 1].row_begin <= r) ++g;
-        const int X = gd[g].X, Xp = gd[g].Xp;
-        const int64_t lr = r - gd[g].row_begin;
-        const uint8_t *row = gd[g].occ + lr * X;
-        uint32_t m = 0;
-        if ((X & 3) == 0 && x0 + S <= X) {
-            const uint32_t *w = reinterpret_cast<const uint32_t *>(row + x0);
-#pragma unroll
-            for (int q = 0; q < S / 4; ++q) {
-                const uint32_t nz = __vcmpne4(__ldg(w + q), 0u) & 0x08040201u;
-                m |= ((nz * 0x01010101u) >> 24) << (4 * q);
-            }
-        } else {
-            for (int i = 0; i < S; ++i) {
-                const int x = x0 + i;
-                if (x < X && row[x]) m |= 1u << i;
-            }
-        }
-        int lastp = m ? x0 + 31 - __clz(m) : kNoLeft;
-        int firstp = m ? x0 + __ffs(m) - 1 : kNoRight;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, lastp, d);
-            const int u = __shfl_down_sync(0xffffffffu, firstp, d);
-            if (lane >= d) lastp = max(lastp, t);
-            if (lane + d < 32) firstp = min(firstp, u);
-        }
-        const bool any = __shfl_sync(0xffffffffu, lastp, 31) >= 0;
-        int L = __shfl_up_sync(0xffffffffu, lastp, 1);
-        int R = __shfl_down_sync(0xffffffffu, firstp, 1);
-        if (lane == 0) L = kNoLeft;
-        if (lane == 31) R = kNoRight;
-        int left[S], best[S];
-        int cur = L;
-#pragma unroll
-        for (int i = 0; i < S; ++i) {
-            if ((m >> i) & 1u) cur = x0 + i;
-            left[i] = cur;
-        }
-        cur = R;
-#pragma unroll
-        for (int i = S - 1; i >= 0; --i) {
-            if ((m >> i) & 1u) cur = x0 + i;
-            const int x = x0 + i;
-            best[i] = (x - left[i] <= cur - x) ? left[i] : cur;
-        }
-        if (x0 < Xp) {
-            if (SMALL) {
-                uint32_t wv[S / 4];
-#pragma unroll
-                for (int q = 0; q < S / 4; ++q)
-                    wv[q] = (best[4 * q] & 0xFF) | ((best[4 * q + 1] & 0xFF) << 8) |
-                            ((best[4 * q + 2] & 0xFF) << 16) | (static_cast<uint32_t>(best[4 * q + 3]) << 24);
-                uint32_t *o = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(gd[g].xs) + lr * Xp + x0);
-#pragma unroll
-                for (int q = 0; q < S / 4; q += 2) *reinterpret_cast<uint2 *>(o + q) = make_uint2(wv[q], wv[q + 1]);
-                if (lane == 0) gd[g].row_has[lr] = any ? 1 : 0;
-            } else {
-                uint32_t wv[S / 2];
-#pragma unroll
-                for (int q = 0; q < S / 2; ++q)
-                    wv[q] = any ? ((best[2 * q] & 0xFFFF) | (static_cast<uint32_t>(best[2 * q + 1]) << 16))
-                                : 0xFFFFFFFFu;
-                uint32_t *o = reinterpret_cast<uint32_t *>(static_cast<uint16_t *>(gd[g].xs) + lr * Xp + x0);
-#pragma unroll
-                for (int q = 0; q < S / 2; q += 4)
-                    *reinterpret_cast<uint4 *>(o + q) = make_uint4(wv[q], wv[q + 1], wv[q + 2], wv[q + 3]);
-            }
-        }
+        pass_x_row<S, SMALL>(gd[g], r - gd[g].row_begin, lane);
     }
 }
 
@@ -134,9 +137,9 @@ __device__ __forceinline__ int find_grid(const GridDesc *__restrict__ gd, int ng
 
 // After a timed-out wait, give copies still in flight a bounded chance to land before
 // the CTA releases its shared memory.
-__device__ __forceinline__ void drain_after_timeout(uint64_t *bar) {
+__device__ __forceinline__ void drain_after_timeout(uint64_t *bar, uint32_t phase) {
     for (uint32_t i = 0; i < (1u << 20); ++i)
-        if (mbar_try_wait(bar, 0)) return;
+        if (mbar_try_wait(bar, phase)) return;
 }
 
 constexpr int kCols = kEnvCols;   // columns per tile (one thread per column and half)
@@ -358,20 +361,19 @@ struct EmitY {
     }
 };
 
+// One pass-Y tile (grid g, tile lt of that grid).  `phase` is the parity of the tile
+// barrier's current phase; the barrier must have been initialised.  Returns false if
+// the staging wait timed out.  Ends with a CTA barrier so the caller may reuse smem.
 template <bool SMALL>
-__global__ void __launch_bounds__(kLanes) k_pass_y(const GridDesc *__restrict__ gd,
-                                                   const CUtensorMap *__restrict__ tm, int ng, int32_t *err) {
+__device__ __forceinline__ bool tile_y(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
+                                       int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
     using E = Env<SMALL>;
     using Link = typename E::Link;
     using XS = typename E::XS;
     using Site = typename E::Site;
-    extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
-    const int64_t t = blockIdx.x;
-    const int g = find_grid(gd, ng, t, 0);
     const int Y = gd[g].Y, Xp = gd[g].Xp;
     const int tiles_x = Xp / kCols;
-    const int64_t lt = t - gd[g].ty_begin;
     const int z = static_cast<int>(lt / tiles_x);
     const int x0 = static_cast<int>(lt % tiles_x) * kCols;
     const int by = min(Y, kBox);
@@ -382,10 +384,8 @@ __global__ void __launch_bounds__(kLanes) k_pass_y(const GridDesc *__restrict__ 
     Link *stack = reinterpret_cast<Link *>(smem + in_bytes);                  // [half][64]
     int *ks = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(stack + static_cast<size_t>(half) * kLanes) + 15) &
                                       ~uintptr_t(15));                        // [64]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(ks + kLanes);
-    uint8_t *rh = reinterpret_cast<uint8_t *>(bar + 1);                       // [Y]
+    uint8_t *rh = reinterpret_cast<uint8_t *>(ks + kLanes);                   // [Y]
     if (tid == 0) {
-        mbar_init(bar, 1);
         mbar_arrive_expect_tx(bar, static_cast<uint32_t>(in_bytes));
         for (int b = 0; b < nbox; ++b)
             tma_load_3d(in + static_cast<size_t>(b) * by * kCols, &tm[2 * g], x0, b * by, z, bar);
@@ -395,9 +395,10 @@ __global__ void __launch_bounds__(kLanes) k_pass_y(const GridDesc *__restrict__ 
         for (int q = tid; q < Y; q += kLanes) rh[q] = src[q];
     }
     __syncthreads();
-    if (!mbar_wait_bounded(bar, 0, err)) {
-        drain_after_timeout(bar);
-        return;
+    if (!mbar_wait_bounded(bar, phase, err)) {
+        drain_after_timeout(bar, phase);
+        __syncthreads();
+        return false;
     }
     const int ci = tid & (kCols - 1);
     const int lo = tid >= kTile ? half : 0;
@@ -406,6 +407,20 @@ __global__ void __launch_bounds__(kLanes) k_pass_y(const GridDesc *__restrict__ 
     int k_total;
     envelope_two_warps<SMALL>(Y, tid, stack, ks, L, emit, k_total);
     if (x0 == 0 && tid == 0) gd[g].slice_has[z] = k_total > 0 ? 1 : 0;
+    __syncthreads();
+    return true;
+}
+
+template <bool SMALL>
+__global__ void __launch_bounds__(kLanes) k_pass_y(const GridDesc *__restrict__ gd,
+                                                   const CUtensorMap *__restrict__ tm, int ng, int32_t *err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bar;
+    const int64_t t = blockIdx.x;
+    const int g = find_grid(gd, ng, t, 0);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    tile_y<SMALL>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, 0, err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -446,18 +461,14 @@ struct EmitZ {
 };
 
 template <bool SMALL>
-__global__ void __launch_bounds__(kLanes) k_pass_z(const GridDesc *__restrict__ gd,
-                                                   const CUtensorMap *__restrict__ tm, int ng, int32_t *err) {
+__device__ __forceinline__ bool tile_z(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
+                                       int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
     using E = Env<SMALL>;
     using Link = typename E::Link;
     using Site = typename E::Site;
-    extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
-    const int64_t t = blockIdx.x;
-    const int g = find_grid(gd, ng, t, 1);
     const int X = gd[g].X, Y = gd[g].Y, Z = gd[g].Z, Xp = gd[g].Xp;
     const int tiles_x = Xp / kCols;
-    const int64_t lt = t - gd[g].tz_begin;
     const int y = static_cast<int>(lt / tiles_x);
     const int x0 = static_cast<int>(lt % tiles_x) * kCols;
     const int bz = min(Z, kBox);
@@ -468,19 +479,18 @@ __global__ void __launch_bounds__(kLanes) k_pass_z(const GridDesc *__restrict__ 
     Link *stack = reinterpret_cast<Link *>(smem + in_bytes);                    // [half][64]
     int *ks = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(stack + static_cast<size_t>(half) * kLanes) + 15) &
                                       ~uintptr_t(15));                          // [64]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(ks + kLanes);
-    uint8_t *has = reinterpret_cast<uint8_t *>(bar + 1);                        // [Z]
+    uint8_t *has = reinterpret_cast<uint8_t *>(ks + kLanes);                    // [Z]
     if (tid == 0) {
-        mbar_init(bar, 1);
         mbar_arrive_expect_tx(bar, static_cast<uint32_t>(in_bytes));
         for (int b = 0; b < nbox; ++b)
             tma_load_3d(in + static_cast<size_t>(b) * bz * kCols, &tm[2 * g + 1], x0, y, b * bz, bar);
     }
     for (int q = tid; q < Z; q += kLanes) has[q] = gd[g].slice_has[q];
     __syncthreads();
-    if (!mbar_wait_bounded(bar, 0, err)) {
-        drain_after_timeout(bar);
-        return;
+    if (!mbar_wait_bounded(bar, phase, err)) {
+        drain_after_timeout(bar, phase);
+        __syncthreads();
+        return false;
     }
     const int ci = tid & (kCols - 1);
     const int lo = tid >= kTile ? half : 0;
@@ -492,6 +502,117 @@ __global__ void __launch_bounds__(kLanes) k_pass_z(const GridDesc *__restrict__ 
     EmitZ<SMALL> emit{gd[g].sqdist + off, gd[g].idx + off, plane, X, X * Y, -1, x < X};
     int k_total;
     envelope_two_warps<SMALL>(Z, tid, stack, ks, L, emit, k_total);
+    __syncthreads();
+    return true;
+}
+
+template <bool SMALL>
+__global__ void __launch_bounds__(kLanes) k_pass_z(const GridDesc *__restrict__ gd,
+                                                   const CUtensorMap *__restrict__ tm, int ng, int32_t *err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bar;
+    const int64_t t = blockIdx.x;
+    const int g = find_grid(gd, ng, t, 1);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    tile_z<SMALL>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, 0, err);
+}
+
+// ------------------------------------------------------------------------------------
+// persistent EDT over a whole table: one launch, work items dequeued in order
+//   [0, nX)            pass-X items (rows_per_item rows of one grid)
+//   [nX, nX + nY)      pass-Y tiles, each waiting for its grid's pass-X items
+//   [nX + nY, total)   pass-Z tiles, each waiting for its grid's pass-Y tiles
+// A tile only ever waits for items with smaller indices, which were dequeued earlier by
+// running CTAs that never wait on later items, so the launch always drains.  Every
+// wait is bounded; on expiry the error word is flagged and the tile is skipped.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool wait_count(const unsigned *p, unsigned target, int32_t *err) {
+    for (uint32_t i = 0; i < (1u << 24); ++i) {
+        if (ld_acquire(p) >= target) return true;
+        __nanosleep(64);
+    }
+    atomicOr(err, kErrTimeout);
+    return false;
+}
+
+template <int S, bool SMALL>
+__global__ void __launch_bounds__(kLanes) k_edt_persistent(const GridDesc *__restrict__ gd,
+                                                           const CUtensorMap *__restrict__ tm, int ng,
+                                                           PersistCounters cnt, int rows_per_item, int32_t *err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bar;
+    __shared__ unsigned item_s;
+    __shared__ int ok_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned nX = cnt.n_x, nY = cnt.n_y, total = cnt.n_x + cnt.n_y + cnt.n_z;
+    if (tid == 0) mbar_init(&bar, 1);
+    uint32_t phase = 0;
+    for (;;) {
+        if (tid == 0) item_s = atomicAdd(cnt.next, 1u);
+        __syncthreads();
+        const unsigned it = item_s;
+        __syncthreads();
+        if (it >= total) break;
+        if (it < nX) {
+            // grid owning this pass-X item
+            int lo = 0, hi = ng - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (static_cast<unsigned>(gd[mid].xi_begin) <= it) lo = mid;
+                else hi = mid - 1;
+            }
+            const int g = lo;
+            const int64_t rows = static_cast<int64_t>(gd[g].Y) * gd[g].Z;
+            const int64_t r0 = static_cast<int64_t>(it - gd[g].xi_begin) * rows_per_item;
+            const int64_t r1 = min(rows, r0 + rows_per_item);
+            for (int64_t r = r0 + warp; r < r1; r += kLanes / 32) pass_x_row<S, SMALL>(gd[g], r, lane);
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(cnt.done_x + g, 1u);
+            }
+        } else if (it < nX + nY) {
+            const int64_t t = it - nX;
+            const int g = find_grid(gd, ng, t, 0);
+            if (tid == 0) {
+                const unsigned need = static_cast<unsigned>((static_cast<int64_t>(gd[g].Y) * gd[g].Z + rows_per_item - 1) /
+                                                            rows_per_item);
+                ok_s = wait_count(cnt.done_x + g, need, err);
+                __threadfence();
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+            __syncthreads();
+            if (ok_s) {
+                tile_y<SMALL>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, phase, err);
+                phase ^= 1u;
+            }
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(cnt.done_y + g, 1u);
+            }
+        } else {
+            const int64_t t = it - nX - nY;
+            const int g = find_grid(gd, ng, t, 1);
+            if (tid == 0) {
+                const unsigned need = static_cast<unsigned>(static_cast<int64_t>(gd[g].Xp / kCols) * gd[g].Z);
+                ok_s = wait_count(cnt.done_y + g, need, err);
+                __threadfence();
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+            __syncthreads();
+            if (ok_s) {
+                tile_z<SMALL>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, phase, err);
+                phase ^= 1u;
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -508,14 +629,14 @@ static size_t smem_y(const GridTable &t) {
     const int by = t.maxY > kBox ? kBox : t.maxY;
     const size_t rows = static_cast<size_t>((t.maxY + by - 1) / by) * by;
     const size_t xs = t.large ? 2 : 1, link = t.large ? 2 : 1;
-    return rows * kCols * xs + static_cast<size_t>((t.maxY + 1) / 2) * kLanes * link + 16 + kLanes * 4 + 8 + t.maxY;
+    return rows * kCols * xs + static_cast<size_t>((t.maxY + 1) / 2) * kLanes * link + 16 + kLanes * 4 + t.maxY;
 }
 
 static size_t smem_z(const GridTable &t) {
     const int bz = t.maxZ > kBox ? kBox : t.maxZ;
     const size_t rows = static_cast<size_t>((t.maxZ + bz - 1) / bz) * bz;
     const size_t site = t.large ? 4 : 2, link = t.large ? 2 : 1;
-    return rows * kCols * site + static_cast<size_t>((t.maxZ + 1) / 2) * kLanes * link + 16 + kLanes * 4 + 8 + t.maxZ;
+    return rows * kCols * site + static_cast<size_t>((t.maxZ + 1) / 2) * kLanes * link + 16 + kLanes * 4 + t.maxZ;
 }
 
 cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s) {
@@ -551,6 +672,35 @@ static cudaError_t launch_z_impl(const GridTable &t, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     k_pass_z<SMALL><<<static_cast<unsigned>(t.tiles_z), kLanes, sm, s>>>(t.desc, t.tmaps, t.n, t.err);
     return cudaGetLastError();
+}
+
+template <int S, bool SMALL>
+static cudaError_t launch_persistent_impl(const GridTable &t, const PersistCounters &c, int ctas_per_sm,
+                                          int rows_per_item, cudaStream_t s) {
+    const size_t sy = smem_y(t), sz = smem_z(t);
+    const size_t sm = sy > sz ? sy : sz;
+    auto k = k_edt_persistent<S, SMALL>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kLanes, sm);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int per_sm = ctas_per_sm > 0 && ctas_per_sm < occ ? ctas_per_sm : occ;
+    const int64_t total = static_cast<int64_t>(c.n_x) + c.n_y + c.n_z;
+    int64_t blocks = static_cast<int64_t>(sm_count()) * per_sm;
+    if (blocks > total) blocks = total;
+    if (blocks < 1) return cudaSuccess;
+    k<<<static_cast<unsigned>(blocks), kLanes, sm, s>>>(t.desc, t.tmaps, t.n, c, rows_per_item, t.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm, int rows_per_item,
+                              cudaStream_t s) {
+    if (!t.large) return launch_persistent_impl<8, true>(t, c, ctas_per_sm, rows_per_item, s);
+    if (t.maxXp <= 256) return launch_persistent_impl<8, false>(t, c, ctas_per_sm, rows_per_item, s);
+    if (t.maxXp <= 512) return launch_persistent_impl<16, false>(t, c, ctas_per_sm, rows_per_item, s);
+    return launch_persistent_impl<32, false>(t, c, ctas_per_sm, rows_per_item, s);
 }
 
 cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) {

@@ -10,20 +10,6 @@ namespace vedt {
 
 struct Origin { float o[3]; };
 
-__device__ __forceinline__ bool voxel_coord(float p, float o, float vs, int n, int &v) {
-    const float f = floorf(__fdiv_rn(__fsub_rn(p, o), vs));
-    if (!(f >= 0.0f) || !(f < static_cast<float>(n))) return false;   // NaN fails both tests
-    v = static_cast<int>(f);
-    return true;
-}
-
-__device__ __forceinline__ void rigid(const float *T, float px, float py, float pz, float &wx,
-                                      float &wy, float &wz) {
-    wx = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[0], px), __fmul_rn(T[1], py)), __fmul_rn(T[2], pz)), T[3]);
-    wy = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[4], px), __fmul_rn(T[5], py)), __fmul_rn(T[6], pz)), T[7]);
-    wz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[8], px), __fmul_rn(T[9], py)), __fmul_rn(T[10], pz)), T[11]);
-}
-
 // ClearMap (Alg. 2 line 4): 16-byte stores over the byte grid, byte tail.
 __global__ void __launch_bounds__(256) k_clear(uint8_t *__restrict__ p, int64_t n) {
     const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;

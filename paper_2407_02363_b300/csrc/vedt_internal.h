@@ -33,6 +33,15 @@ struct GridDesc {
     int64_t row_begin;      // prefix over rows (Y*Z) of the grids before this one
     int64_t ty_begin;       // prefix over pass-Y tiles ((Xp/32)*Z)
     int64_t tz_begin;       // prefix over pass-Z tiles ((Xp/32)*Y)
+    int64_t xi_begin;       // prefix over persistent pass-X items (ceil(Y*Z / rows_per_item))
+};
+
+// Work counters of one persistent EDT launch (device memory, zeroed before the launch).
+struct PersistCounters {
+    unsigned *next;         // next work item
+    unsigned *done_x;       // [n grids] pass-X items finished
+    unsigned *done_y;       // [n grids] pass-Y tiles finished
+    unsigned n_x, n_y, n_z; // item counts per pass
 };
 
 struct GridTable {
@@ -53,6 +62,8 @@ CUresult encode_tmap(CUtensorMap *m, CUtensorMapDataType t, int elem, void *base
 cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s);
 cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s);
 cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s);
+cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm, int rows_per_item,
+                              cudaStream_t s);
 
 // launchers (insert.cu)
 struct LinkPose { float T[VEDT_MAX_LINKS][12]; };
@@ -70,11 +81,81 @@ cudaError_t launch_query(const QueryGrid *g, int ng, int X, int Y, int Z, float 
 
 }  // namespace vedt
 
+#include <vector>
+
+namespace vedt {
+constexpr int kMaxQuery = 4096;
+struct EvPair {
+    int kind;
+    cudaEvent_t a, b;
+};
+}  // namespace vedt
+
+// A map handle: the environment grid M_I ([0]) and self grid M_S ([1]), their fields
+// and EDT scratch, all owned.
+struct vedt_map {
+    using GridTable = vedt::GridTable;
+    using QueryGrid = vedt::QueryGrid;
+    using EvPair = vedt::EvPair;
+    int32_t X = 0, Y = 0, Z = 0, Xp = 0;
+    float vs = 0.f;
+    float origin[3] = {0, 0, 0};
+    cudaStream_t stream = nullptr;
+    int large = 0;
+    int64_t N = 0;
+    // [0] = environment M_I, [1] = self M_S
+    uint8_t *occ[2] = {nullptr, nullptr};
+    int32_t *sq[2] = {nullptr, nullptr};
+    int32_t *ix[2] = {nullptr, nullptr};
+    void *xs[2] = {nullptr, nullptr};
+    uint8_t *row_has[2] = {nullptr, nullptr};
+    void *s2[2] = {nullptr, nullptr};
+    uint8_t *slice_has[2] = {nullptr, nullptr};
+    int32_t *err = nullptr;
+    // EDT launch tables for which = ENV (0), SELF (1), BOTH (2)
+    GridTable tab[3];
+    void *tab_mem = nullptr;
+    // query scratch
+    QueryGrid *qgrids = nullptr;   // device [3]: env, self, env+self ... see below
+    float *q_in = nullptr;         // device centres (3*kMaxQuery) + radii (kMaxQuery)
+    vedt_sphere_result *q_out = nullptr;
+    // links
+    float *link_pts = nullptr;
+    uint8_t *link_of = nullptr;
+    float *stage = nullptr;        // device staging for host point clouds
+    int64_t stage_cap = 0;         // points
+    int64_t n_link_pts = 0;
+    int n_links = 0;
+    // timing
+    bool timing = false;
+    std::vector<EvPair> pending;
+    std::vector<cudaEvent_t> free_events;
+    double ms[VEDT_NUM_KERNELS] = {};
+    int64_t cnt[VEDT_NUM_KERNELS] = {};
+};
+
+
 // ---------------------------------------------------------------------------------
 // device helpers: mbarrier + TMA (sm_90+ PTX, used here on sm_103a)
 // ---------------------------------------------------------------------------------
 #ifdef __CUDACC__
 namespace vedt {
+
+// World point -> voxel along one axis: floor((p - o) / vs) in fp32 with explicitly
+// rounded subtraction and division; inside iff 0 <= v < n (NaN is outside).
+__device__ __forceinline__ bool voxel_coord(float p, float o, float vs, int n, int &v) {
+    const float f = floorf(__fdiv_rn(__fsub_rn(p, o), vs));
+    if (!(f >= 0.0f) || !(f < static_cast<float>(n))) return false;
+    v = static_cast<int>(f);
+    return true;
+}
+
+// w_a = ((T_a0 p_x + T_a1 p_y) + T_a2 p_z) + T_a3 in fp32, every step rounded, no FMA.
+__device__ __forceinline__ void rigid(const float *T, float px, float py, float pz, float &wx, float &wy, float &wz) {
+    wx = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[0], px), __fmul_rn(T[1], py)), __fmul_rn(T[2], pz)), T[3]);
+    wy = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[4], px), __fmul_rn(T[5], py)), __fmul_rn(T[6], pz)), T[7]);
+    wz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[8], px), __fmul_rn(T[9], py)), __fmul_rn(T[10], pz)), T[11]);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

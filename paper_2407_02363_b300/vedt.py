@@ -65,6 +65,16 @@ _sig = {
     "vedt_frame": [_P, _P, _I64, _P, _P, _P, _U32, _P, _P, _I32, _P],
     "vedt_frame_host": [_P, _P, _I64, _P, _P, _P, _U32, _P, _P, _I32, _P],
     "vedt_edt_noalloc": [_P, _I32, _I32, _I32, _P, _P, _P],
+    "vedt_batch_create": [_P, _I32, _P, _P],
+    "vedt_batch_destroy": [_P],
+    "vedt_batch_set_tuning": [_P, _I32, _I32, _I32],
+    "vedt_batch_compute_edt": [_P],
+    "vedt_batch_register_links": [_P, _I32, _P, _P],
+    "vedt_batch_set_frame": [_P, _P, _P, _P, _U32, _P, _P, _I32, _P],
+    "vedt_batch_run": [_P],
+    "vedt_batch_capture": [_P],
+    "vedt_batch_replay": [_P],
+    "vedt_batch_check": [_P],
 }
 for _n, _a in _sig.items():
     _f = getattr(_lib, _n)
@@ -290,6 +300,62 @@ class Map:
         src = torch.as_tensor(np.ascontiguousarray(occ, dtype=np.uint8)) if isinstance(occ, np.ndarray) else occ
         dst.copy_(src.reshape(dst.shape))
         torch.cuda.synchronize()
+
+
+class Batch:
+    """Many maps processed together (vedt_batch_*): batched pipeline launches, one
+    persistent EDT launch, optional CUDA-graph capture."""
+
+    def __init__(self, maps, stream=None):
+        self.maps = list(maps)
+        arr = (ctypes.c_void_p * len(self.maps))(*[m.handle.value for m in self.maps])
+        h = ctypes.c_void_p()
+        _chk(_lib.vedt_batch_create(arr, len(self.maps), stream_handle(stream), ctypes.byref(h)), "vedt_batch_create")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            _lib.vedt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, ctas_per_sm=0, rows_per_item=32, persistent=True):
+        _chk(_lib.vedt_batch_set_tuning(self._h, int(ctas_per_sm), int(rows_per_item), 1 if persistent else 0),
+             "vedt_batch_set_tuning")
+
+    def compute_edt(self):
+        _chk(_lib.vedt_batch_compute_edt(self._h), "vedt_batch_compute_edt")
+
+    def register_links(self, link_points):
+        arrs = [np.ascontiguousarray(p, dtype=np.float32).reshape(-1, 3) for p in link_points]
+        ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+        nv = np.array([a.shape[0] for a in arrs], dtype=np.int64)
+        _chk(_lib.vedt_batch_register_links(self._h, len(arrs), ptrs, _np_ptr(nv)), "vedt_batch_register_links")
+        self._links = arrs
+
+    def set_frame(self, xyz_dev, offsets, poses_f32, link_mask, centres_dev, radii_dev, m, out_dev):
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        P = np.ascontiguousarray(poses_f32, dtype=np.float32)
+        _chk(_lib.vedt_batch_set_frame(self._h, dev_ptr(xyz_dev), _np_ptr(offs), _np_ptr(P), int(link_mask),
+                                       dev_ptr(centres_dev), dev_ptr(radii_dev), int(m), dev_ptr(out_dev)),
+             "vedt_batch_set_frame")
+
+    def run(self):
+        _chk(_lib.vedt_batch_run(self._h), "vedt_batch_run")
+
+    def capture(self):
+        _chk(_lib.vedt_batch_capture(self._h), "vedt_batch_capture")
+
+    def replay(self):
+        _chk(_lib.vedt_batch_replay(self._h), "vedt_batch_replay")
+
+    def check(self):
+        _chk(_lib.vedt_batch_check(self._h), "vedt_batch_check")
 
 
 class _CudaArray:
