@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--frames", type=int, default=60, help="distinct synthetic frames, cycled")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batch-steps", type=int, default=50, help="graph replays timed for the 64-map batch (0: skip)")
     return p.parse_args()
 
 
@@ -361,6 +362,8 @@ def run_vedt(args):
         e2e = run_e2e(args, v, m, W, n_frames, cchain, world, dev)
     m.close()
 
+    batched = run_batched(args, v, dev) if args.batch_steps > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(W, args.cpu_seconds)
@@ -377,9 +380,76 @@ def run_vedt(args):
                                                                                      int(0.99 * len(frame_ms)))],
                            "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
             "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
+            "batched": batched,
             "gpu_launches": int(sum(k["launches"] for k in kernels.values())), "clocks": clk,
         }
         print(json.dumps(line))
+
+
+def run_batched(args, v, dev):
+    """64 independent maps (each axis uniform in 64..192 voxels of 2 cm), each with its own
+    50k-point cloud and 7-DoF joint state: the whole insert -> EDT -> query frame as one
+    CUDA graph over all maps, launch shapes picked by the autotuner."""
+    import torch
+
+    import paper_2407_02363_b300.autotune as at
+    from paper_2407_02363_b300 import synth
+    seed = 1234 + 3000
+    dims_list = synth.batch_dims(seed, n_maps=64)
+    chain = synth.make_chain(seed, (0.0, 0.0, 0.0))
+    links = synth.link_models(chain, 0.02)
+    spheres = synth.sphere_model(chain)
+    m_sph = len(spheres.radius)
+    qs = synth.joint_states(seed, len(dims_list))
+    stream = torch.cuda.Stream(device=dev)
+    maps = [v.Map(tuple(int(x) for x in d), 0.02, stream=stream) for d in dims_list]
+    clouds, poses, centres = [], [], []
+    for i, d in enumerate(dims_list):
+        grid = synth.GridSpec(tuple(int(x) for x in d), 0.02)
+        clouds.append(synth.surface_cloud(seed + i, grid, 50_000))
+        ch = synth.Chain(base=chain.base.copy(), offsets=chain.offsets, lengths=chain.lengths, radius=chain.radius)
+        ch.base[:, 3] = np.array(grid.extent) / 2
+        P = v.fk(ch, qs[i])
+        poses.append(P.astype(np.float32))
+        R = P[spheres.link]
+        centres.append((np.einsum("nij,nj->ni", R[:, :, :3], spheres.local) + R[:, :, 3]).astype(np.float32))
+    offs = np.zeros(len(dims_list) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum([len(c) for c in clouds])
+    xyz = torch.from_numpy(np.concatenate(clouds)).to(dev)
+    cen = torch.from_numpy(np.stack(centres)).to(dev)
+    radii = torch.from_numpy(spheres.radius).to(dev)
+    out = torch.empty(len(maps) * 2 * m_sph * 32, dtype=torch.uint8, device=dev)
+    b = v.Batch(maps, stream=stream)
+    b.register_links(links)
+    b.set_frame(xyz, offs, np.stack(poses), SELF_MASK, cen, radii, m_sph, out)
+    b.run()
+    b.check()
+    cands = [(0, 0, 32), (1, 0, 8), (1, 0, 32), (1, 0, 128), (1, 4, 32), (1, 8, 32)]
+    best, times = at.tune(b, stream, dims_list, candidates=cands, reps=3, force=True)
+    b.capture()
+    for _ in range(3):
+        b.replay()
+    b.check()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.batch_steps):
+        b.replay()
+    e.record(stream)
+    torch.cuda.synchronize()
+    b.check()
+    ms = a.elapsed_time(e) / args.batch_steps
+    vox = 2 * sum(int(d[0]) * int(d[1]) * int(d[2]) for d in dims_list)
+    b.close()
+    for m in maps:
+        m.close()
+    return {"workload": "batch64: 64 maps, each axis U{64..192} voxels of 2 cm, 50k points + own 7-DoF joint state "
+                        "per map; clear+insert+EDT+query of both grids of every map as one CUDA graph",
+            "maps": len(dims_list), "voxels_per_frame": vox, "ms_per_frame": ms,
+            "gvoxel_s": vox / (ms * 1e-3) / 1e9, "replays": args.batch_steps,
+            "tuning": {"persistent": best.persistent, "ctas_per_sm": best.ctas_per_sm,
+                       "rows_per_item": best.rows_per_item},
+            "edt_ms_by_tuning": {f"{t.persistent}/{t.ctas_per_sm}/{t.rows_per_item}": ms_ for t, ms_ in times.items()}}
 
 
 def run_e2e(args, v, m, W, n_frames, cchain, world, dev):
