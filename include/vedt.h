@@ -255,6 +255,36 @@ enum { VEDT_K_CLEAR = 0, VEDT_K_INSERT_LINKS, VEDT_K_INSERT_POINTS, VEDT_K_EDT_X
 vedt_status vedt_set_timing(vedt_map *map, int enable);
 vedt_status vedt_kernel_times(vedt_map *map, double *ms_out, int64_t *count_out);
 
+/* ---- learned self-distance surrogate (not in the paper) ----------------------------------- */
+
+/* A BF16 MLP  [sin q, cos q] (14) -> 4 x (Linear 256 + ReLU) -> Linear 24  predicting the
+ * 24 per-sphere self-collision distances x_si of Eq. (selftaskvar) (metres) from the 7
+ * joint angles, trained on labels from the exact self-map EDT.  Every matrix product runs
+ * on the tensor cores (tcgen05.mma, bf16 operands, fp32 accumulation in tensor memory).
+ * Parameters are exchanged as one flat fp32 array, layer by layer W_l (out x in,
+ * row-major) then b_l (out): vedt_mlp_num_params() values. */
+typedef struct vedt_mlp vedt_mlp;
+
+int64_t vedt_mlp_num_params(void);
+/* batch_capacity: largest batch any later call may pass (rounded up to 128). */
+vedt_status vedt_mlp_create(int batch_capacity, void *stream, vedt_mlp **out);
+vedt_status vedt_mlp_destroy(vedt_mlp *net);
+/* Loads fp32 parameters (host), resets the AdamW moments and step count; synchronises. */
+vedt_status vedt_mlp_set_params(vedt_mlp *net, const float *params_host, int64_t count);
+vedt_status vedt_mlp_get_params(vedt_mlp *net, float *params_host, int64_t count);
+/* q_dev: B x 7 fp32 joint angles; out_dev: B x 24 fp32 predicted distances.  Async. */
+vedt_status vedt_mlp_forward(vedt_mlp *net, const float *q_dev, int B, float *out_dev);
+/* Masked mean-squared-error loss on (q_dev, y_dev B x 24, mask_dev B x 24 or NULL):
+ * gradient of every parameter (host, flat layout) and the loss; synchronises. */
+vedt_status vedt_mlp_grads(vedt_mlp *net, const float *q_dev, const float *y_dev, const float *mask_dev, int B,
+                           float *grads_host, int64_t count, float *loss_host);
+/* One AdamW step (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay wd) on that loss;
+ * loss_sums_dev (nullable, 2 floats) receives {sum of squared errors, mask count}.  Async. */
+vedt_status vedt_mlp_train_step(vedt_mlp *net, const float *q_dev, const float *y_dev, const float *mask_dev, int B,
+                                float lr, float wd, float *loss_sums_dev);
+/* Synchronises; ETIMEOUT if an in-kernel wait expired. */
+vedt_status vedt_mlp_check(vedt_mlp *net);
+
 /* ---- EDT without device allocation -------------------------------------------------------- */
 
 /* The paper has no counterpart to this call; it exists for callers that must not allocate

@@ -75,6 +75,14 @@ _sig = {
     "vedt_batch_capture": [_P],
     "vedt_batch_replay": [_P],
     "vedt_batch_check": [_P],
+    "vedt_mlp_create": [_I32, _P, _P],
+    "vedt_mlp_destroy": [_P],
+    "vedt_mlp_set_params": [_P, _P, _I64],
+    "vedt_mlp_get_params": [_P, _P, _I64],
+    "vedt_mlp_forward": [_P, _P, _I32, _P],
+    "vedt_mlp_grads": [_P, _P, _P, _P, _I32, _P, _I64, _P],
+    "vedt_mlp_train_step": [_P, _P, _P, _P, _I32, _F32, _F32, _P],
+    "vedt_mlp_check": [_P],
 }
 for _n, _a in _sig.items():
     _f = getattr(_lib, _n)
@@ -83,6 +91,8 @@ for _n, _a in _sig.items():
 _lib.vedt_status_string.argtypes = [ctypes.c_int]
 _lib.vedt_status_string.restype = ctypes.c_char_p
 _lib.vedt_version.restype = ctypes.c_char_p
+_lib.vedt_mlp_num_params.restype = ctypes.c_int64
+_lib.vedt_mlp_num_params.argtypes = []
 
 
 def status_string(s: int) -> str:
@@ -356,6 +366,57 @@ class Batch:
 
     def check(self):
         _chk(_lib.vedt_batch_check(self._h), "vedt_batch_check")
+
+
+class MLP:
+    """The learned self-distance surrogate (vedt_mlp_*): forward, gradients and AdamW
+    steps in the library's tensor-core kernels."""
+
+    def __init__(self, batch_capacity, stream=None):
+        h = ctypes.c_void_p()
+        _chk(_lib.vedt_mlp_create(int(batch_capacity), stream_handle(stream), ctypes.byref(h)), "vedt_mlp_create")
+        self._h = h
+        self.n_params = int(_lib.vedt_mlp_num_params())
+
+    def close(self):
+        if self._h:
+            _lib.vedt_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _chk(_lib.vedt_mlp_set_params(self._h, _np_ptr(p), p.size), "vedt_mlp_set_params")
+
+    def get_params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _chk(_lib.vedt_mlp_get_params(self._h, _np_ptr(p), p.size), "vedt_mlp_get_params")
+        return p
+
+    def forward(self, q_dev, out_dev, B=None):
+        B = int(q_dev.shape[0]) if B is None else int(B)
+        _chk(_lib.vedt_mlp_forward(self._h, dev_ptr(q_dev), B, dev_ptr(out_dev)), "vedt_mlp_forward")
+
+    def grads(self, q_dev, y_dev, mask_dev=None, B=None):
+        B = int(q_dev.shape[0]) if B is None else int(B)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _chk(_lib.vedt_mlp_grads(self._h, dev_ptr(q_dev), dev_ptr(y_dev), dev_ptr(mask_dev), B, _np_ptr(g), g.size,
+                                 ctypes.byref(loss)), "vedt_mlp_grads")
+        return float(loss.value), g
+
+    def train_step(self, q_dev, y_dev, mask_dev=None, lr=1e-3, wd=0.0, loss_sums_dev=None, B=None):
+        B = int(q_dev.shape[0]) if B is None else int(B)
+        _chk(_lib.vedt_mlp_train_step(self._h, dev_ptr(q_dev), dev_ptr(y_dev), dev_ptr(mask_dev), B, float(lr),
+                                      float(wd), dev_ptr(loss_sums_dev)), "vedt_mlp_train_step")
+
+    def check(self):
+        _chk(_lib.vedt_mlp_check(self._h), "vedt_mlp_check")
 
 
 class _CudaArray:
