@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch-steps", type=int, default=50, help="graph replays timed for the 64-map batch (0: skip)")
+    p.add_argument("--sur-train", type=int, default=2 * 1024 * 1024, help="surrogate training configurations (0: skip)")
+    p.add_argument("--sur-steps", type=int, default=20000, help="surrogate AdamW steps (batch 8192)")
     return p.parse_args()
 
 
@@ -363,6 +365,7 @@ def run_vedt(args):
     m.close()
 
     batched = run_batched(args, v, dev) if args.batch_steps > 0 else None
+    sur = run_surrogate(args, v, dev) if (args.sur_train > 0 and rank == 0) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -380,7 +383,7 @@ def run_vedt(args):
                                                                                      int(0.99 * len(frame_ms)))],
                            "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
             "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
-            "batched": batched,
+            "batched": batched, "surrogate": sur,
             "gpu_launches": int(sum(k["launches"] for k in kernels.values())), "clocks": clk,
         }
         print(json.dumps(line))
@@ -450,6 +453,68 @@ def run_batched(args, v, dev):
             "tuning": {"persistent": best.persistent, "ctas_per_sm": best.ctas_per_sm,
                        "rows_per_item": best.rows_per_item},
             "edt_ms_by_tuning": {f"{t.persistent}/{t.ctas_per_sm}/{t.rows_per_item}": ms_ for t, ms_ in times.items()}}
+
+
+def run_surrogate(args, v, dev):
+    """Learned self-distance surrogate: labels from the exact 128^3 / 2 cm self-map EDT,
+    BF16 MLP trained by the library's tensor-core kernels, evaluated on held-out
+    configurations; surrogate vs exact query throughput on this GPU."""
+    import torch
+
+    from oracle import mlp as omlp
+    from paper_2407_02363_b300 import surrogate as sg
+    from paper_2407_02363_b300 import synth
+    seed = 1234 + 4000
+    chain = synth.make_chain(seed, (1.28, 1.28, 1.28))
+    spheres = synth.sphere_model(chain)
+    lab = sg.ExactSelfDistance(chain, spheres, n_maps=512)
+    net = v.MLP(65536)
+    net.set_params(omlp.init_params(seed).astype(np.float32))
+    t0 = time.perf_counter()
+    hist, r_va, margin, label_qps = sg.fit(lab, net, n_train=args.sur_train, n_val=65536, seed=seed + 1,
+                                           steps=args.sur_steps, log_every=max(1, args.sur_steps // 4))
+    t_fit = time.perf_counter() - t0
+    dev_ = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    q_te = synth.joint_states(seed + 7, 65536)
+    d_te, s_te = lab(q_te)
+    valid = lab.valid_mask(s_te)
+    p_te = sg.clip(sg.predict(net, dev_(q_te)).cpu().numpy())
+    r_plain = sg.evaluate(p_te, sg.clip(d_te), valid, margin=0.05)
+    r_safe = sg.evaluate(p_te, sg.clip(d_te), valid, margin=margin)
+    qd = dev_(q_te)
+    out = torch.empty((65536, 24), device=dev)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        net.forward(qd, out)
+    torch.cuda.synchronize()
+    reps = 20
+    a.record()
+    for _ in range(reps):
+        net.forward(qd, out)
+    e.record()
+    torch.cuda.synchronize()
+    net.check()
+    sur_ms = a.elapsed_time(e) / reps
+    sur_qps = 65536 / (sur_ms * 1e-3)
+    exact_qps = label_qps
+    hybrid_qps = 1.0 / (1.0 / sur_qps + r_safe.fallback_rate / exact_qps)
+    flops = 2.0 * 65536 * sum(i * o for i, o in zip(omlp.SIZES[:-1], omlp.SIZES[1:]))
+    lab.close()
+    net.close()
+    return {"workload": "surrogate: MLP 14 -> 4x256 -> 24 (BF16, fp32 accumulate, tcgen05), trained on "
+                        f"{args.sur_train} uniform joint configs labelled by the exact 128^3 / 2 cm self-map EDT "
+                        f"({args.sur_steps} AdamW steps of 8192); inference batch 65536; distances clipped at "
+                        f"{sg.DIST_CLIP} m",
+            "train_seconds": t_fit, "final_train_loss": hist[-1][1] if hist else None,
+            "test": {"max_err_mm": r_plain.max_err_mm, "p99_err_mm": r_plain.p99_err_mm,
+                     "mean_err_mm": r_plain.mean_err_mm, "n": r_plain.n},
+            "fallback_5cm": {"rate": r_plain.fallback_rate, "missed_rate": r_plain.missed_rate},
+            "fallback_safe": {"margin_m": margin, "rate": r_safe.fallback_rate, "missed_rate": r_safe.missed_rate,
+                              "what": "margin = 5 cm + validation max error"},
+            "surrogate_query_per_s": sur_qps, "surrogate_ms_per_65536": sur_ms,
+            "surrogate_tflops": flops / (sur_ms * 1e-3) / 1e12,
+            "exact_query_per_s": exact_qps, "hybrid_query_per_s": hybrid_qps,
+            "gain_hybrid_over_exact": hybrid_qps / exact_qps}
 
 
 def run_e2e(args, v, m, W, n_frames, cchain, world, dev):

@@ -138,6 +138,9 @@ vedt_status vedt_insert_links(vedt_map *map, const float *poses_host, uint32_t l
  * matrix entry is summed left to right without FMA.  Errors: EINVAL. */
 vedt_status vedt_fk(const vedt_chain *chain, const double *q, double *poses_out);
 
+/* vedt_fk for n joint vectors q[n][n_joints]: poses_out[n][n_joints + 1][12]. */
+vedt_status vedt_fk_batch(const vedt_chain *chain, const double *q, int64_t n, double *poses_out);
+
 /* vedt_fk followed by rounding the poses to fp32 and vedt_insert_links(link_mask).
  * The chain must have n_joints + 1 <= registered links.  Errors: as both calls. */
 vedt_status vedt_insert_robot(vedt_map *map, const vedt_chain *chain, const double *q,
@@ -202,8 +205,12 @@ vedt_status vedt_batch_destroy(vedt_batch *batch);
  * Drops a recorded graph. */
 vedt_status vedt_batch_set_tuning(vedt_batch *batch, int ctas_per_sm, int rows_per_item, int persistent);
 
-/* PBA_EDT (Alg. 2 line 9) of both grids of every map in the batch. */
+/* PBA_EDT (Alg. 2 line 9) of the selected grids (default both) of every map in the batch. */
 vedt_status vedt_batch_compute_edt(vedt_batch *batch);
+
+/* Restricts the batch EDT to one grid of every map (VEDT_MAP_ENV / _SELF) or both
+ * (default); the skipped grid's field keeps its old contents.  Drops a recorded graph. */
+vedt_status vedt_batch_set_grids(vedt_batch *batch, int which);
 
 /* Offline link models shared by every map of the batch (same robot, own joint states);
  * as vedt_register_links. */

@@ -383,6 +383,16 @@ vedt_status vedt_fk(const vedt_chain *c, const double *q, double *out) {
     return VEDT_OK;
 }
 
+vedt_status vedt_fk_batch(const vedt_chain *c, const double *q, int64_t n, double *poses_out) {
+    if (!c || (n > 0 && (!q || !poses_out)) || n < 0) return VEDT_EINVAL;
+    const int J = c->n_joints;
+    for (int64_t i = 0; i < n; ++i) {
+        const vedt_status st = vedt_fk(c, q + i * J, poses_out + i * (J + 1) * 12);
+        if (st != VEDT_OK) return st;
+    }
+    return VEDT_OK;
+}
+
 vedt_status vedt_insert_robot(vedt_map *m, const vedt_chain *c, const double *q, uint32_t mask) {
     if (!m || !c || !q || c->n_joints < 1 || c->n_joints > VEDT_MAX_JOINTS) return VEDT_EINVAL;
     if (c->n_joints + 1 > m->n_links) return VEDT_EINVAL;

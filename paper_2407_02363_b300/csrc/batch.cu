@@ -162,6 +162,7 @@ struct vedt_batch {
     size_t counter_bytes = 0;
     int32_t *err = nullptr;
     int ctas_per_sm = 0, rows_per_item = 32, persistent = 1;
+    int which = VEDT_MAP_BOTH;           // grids the EDT covers
     // pipeline
     MapRef *refs = nullptr;
     float *link_pts = nullptr;
@@ -217,7 +218,8 @@ GridDesc grid_desc(const vedt_map *m, int i) {
 vedt_status build_tables(vedt_batch *b) {
     std::vector<GridDesc> mode[2];
     for (vedt_map *m : b->maps)
-        for (int i = 0; i < 2; ++i) mode[m->large].push_back(grid_desc(m, i));
+        for (int i = 0; i < 2; ++i)
+            if (b->which & (1 << i)) mode[m->large].push_back(grid_desc(m, i));
     char *base = static_cast<char *>(b->tab_mem);
     size_t off = 0;
     for (int md = 0; md < 2; ++md) {
@@ -319,6 +321,19 @@ vedt_status vedt_batch_set_tuning(vedt_batch *b, int ctas_per_sm, int rows_per_i
     return VEDT_OK;
 }
 
+vedt_status vedt_batch_set_grids(vedt_batch *b, int which) {
+    if (!b || (which != VEDT_MAP_ENV && which != VEDT_MAP_SELF && which != VEDT_MAP_BOTH)) return VEDT_EINVAL;
+    BCHECK(cudaStreamSynchronize(b->stream));
+    b->which = which;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+    }
+    return build_tables(b);
+}
+
 vedt_status vedt_batch_compute_edt(vedt_batch *b) {
     if (!b) return VEDT_EINVAL;
     for (int md = 0; md < 2; ++md) {
@@ -332,9 +347,10 @@ vedt_status vedt_batch_compute_edt(vedt_batch *b) {
             c.done_x = base + 1;
             c.done_y = base + 1 + b->ngrid[md];
             int64_t nx = 0;
+            const int gpm = (b->which == VEDT_MAP_BOTH) ? 2 : 1;
             for (vedt_map *m : b->maps)
                 if (m->large == md)
-                    nx += 2 * ((static_cast<int64_t>(m->Y) * m->Z + b->rows_per_item - 1) / b->rows_per_item);
+                    nx += gpm * ((static_cast<int64_t>(m->Y) * m->Z + b->rows_per_item - 1) / b->rows_per_item);
             c.n_x = static_cast<unsigned>(nx);
             c.n_y = static_cast<unsigned>(t.tiles_y);
             c.n_z = static_cast<unsigned>(t.tiles_z);

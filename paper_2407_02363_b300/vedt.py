@@ -83,6 +83,8 @@ _sig = {
     "vedt_mlp_grads": [_P, _P, _P, _P, _I32, _P, _I64, _P],
     "vedt_mlp_train_step": [_P, _P, _P, _P, _I32, _F32, _F32, _P],
     "vedt_mlp_check": [_P],
+    "vedt_fk_batch": [_P, _P, _I64, _P],
+    "vedt_batch_set_grids": [_P, _I32],
 }
 for _n, _a in _sig.items():
     _f = getattr(_lib, _n)
@@ -154,6 +156,15 @@ def fk(chain, q) -> np.ndarray:
     qa = np.ascontiguousarray(q, dtype=np.float64)
     out = np.zeros((c.n_joints + 1, 3, 4), dtype=np.float64)
     _chk(_lib.vedt_fk(ctypes.byref(c), _np_ptr(qa), _np_ptr(out)), "vedt_fk")
+    return out
+
+
+def fk_batch(chain, q) -> np.ndarray:
+    """vedt_fk for many joint vectors: (n, n_joints + 1, 3, 4) float64 poses."""
+    c = chain if isinstance(chain, Chain) else make_chain(chain)
+    qa = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, c.n_joints)
+    out = np.zeros((qa.shape[0], c.n_joints + 1, 3, 4), dtype=np.float64)
+    _chk(_lib.vedt_fk_batch(ctypes.byref(c), _np_ptr(qa), qa.shape[0], _np_ptr(out)), "vedt_fk_batch")
     return out
 
 
@@ -341,6 +352,9 @@ class Batch:
     def compute_edt(self):
         _chk(_lib.vedt_batch_compute_edt(self._h), "vedt_batch_compute_edt")
 
+    def set_grids(self, which):
+        _chk(_lib.vedt_batch_set_grids(self._h, int(which)), "vedt_batch_set_grids")
+
     def register_links(self, link_points):
         arrs = [np.ascontiguousarray(p, dtype=np.float32).reshape(-1, 3) for p in link_points]
         ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
@@ -376,6 +390,7 @@ class MLP:
         h = ctypes.c_void_p()
         _chk(_lib.vedt_mlp_create(int(batch_capacity), stream_handle(stream), ctypes.byref(h)), "vedt_mlp_create")
         self._h = h
+        self.cap = int(batch_capacity)
         self.n_params = int(_lib.vedt_mlp_num_params())
 
     def close(self):

@@ -1,0 +1,79 @@
+"""The learned self-distance surrogate end to end: exact labels against the oracle, the
+evaluation / fallback bookkeeping on the CPU, and on the GPU a short training run whose
+network, with the exact fallback below the margin, answers faster than the exact path
+alone without missing a near-collision configuration of the held-out set."""
+import numpy as np
+import pytest
+
+from paper_2407_02363_b300 import synth
+
+
+def test_evaluate_fallback_and_missed_bookkeeping():
+    from paper_2407_02363_b300.surrogate import evaluate
+    exact = np.array([[0.20, 0.30], [0.04, 0.30], [0.06, 0.30], [0.30, 0.01]])
+    pred = np.array([[0.21, 0.30], [0.07, 0.30], [0.045, 0.30], [0.30, 0.50]])
+    valid = np.array([[True, True], [True, True], [True, True], [True, False]])
+    r = evaluate(pred, exact, valid, margin=0.05)
+    # row 1: exact 4 cm but predicted 7 cm -> missed; row 2 falls back; row 3's near
+    # entry is masked so it is neither near nor a fallback
+    assert r.fallback_rate == 0.25 and r.missed_rate == 0.25
+    assert np.isclose(r.max_err_mm, 30.0)
+
+
+def _setup():
+    chain = synth.make_chain(1234 + 4000, (1.28, 1.28, 1.28))
+    spheres = synth.sphere_model(chain)
+    return chain, spheres
+
+
+@pytest.mark.gpu
+def test_exact_labels_match_oracle():
+    import oracle
+    from paper_2407_02363_b300.surrogate import ExactSelfDistance
+    chain, spheres = _setup()
+    lab = ExactSelfDistance(chain, spheres, n_maps=8)
+    q = synth.joint_states(1234 + 4000, 19)
+    dist, stat = lab(q)
+    links = synth.link_models(chain, 0.02)
+    for i in range(len(q)):
+        s = np.zeros((128, 128, 128), np.uint8)
+        oracle.insert_links(s, (128, 128, 128), 0.02, (0, 0, 0), links, oracle.fk(chain, q[i]).astype(np.float32),
+                            0b111)
+        sq, ix = oracle.edt(s)
+        r = oracle.query_spheres(sq, ix, (128, 128, 128), 0.02, (0, 0, 0), oracle.sphere_centres(chain, spheres, q[i]),
+                                 spheres.radius)
+        assert np.array_equal(stat[i], r["status"])
+        assert np.array_equal(dist[i].view(np.uint32), r["dist"].view(np.uint32))
+    lab.close()
+
+
+@pytest.mark.gpu
+def test_surrogate_trains_and_hybrid_beats_exact_safely():
+    import torch
+
+    from oracle import mlp as omlp
+    from paper_2407_02363_b300 import surrogate as sg
+    from paper_2407_02363_b300 import vedt as v
+    chain, spheres = _setup()
+    lab = sg.ExactSelfDistance(chain, spheres, n_maps=512)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    net = v.MLP(65536)
+    net.set_params(omlp.init_params(0).astype(np.float32))
+    hist, r_va, margin, _ = sg.fit(lab, net, n_train=262144, n_val=8192, seed=1, steps=12000, log_every=4000)
+    assert hist[-1][1] < 0.2 * hist[0][1], hist
+    q_te = synth.joint_states(3, 8192)
+    d_te, s_te = lab(q_te)
+    p_te = sg.clip(sg.predict(net, dev(q_te)).cpu().numpy())
+    r_te = sg.evaluate(p_te, sg.clip(d_te), lab.valid_mask(s_te), margin=margin)
+    assert r_te.p99_err_mm < 60.0, r_te
+    assert r_te.missed_rate == 0.0, r_te
+    # throughput: exact labels vs surrogate + exact fallback on the flagged fraction
+    qd = dev(synth.joint_states(4, 65536))
+    out = torch.empty((65536, 24), device="cuda")
+    sur_qps = sg.throughput(lambda: net.forward(qd, out), 65536, reps=5)
+    exact_qps = sg.throughput(lambda: lab(q_te[:1024]), 1024, reps=2, warmup=1)
+    hybrid_qps = 1.0 / (1.0 / sur_qps + r_te.fallback_rate / exact_qps)
+    assert sur_qps > 50 * exact_qps
+    assert r_te.fallback_rate < 0.9 and hybrid_qps > 1.1 * exact_qps, (r_te, sur_qps, exact_qps, hybrid_qps)
+    net.close()
+    lab.close()
