@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--batch-steps", type=int, default=50, help="graph replays timed for the 64-map batch (0: skip)")
     p.add_argument("--sur-train", type=int, default=2 * 1024 * 1024, help="surrogate training configurations (0: skip)")
     p.add_argument("--sur-steps", type=int, default=20000, help="surrogate AdamW steps (batch 8192)")
+    p.add_argument("--serve-frames", type=int, default=80, help="frames per arrival rate in the serving leg (0: skip)")
     return p.parse_args()
 
 
@@ -366,6 +367,7 @@ def run_vedt(args):
 
     batched = run_batched(args, v, dev) if args.batch_steps > 0 else None
     sur = run_surrogate(args, v, dev) if (args.sur_train > 0 and rank == 0) else None
+    srv = run_serving(args, v, dev) if (args.serve_frames > 0 and rank == 0) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -383,7 +385,7 @@ def run_vedt(args):
                                                                                      int(0.99 * len(frame_ms)))],
                            "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
             "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
-            "batched": batched, "surrogate": sur,
+            "batched": batched, "surrogate": sur, "serving": srv,
             "gpu_launches": int(sum(k["launches"] for k in kernels.values())), "clocks": clk,
         }
         print(json.dumps(line))
@@ -515,6 +517,47 @@ def run_surrogate(args, v, dev):
             "surrogate_tflops": flops / (sur_ms * 1e-3) / 1e12,
             "exact_query_per_s": exact_qps, "hybrid_query_per_s": hybrid_qps,
             "gain_hybrid_over_exact": hybrid_qps / exact_qps}
+
+
+def run_serving(args, v, dev):
+    """Continuous batching of control frames of mixed map sizes (128^3, 256^3, 512^3 at
+    1 cm, 50k-1M points each), maps resident as slots admitted by free HBM, Poisson
+    arrivals at 30 / 60 / 120 / 240 Hz aggregate; plus a saturation run (all frames
+    queued at once) for the aggregate throughput."""
+    import copy
+
+    from paper_2407_02363_b300 import serve
+    seed = 1234 + 5000
+    n = args.serve_frames
+    reqs, chains, spheres = serve.make_requests(seed, n, sizes=(128, 256, 512), rate_hz=60.0,
+                                                points=(50_000, 1_000_000), clouds_per_size=2)
+    srv = serve.gpu_server(chains, max_slots=24)
+    warm = [copy.copy(r) for r in reqs[:12]]          # creates the slots (allocation) outside the timing
+    srv.run(warm, realtime=False)
+    vox = lambda d: 2 * d[0] * d[1] * d[2]
+    out = {"workload": "serve: frames of 128^3 / 256^3 / 512^3 maps at 1 cm (1/3 each), 50k-1M points, maps "
+                       "resident as slots admitted by free HBM, one stream per slot, Poisson arrivals",
+           "rates": {}}
+    rng = np.random.default_rng(seed)
+    for rate in (30, 60, 120, 240):
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        batch = []
+        for r, t in zip(reqs, arr):
+            r2 = copy.copy(r)
+            r2.arrival = float(t)
+            batch.append(r2)
+        srv.done = []
+        done = srv.run(batch, realtime=True)
+        out["rates"][str(rate)] = serve.stats(done, vox)
+    srv.done = []
+    done = srv.run([copy.copy(r) for r in reqs], realtime=False)
+    out["saturation"] = serve.stats(done, vox)
+    out["slots"] = len(srv.slots)
+    out["max_inflight"] = srv.max_inflight
+    out["evictions"] = srv.evictions
+    for s_ in srv.slots:
+        s_.map.close()
+    return out
 
 
 def run_e2e(args, v, m, W, n_frames, cchain, world, dev):

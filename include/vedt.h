@@ -241,6 +241,25 @@ vedt_status vedt_batch_replay(vedt_batch *batch);
 /* Synchronises the batch's stream; ETIMEOUT if an in-kernel wait expired. */
 vedt_status vedt_batch_check(vedt_batch *batch);
 
+/* Asynchronous vedt_frame_host: the copies in, the frame and the copy of the 2m results
+ * out are queued on the map's stream and the call returns at once.  xyz_host and out_host
+ * must stay valid until vedt_frame_done reports completion (page-locked memory keeps the
+ * copies asynchronous); centres/radii are copied before the call returns. */
+vedt_status vedt_frame_host_async(vedt_map *map, const float *xyz_host, int64_t n_points,
+                                  const float *T_world_sensor_host, const vedt_chain *chain, const double *q,
+                                  uint32_t link_mask, const float *centres_host, const float *radii_host,
+                                  int m, vedt_sphere_result *out_host);
+
+/* VEDT_OK once every frame queued by vedt_frame_host_async on this map has completed,
+ * VEDT_EBUSY while one is still running, ETIMEOUT/ECUDA on failure.  Never blocks. */
+vedt_status vedt_frame_done(vedt_map *map);
+
+/* Device memory a map of these dims allocates (bytes), for admission control. */
+int64_t vedt_map_bytes(const int32_t dims[3]);
+
+/* Free and total device memory of the current device (cudaMemGetInfo). */
+vedt_status vedt_device_memory(int64_t *free_bytes, int64_t *total_bytes);
+
 /* ---- access ---------------------------------------------------------------------------- */
 
 /* Borrowed device pointers to the selected map's fields (which = ENV or SELF), valid

@@ -153,6 +153,7 @@ void free_map(vedt_map *m) {
     cudaFree(m->link_pts);
     cudaFree(m->link_of);
     cudaFree(m->stage);
+    if (m->done) cudaEventDestroy(m->done);
     for (auto &p : m->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -492,6 +493,69 @@ vedt_status vedt_frame_host(vedt_map *m, const float *xyz, int64_t n, const floa
         VCHECK(cudaMemcpyAsync(out, m->q_out, sizeof(vedt_sphere_result) * 2 * nq, cudaMemcpyDeviceToHost,
                                m->stream));
     return vedt_check(m);
+}
+
+vedt_status vedt_frame_host_async(vedt_map *m, const float *xyz, int64_t n, const float *T, const vedt_chain *chain,
+                                  const double *q, uint32_t mask, const float *centres, const float *radii, int nq,
+                                  vedt_sphere_result *out) {
+    if (!m || n < 0 || (n > 0 && !xyz) || nq < 0 || nq > kMaxQuery) return VEDT_EINVAL;
+    if (nq > 0 && (!centres || !radii || !out)) return VEDT_EINVAL;
+    if (!m->done) VCHECK(cudaEventCreateWithFlags(&m->done, cudaEventDisableTiming));
+    if (n > m->stage_cap) {
+        VCHECK(cudaStreamSynchronize(m->stream));
+        cudaFree(m->stage);
+        m->stage = nullptr;
+        m->stage_cap = 0;
+        VCHECK(cudaMalloc(&m->stage, sizeof(float) * 3 * n));
+        m->stage_cap = n;
+    }
+    if (n > 0) VCHECK(cudaMemcpyAsync(m->stage, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->stream));
+    if (nq > 0) {
+        VCHECK(cudaMemcpyAsync(m->q_in, centres, sizeof(float) * 3 * nq, cudaMemcpyHostToDevice, m->stream));
+        VCHECK(cudaMemcpyAsync(m->q_in + 3 * kMaxQuery, radii, sizeof(float) * nq, cudaMemcpyHostToDevice,
+                               m->stream));
+    }
+    vedt_status st = vedt_frame(m, m->stage, n, T, chain, q, mask, m->q_in, m->q_in + 3 * kMaxQuery, nq, m->q_out);
+    if (st != VEDT_OK) return st;
+    if (nq > 0)
+        VCHECK(cudaMemcpyAsync(out, m->q_out, sizeof(vedt_sphere_result) * 2 * nq, cudaMemcpyDeviceToHost,
+                               m->stream));
+    VCHECK(cudaEventRecord(m->done, m->stream));
+    return VEDT_OK;
+}
+
+vedt_status vedt_frame_done(vedt_map *m) {
+    if (!m) return VEDT_EINVAL;
+    if (!m->done) return VEDT_OK;
+    const cudaError_t e = cudaEventQuery(m->done);
+    if (e == cudaErrorNotReady) return VEDT_EBUSY;
+    if (e != cudaSuccess) return from_cuda(e);
+    int32_t err = 0;
+    VCHECK(cudaMemcpy(&err, m->err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) {
+        VCHECK(cudaMemset(m->err, 0, sizeof(int32_t)));
+        return (err & kErrTimeout) ? VEDT_ETIMEOUT : VEDT_ECUDA;
+    }
+    return VEDT_OK;
+}
+
+int64_t vedt_map_bytes(const int32_t dims[3]) {
+    if (!dims) return -1;
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > VEDT_MAX_DIM) return -1;
+    const bool large = dims[0] > kSmallMax || dims[1] > kSmallMax || dims[2] > kSmallMax;
+    const int64_t N = static_cast<int64_t>(dims[0]) * dims[1] * dims[2];
+    const int64_t Np = static_cast<int64_t>((dims[0] + kTile - 1) / kTile * kTile) * dims[1] * dims[2];
+    const int64_t per_grid = N * 9 + Np * (large ? 6 : 3) + static_cast<int64_t>(dims[1]) * dims[2] + dims[2];
+    return 2 * per_grid + (1 << 20);
+}
+
+vedt_status vedt_device_memory(int64_t *free_bytes, int64_t *total_bytes) {
+    size_t f = 0, t = 0;
+    VCHECK(cudaMemGetInfo(&f, &t));
+    if (free_bytes) *free_bytes = static_cast<int64_t>(f);
+    if (total_bytes) *total_bytes = static_cast<int64_t>(t);
+    return VEDT_OK;
 }
 
 vedt_status vedt_get_field(vedt_map *m, int which, const int32_t **sq, const int32_t **ix) {

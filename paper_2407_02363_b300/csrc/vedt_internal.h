@@ -123,6 +123,7 @@ struct vedt_map {
     float *link_pts = nullptr;
     uint8_t *link_of = nullptr;
     float *stage = nullptr;        // device staging for host point clouds
+    cudaEvent_t done = nullptr;    // completion of the last asynchronous host frame
     int64_t stage_cap = 0;         // points
     int64_t n_link_pts = 0;
     int n_links = 0;

@@ -131,8 +131,13 @@ class CameraScene:
     W, H, F, CX, CY = 640, 480, 525.0, 319.5, 239.5
 
     def __init__(self, seed: int, grid: GridSpec, n_boxes=6, n_spheres=4, n_cyl=4,
-                 n_points=300_000, noise=0.002, fps=30.0, speed=1.0, radius=0.3):
+                 n_points=300_000, noise=0.002, fps=30.0, speed=1.0, radius=0.3, resolution_scale=1.0):
         rng = np.random.default_rng(seed)
+        if resolution_scale != 1.0:     # a denser sensor: more pixels, same field of view
+            self.W = int(round(640 * resolution_scale))
+            self.H = int(round(480 * resolution_scale))
+            self.F = 525.0 * resolution_scale
+            self.CX, self.CY = (self.W - 1) / 2, (self.H - 1) / 2
         self.seed, self.grid, self.n_points, self.noise = seed, grid, n_points, noise
         self.fps, self.speed, self.radius = fps, speed, radius
         lo = np.asarray(grid.origin, np.float64)

@@ -85,6 +85,9 @@ _sig = {
     "vedt_mlp_check": [_P],
     "vedt_fk_batch": [_P, _P, _I64, _P],
     "vedt_batch_set_grids": [_P, _I32],
+    "vedt_frame_host_async": [_P, _P, _I64, _P, _P, _P, _U32, _P, _P, _I32, _P],
+    "vedt_frame_done": [_P],
+    "vedt_device_memory": [_P, _P],
 }
 for _n, _a in _sig.items():
     _f = getattr(_lib, _n)
@@ -94,6 +97,8 @@ _lib.vedt_status_string.argtypes = [ctypes.c_int]
 _lib.vedt_status_string.restype = ctypes.c_char_p
 _lib.vedt_version.restype = ctypes.c_char_p
 _lib.vedt_mlp_num_params.restype = ctypes.c_int64
+_lib.vedt_map_bytes.restype = ctypes.c_int64
+_lib.vedt_map_bytes.argtypes = [ctypes.c_void_p]
 _lib.vedt_mlp_num_params.argtypes = []
 
 
@@ -157,6 +162,19 @@ def fk(chain, q) -> np.ndarray:
     out = np.zeros((c.n_joints + 1, 3, 4), dtype=np.float64)
     _chk(_lib.vedt_fk(ctypes.byref(c), _np_ptr(qa), _np_ptr(out)), "vedt_fk")
     return out
+
+
+def map_bytes(dims) -> int:
+    """Device bytes a map of these dims allocates (admission control)."""
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    return int(_lib.vedt_map_bytes(_np_ptr(d)))
+
+
+def device_memory():
+    """(free, total) bytes of the current device."""
+    f, t = ctypes.c_int64(), ctypes.c_int64()
+    _chk(_lib.vedt_device_memory(ctypes.byref(f), ctypes.byref(t)), "vedt_device_memory")
+    return int(f.value), int(t.value)
 
 
 def fk_batch(chain, q) -> np.ndarray:
@@ -269,6 +287,31 @@ class Map:
                                   None if chain is None else ctypes.byref(chain), _np_ptr(qa), int(link_mask),
                                   _np_ptr(c), _np_ptr(r), c.shape[0], _np_ptr(out)), "vedt_frame_host")
         return out
+
+    def frame_host_async(self, xyz_host, chain, q, link_mask, centres, radii, out, T_world_sensor=None):
+        """Queues one control cycle from host buffers (vedt_frame_host_async); `xyz_host`
+        and `out` (a SPHERE_DTYPE array of 2m, or a pinned torch uint8 tensor) must stay
+        alive until done() is true."""
+        if hasattr(xyz_host, "data_ptr"):
+            n, xp = int(xyz_host.shape[0]), xyz_host.data_ptr()
+        else:
+            n, xp = int(xyz_host.shape[0]), _np_ptr(xyz_host)
+        c = np.ascontiguousarray(centres, dtype=np.float32).reshape(-1, 3)
+        r = np.ascontiguousarray(radii, dtype=np.float32).reshape(-1)
+        op = out.data_ptr() if hasattr(out, "data_ptr") else _np_ptr(out)
+        T = None if T_world_sensor is None else np.ascontiguousarray(T_world_sensor, np.float32).reshape(12)
+        qa = np.ascontiguousarray(q, dtype=np.float64)
+        _chk(_lib.vedt_frame_host_async(self._h, xp, n, None if T is None else _np_ptr(T),
+                                        None if chain is None else ctypes.byref(chain), _np_ptr(qa), int(link_mask),
+                                        _np_ptr(c), _np_ptr(r), c.shape[0], op), "vedt_frame_host_async")
+
+    def done(self):
+        """True once every queued asynchronous frame has completed (raises on failure)."""
+        st = _lib.vedt_frame_done(self._h)
+        if st == EBUSY:
+            return False
+        _chk(st, "vedt_frame_done")
+        return True
 
     def field_ptrs(self, which):
         sq, ix = ctypes.c_void_p(), ctypes.c_void_p()
