@@ -40,9 +40,20 @@ WORKLOAD = ("frame256: 256^3 grid at 1 cm; 300k-point synthetic depth-camera clo
             "into M_S from a smooth joint trajectory; exact int32 EDT (sqdist + nearest index) of both "
             "maps; 24-sphere query on both maps; consecutive frames")
 
-# ncu DRAM traffic per launch (read + write bytes) of the dominant kernel, with the
-# source it was taken from; set to None when the kernel changes.
-NCU_TRAFFIC = {}
+# ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one capture
+# of the frame256 workload, profiles/edt_passes_frame256.md) with a hash of the kernel
+# sources it was taken from; reported only while the sources still hash the same.
+NCU_TRAFFIC = {"edt_z": {"bytes": 67164416 + 207992064, "src": "cbdb8594da8316f3"}}
+KERNEL_SOURCES = ("paper_2407_02363_b300/csrc/edt.cu", "paper_2407_02363_b300/csrc/vedt_internal.h")
+
+
+def kernel_src_hash():
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -350,7 +361,8 @@ def run_vedt(args):
         k["share"] = k["total_ms"] / tot if tot else 0.0
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
     dk = kernels[dom]
-    traffic = NCU_TRAFFIC.get(dom)
+    tr = NCU_TRAFFIC.get(dom)
+    traffic = tr["bytes"] if tr and tr["src"] == kernel_src_hash() else None
     roof = {"kernel": dom, "bound": "hbm", "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
             "frac": dk["achieved_gbs"] / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
             "alg_bytes_per_launch": dk["alg_bytes_per_launch"]}

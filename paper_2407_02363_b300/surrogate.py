@@ -190,3 +190,44 @@ def throughput(fn, n_items, reps=5, warmup=2):
         fn()
     torch.cuda.synchronize()
     return n_items * reps / (time.perf_counter() - t0)
+
+
+def _main():
+    """`python -m paper_2407_02363_b300.surrogate forward [--batch B] [--reps R]`: runs the
+    surrogate forward on seeded random joint angles (He-uniform weights), for timing and
+    profiling; prints ms per batch."""
+    import argparse
+
+    import torch
+
+    from . import build
+    ap = argparse.ArgumentParser()
+    ap.add_argument("mode", choices=("forward",))
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--reps", type=int, default=10)
+    a = ap.parse_args()
+    build.build()
+    rng = np.random.default_rng(0)
+    net = v.MLP(a.batch)
+    params = []
+    for i, o in zip((14, 256, 256, 256, 256), (256, 256, 256, 256, 24)):
+        params += [rng.uniform(-math.sqrt(6 / i), math.sqrt(6 / i), o * i), np.zeros(o)]
+    net.set_params(np.concatenate(params).astype(np.float32))
+    q = torch.from_numpy(synth.joint_states(1, a.batch).astype(np.float32)).cuda()
+    out = torch.empty((a.batch, 24), device="cuda")
+    for _ in range(3):
+        net.forward(q, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        net.forward(q, out)
+    e1.record()
+    torch.cuda.synchronize()
+    net.check()
+    print(f"forward batch {a.batch}: {e0.elapsed_time(e1) / a.reps:.4f} ms")
+    net.close()
+
+
+if __name__ == "__main__":
+    _main()
