@@ -330,6 +330,13 @@ vedt_status vedt_mlp_check(vedt_mlp *net);
 vedt_status vedt_edt_noalloc(const uint8_t *occ_dev, int32_t X, int32_t Y, int32_t Z,
                              int32_t *sqdist_dev, int32_t *idx_dev, void *stream);
 
+/* Failure-detection self-test: launches the bounded in-kernel wait used by the persistent
+ * EDT on a counter that nothing increments, with `limit` polls (each followed by a ~64 ns
+ * sleep).  Returns VEDT_ETIMEOUT when the wait expired and flagged the error word as it
+ * should (the kernel then exits normally and the context stays usable), VEDT_OK if it did
+ * not.  Synchronises `stream`. */
+vedt_status vedt_selftest_wait(void *stream, uint32_t limit);
+
 /* Human-readable text for a status code (static storage). */
 const char *vedt_status_string(vedt_status s);
 

@@ -539,6 +539,24 @@ vedt_status vedt_frame_done(vedt_map *m) {
     return VEDT_OK;
 }
 
+vedt_status vedt_selftest_wait(void *stream, uint32_t limit) {
+    unsigned *counter = nullptr;
+    int32_t *err = nullptr;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMalloc(&counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_wait_selftest(counter, limit, err, s);
+    int32_t flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, err, sizeof(flag), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(counter);
+    cudaFree(err);
+    if (e != cudaSuccess) return from_cuda(e);
+    return (flag & kErrTimeout) ? VEDT_ETIMEOUT : VEDT_OK;
+}
+
 int64_t vedt_map_bytes(const int32_t dims[3]) {
     if (!dims) return -1;
     for (int a = 0; a < 3; ++a)

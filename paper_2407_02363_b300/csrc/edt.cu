@@ -533,13 +533,24 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
-__device__ __forceinline__ bool wait_count(const unsigned *p, unsigned target, int32_t *err) {
-    for (uint32_t i = 0; i < (1u << 24); ++i) {
+__device__ __forceinline__ bool wait_count(const unsigned *p, unsigned target, int32_t *err,
+                                           uint32_t limit = 1u << 24) {
+    for (uint32_t i = 0; i < limit; ++i) {
         if (ld_acquire(p) >= target) return true;
         __nanosleep(64);
     }
     atomicOr(err, kErrTimeout);
     return false;
+}
+
+// Self-test of the bounded wait: waits for a counter that nothing increments.
+__global__ void k_wait_selftest(const unsigned *counter, uint32_t limit, int32_t *err) {
+    if (threadIdx.x == 0) wait_count(counter, 1u, err, limit);
+}
+
+cudaError_t launch_wait_selftest(const unsigned *counter, uint32_t limit, int32_t *err, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(counter, limit, err);
+    return cudaGetLastError();
 }
 
 template <int S, bool SMALL>

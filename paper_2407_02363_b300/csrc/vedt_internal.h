@@ -64,6 +64,7 @@ cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s);
 cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s);
 cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm, int rows_per_item,
                               cudaStream_t s);
+cudaError_t launch_wait_selftest(const unsigned *counter, uint32_t limit, int32_t *err, cudaStream_t s);
 
 // launchers (insert.cu)
 struct LinkPose { float T[VEDT_MAX_LINKS][12]; };

@@ -88,6 +88,7 @@ _sig = {
     "vedt_frame_host_async": [_P, _P, _I64, _P, _P, _P, _U32, _P, _P, _I32, _P],
     "vedt_frame_done": [_P],
     "vedt_device_memory": [_P, _P],
+    "vedt_selftest_wait": [_P, _U32],
 }
 for _n, _a in _sig.items():
     _f = getattr(_lib, _n)

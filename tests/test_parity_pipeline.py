@@ -150,3 +150,15 @@ def test_timing_api_counts_launches():
     assert t["edt_x"][1] == 3 and t["edt_y"][1] == 3 and t["edt_z"][1] == 3 and t["clear"][1] == 6
     assert all(ms >= 0 for ms, _ in t.values())
     m.close()
+
+
+def test_bounded_wait_expires_with_status_not_hang():
+    """A wait on a counter nothing sets gives up after its limit, flags the error word,
+    and the host reads ETIMEOUT; the context keeps working afterwards."""
+    v = lib()
+    s = torch.cuda.Stream()
+    assert v._lib.vedt_selftest_wait(s.cuda_stream, 1 << 12) == v.ETIMEOUT
+    m = v.Map((16, 16, 16), 0.1)
+    m.compute_edt(v.MAP_BOTH)
+    m.check()
+    m.close()
