@@ -298,8 +298,12 @@ vedt_status vedt_mlp_destroy(vedt_mlp *net);
 /* Loads fp32 parameters (host), resets the AdamW moments and step count; synchronises. */
 vedt_status vedt_mlp_set_params(vedt_mlp *net, const float *params_host, int64_t count);
 vedt_status vedt_mlp_get_params(vedt_mlp *net, float *params_host, int64_t count);
-/* q_dev: B x 7 fp32 joint angles; out_dev: B x 24 fp32 predicted distances.  Async. */
+/* q_dev: B x 7 fp32 joint angles; out_dev: B x 24 fp32 predicted distances.  Async.
+ * One fused kernel: each CTA keeps its 128-row activation tile in shared memory through
+ * all five layers and streams the weights through a double buffer. */
 vedt_status vedt_mlp_forward(vedt_mlp *net, const float *q_dev, int B, float *out_dev);
+/* The same forward as one GEMM launch per layer (the training path's kernels). */
+vedt_status vedt_mlp_forward_layers(vedt_mlp *net, const float *q_dev, int B, float *out_dev);
 /* Masked mean-squared-error loss on (q_dev, y_dev B x 24, mask_dev B x 24 or NULL):
  * gradient of every parameter (host, flat layout) and the loss; synchronises. */
 vedt_status vedt_mlp_grads(vedt_mlp *net, const float *q_dev, const float *y_dev, const float *mask_dev, int B,

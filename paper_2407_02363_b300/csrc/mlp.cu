@@ -313,6 +313,163 @@ __global__ void k_to_bf16(const float *__restrict__ w, int N, int K, bf16 *__res
     wt[k * N + n] = h;
 }
 
+// ---------------------------------------------------------------- fused forward
+// One CTA computes all five layers for 128 rows.  The activation tile (128 x 256 bf16)
+// stays in shared memory in the canonical K-major layout (SBO 4096 B); weights stream in
+// K chunks of 32 columns (all N rows) through two cp.async buffers; chunk g of the whole
+// forward uses buffer g % 2, its MMAs commit to that buffer's mbarrier, and the buffer is
+// refilled only after that commit completed (parity (g / 2) & 1).
+struct FusedArgs {
+    const bf16 *w[kLayers];     // [N_l][K_l] row-major bf16
+    const float *b[kLayers];    // [N_l] fp32
+};
+
+constexpr int kFKC = 32;                    // weight K chunk
+constexpr int kActBytes = 128 * kHidden * 2;
+constexpr int kFeatBytes = 128 * kInPad * 2;
+constexpr int kWBufBytes = kHidden * kFKC * 2;
+constexpr int kFusedSmem = kActBytes + kFeatBytes + 2 * kWBufBytes;
+constexpr int kChunks = 1 + (kLayers - 1) * (kHidden / kFKC);   // 33
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// layer and K-chunk of global chunk index g
+__device__ __forceinline__ void chunk_of(int g, int &l, int &kc) {
+    if (g == 0) {
+        l = 0;
+        kc = 0;
+    } else {
+        l = 1 + (g - 1) / (kHidden / kFKC);
+        kc = (g - 1) % (kHidden / kFKC);
+    }
+}
+
+// stages weight chunk g (rows 0..N_l-1, K columns of the chunk) into buf, canonical layout
+__device__ __forceinline__ void stage_w(const FusedArgs &a, int g, uint8_t *buf) {
+    int l, kc;
+    chunk_of(g, l, kc);
+    const int N = layer_n(l), K = layer_k(l);
+    const int kw = (l == 0) ? kInPad : kFKC;    // chunk width in elements
+    const int kv = kw / 8;
+    const int V = N * kv;
+    const bf16 *W = a.w[l];
+    for (int v = threadIdx.x; v < V; v += kThreads) {
+        const int rr = v & 7, gg = v >> 3;
+        const int r = (gg / kv) * 8 + rr, k8 = gg % kv;
+        cp_async16(buf + 16 * v, W + static_cast<int64_t>(r) * K + kc * kFKC + 8 * k8);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mlp_fused(const float *__restrict__ q, int B, FusedArgs a,
+                                                        float *__restrict__ out, int32_t *err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    uint8_t *act = smem;
+    uint8_t *feat = smem + kActBytes;
+    uint8_t *wbuf[2] = {feat + kFeatBytes, feat + kFeatBytes + kWBufBytes};
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = blockIdx.x * 128 + tid;     // feature row of this thread
+    if (warp == 0) tmem_alloc(&tmem_base, 256);
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+    }
+    // features [sin q, cos q, 0, 0] of row `tid` in the canonical layout (kv = 2)
+    {
+        alignas(16) bf16 f[kInPad];
+        for (int j = 0; j < kInPad; ++j) {
+            float val = 0.f;
+            if (row < B && j < kIn) val = j < 7 ? sinf(q[row * 7 + j]) : cosf(q[row * 7 + j - 7]);
+            f[j] = __float2bfloat16_rn(val);
+        }
+        const int base = (tid >> 3) * 2 * 128 + (tid & 7) * 16;
+        *reinterpret_cast<uint4 *>(feat + base) = *reinterpret_cast<const uint4 *>(f);
+        *reinterpret_cast<uint4 *>(feat + base + 128) = *reinterpret_cast<const uint4 *>(f + 8);
+    }
+    stage_w(a, 0, wbuf[0]);
+    cp_async_commit();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = tmem_base;
+    bool ok = true;
+    for (int g = 0; g < kChunks && ok; ++g) {
+        int l, kc;
+        chunk_of(g, l, kc);
+        const int N = layer_n(l);
+        // refill the other buffer with chunk g+1 once chunk g-1's MMAs released it
+        if (g + 1 < kChunks) {
+            if (g >= 1) ok = mbar_wait_bounded(&mbar[(g + 1) & 1], ((g - 1) >> 1) & 1, err);
+            stage_w(a, g + 1, wbuf[(g + 1) & 1]);
+        }
+        cp_async_commit();
+        cp_async_wait_1();                       // chunk g has landed
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            if (l == 0) {
+                const uint64_t da = smem_desc(smem_u32(feat), 128, 256);
+                const uint64_t db = smem_desc(smem_u32(wbuf[0]), 128, 256);
+                mma_bf16(taddr, da, db, idesc_bf16(128, kHidden), 0u);
+            } else {
+                const uint32_t idesc = idesc_bf16(128, N);
+                for (int s = 0; s < kFKC / 16; ++s) {
+                    const int k16 = kc * (kFKC / 16) + s;
+                    const uint64_t da = smem_desc(smem_u32(act + k16 * 256), 128, (kHidden / 8) * 128);
+                    const uint64_t db = smem_desc(smem_u32(wbuf[g & 1] + s * 256), 128, (kFKC / 8) * 128);
+                    mma_bf16(taddr, da, db, idesc, (kc > 0 || s > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(&mbar[g & 1]);
+        }
+        const bool last = (l == 0) || (kc == kHidden / kFKC - 1);
+        if (!last || !ok) continue;
+        // layer done: wait for its MMAs, then epilogue from TMEM
+        ok = mbar_wait_bounded(&mbar[g & 1], (g >> 1) & 1, err);
+        if (!ok) break;
+        tc_fence_after();
+        const int r = blockIdx.x * 128 + warp * 32 + lane;
+        const int rl = warp * 32 + lane;       // row within the tile = TMEM lane
+        if (l < kLayers - 1) {
+            for (int c0 = 0; c0 < kHidden; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+                alignas(16) bf16 h[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(fmaxf(v[i] + a.b[l][c0 + i], 0.0f));
+                const int base = ((rl >> 3) * (kHidden / 8) + (c0 >> 3)) * 128 + (rl & 7) * 16;
+                *reinterpret_cast<uint4 *>(act + base) = *reinterpret_cast<const uint4 *>(h);
+                *reinterpret_cast<uint4 *>(act + base + 128) = *reinterpret_cast<const uint4 *>(h + 8);
+            }
+        } else {
+            for (int c0 = 0; c0 < kOutPad; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+                if (r < B) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (c0 + i < kOut) out[static_cast<int64_t>(r) * kOut + c0 + i] = v[i] + a.b[l][c0 + i];
+                }
+            }
+        }
+        tc_fence_before();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        tc_fence_after();
+    }
+    cp_async_wait_0();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, 256);
+}
+
 }  // namespace mlpk
 }  // namespace vedt
 
@@ -581,6 +738,20 @@ vedt_status vedt_mlp_get_params(vedt_mlp *n, float *params, int64_t count) {
 }
 
 vedt_status vedt_mlp_forward(vedt_mlp *n, const float *q_dev, int B, float *out_dev) {
+    if (!check_rows(n, B) || !q_dev || !out_dev) return VEDT_EINVAL;
+    FusedArgs a{};
+    for (int l = 0; l < kLayers; ++l) {
+        a.w[l] = n->wb[l];
+        a.b[l] = n->p + n->offB[l];
+    }
+    MCHECK(cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem));
+    k_mlp_fused<<<(B + 127) / 128, kThreads, kFusedSmem, n->stream>>>(q_dev, B, a, out_dev, n->err);
+    MCHECK(cudaGetLastError());
+    return VEDT_OK;
+}
+
+// Layer-by-layer forward (the training path's), kept for comparison.
+vedt_status vedt_mlp_forward_layers(vedt_mlp *n, const float *q_dev, int B, float *out_dev) {
     if (!check_rows(n, B) || !q_dev || !out_dev) return VEDT_EINVAL;
     const int rows = (B + 127) / 128 * 128;
     vedt_status st = features(n, q_dev, B, rows);

@@ -80,6 +80,7 @@ _sig = {
     "vedt_mlp_set_params": [_P, _P, _I64],
     "vedt_mlp_get_params": [_P, _P, _I64],
     "vedt_mlp_forward": [_P, _P, _I32, _P],
+    "vedt_mlp_forward_layers": [_P, _P, _I32, _P],
     "vedt_mlp_grads": [_P, _P, _P, _P, _I32, _P, _I64, _P],
     "vedt_mlp_train_step": [_P, _P, _P, _P, _I32, _F32, _F32, _P],
     "vedt_mlp_check": [_P],
@@ -460,6 +461,10 @@ class MLP:
     def forward(self, q_dev, out_dev, B=None):
         B = int(q_dev.shape[0]) if B is None else int(B)
         _chk(_lib.vedt_mlp_forward(self._h, dev_ptr(q_dev), B, dev_ptr(out_dev)), "vedt_mlp_forward")
+
+    def forward_layers(self, q_dev, out_dev, B=None):
+        B = int(q_dev.shape[0]) if B is None else int(B)
+        _chk(_lib.vedt_mlp_forward_layers(self._h, dev_ptr(q_dev), B, dev_ptr(out_dev)), "vedt_mlp_forward_layers")
 
     def grads(self, q_dev, y_dev, mask_dev=None, B=None):
         B = int(q_dev.shape[0]) if B is None else int(B)

@@ -109,3 +109,24 @@ def test_training_reduces_loss():
     net.check()
     assert losses[-1] < 0.2 * losses[0], losses
     net.close()
+
+
+@pytest.mark.parametrize("B", [128, 777, 65536])
+def test_fused_forward_matches_layer_path(B):
+    """The fused one-kernel forward and the per-layer GEMM forward round at the same
+    points (bf16 features and activations); only fp32 accumulation order may differ."""
+    v = lib()
+    rng = np.random.default_rng(B + 1)
+    theta = omlp.init_params(9) + rng.normal(scale=0.02, size=omlp.n_params())
+    net = _net(v, B, theta)
+    q = torch.from_numpy(rng.uniform(-np.pi, np.pi, size=(B, 7)).astype(np.float32)).cuda()
+    a = torch.zeros((B, 24), device="cuda")
+    b = torch.zeros((B, 24), device="cuda")
+    net.forward(q, a)
+    net.forward_layers(q, b)
+    net.check()
+    an, bn = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+    assert rel(an, bn) < 2e-3, rel(an, bn)
+    ref = ref_forward_bf16(theta.astype(np.float32).astype(np.float64), q.cpu().numpy().astype(np.float64))
+    assert rel(an, ref) < 1e-2
+    net.close()
