@@ -299,8 +299,10 @@ vedt_status vedt_mlp_destroy(vedt_mlp *net);
 vedt_status vedt_mlp_set_params(vedt_mlp *net, const float *params_host, int64_t count);
 vedt_status vedt_mlp_get_params(vedt_mlp *net, float *params_host, int64_t count);
 /* q_dev: B x 7 fp32 joint angles; out_dev: B x 24 fp32 predicted distances.  Async.
- * One fused kernel: each CTA keeps its 128-row activation tile in shared memory through
- * all five layers and streams the weights through a double buffer. */
+ * One persistent fused kernel, one CTA per SM: each CTA keeps two 128-row activation
+ * tiles in shared memory through all five layers, with one fp32 accumulator per tile in
+ * tensor memory, and streams pre-packed weight chunks through a ring of shared-memory
+ * stages. */
 vedt_status vedt_mlp_forward(vedt_mlp *net, const float *q_dev, int B, float *out_dev);
 /* The same forward as one GEMM launch per layer (the training path's kernels). */
 vedt_status vedt_mlp_forward_layers(vedt_mlp *net, const float *q_dev, int B, float *out_dev);

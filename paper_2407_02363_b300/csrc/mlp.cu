@@ -11,9 +11,11 @@
 // adjacent along M/N (KC/8)*128 bytes apart (SBO) for a K chunk of KC elements.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "vedt_internal.h"
@@ -314,160 +316,378 @@ __global__ void k_to_bf16(const float *__restrict__ w, int N, int K, bf16 *__res
 }
 
 // ---------------------------------------------------------------- fused forward
-// One CTA computes all five layers for 128 rows.  The activation tile (128 x 256 bf16)
-// stays in shared memory in the canonical K-major layout (SBO 4096 B); weights stream in
-// K chunks of 32 columns (all N rows) through two cp.async buffers; chunk g of the whole
-// forward uses buffer g % 2, its MMAs commit to that buffer's mbarrier, and the buffer is
-// refilled only after that commit completed (parity (g / 2) & 1).
+// All five layers run in one persistent kernel, one CTA per SM.  A CTA holds two 128-row
+// tiles ("slots") at once: each slot has its activation tile (128 x 256 bf16, canonical
+// K-major layout, SBO 4096 B) in shared memory and its own 256-column fp32 accumulator
+// in tensor memory (the two fill all 512 columns).  Warp roles:
+//   warp 0           streams weight chunks into a ring of kStages shared-memory stages
+//                    with bulk asynchronous copies (cp.async.bulk, mbarrier completion),
+//                    lane k filling stage k (one copy stream per lane: a single issuing
+//                    thread serialises the ring's round trips);
+//   warp 1, lane 0   issues the tcgen05.mma: every weight chunk feeds both slots;
+//   warps 2..9       epilogue of slot 0, warps 10..17 of slot 1 (two warps per TMEM lane
+//                    quadrant, one per column half): read the finished accumulator from
+//                    tensor memory, add bias, ReLU, round to bf16 and write the next
+//                    layer's input in place (or the fp32 output after the last layer),
+//                    then start the slot's next tile with its features.
+// Weight bytes, not MMAs, set the pace when a chunk feeds only 128 rows: a 32 KB chunk
+// holds 4 MMAs of work per slot, and a ring of three stages then buffers less tensor work
+// than one copy round trip lasts.  Feeding both slots from each chunk doubles the work per
+// byte; the price is that a layer's epilogue cannot overlap the same layer's MMAs, so the
+// MMA thread orders its work to hide most of it: slot 0's accumulator is committed before
+// slot 1's last MMAs, and at the next layer slot 1 waits behind slot 0's first chunk.
+// The weights are read as 14 pre-packed chunk images (each the exact shared-memory image
+// of its K columns), written by k_pack_w whenever the parameters change.
+struct WChunk {
+    int l, k0, kc, n, off;   // layer, first K column, K width, N rows, byte offset in the image
+};
+constexpr int kWKC = 64;                                  // K width of hidden-layer chunks
+constexpr int kChunksPerHidden = kHidden / kWKC;          // 4
+constexpr int kNumWChunks = 1 + 3 * kChunksPerHidden + 1; // 14
+constexpr int kStageBytes = kHidden * kWKC * 2;           // 32 KB
+constexpr int kWImageBytes = kHidden * kInPad * 2 + 3 * kChunksPerHidden * kStageBytes + kOutPad * kHidden * 2;
+
+__host__ __device__ constexpr WChunk wchunk(int c) {
+    return c == 0 ? WChunk{0, 0, kInPad, kHidden, 0}
+           : c <= 3 * kChunksPerHidden
+               ? WChunk{1 + (c - 1) / kChunksPerHidden, ((c - 1) % kChunksPerHidden) * kWKC, kWKC, kHidden,
+                        kHidden * kInPad * 2 + (c - 1) * kStageBytes}
+               : WChunk{kLayers - 1, 0, kHidden, kOutPad, kHidden * kInPad * 2 + 3 * kChunksPerHidden * kStageBytes};
+}
+// first chunk of layer l (l = kLayers gives the end)
+__host__ __device__ constexpr int layer_chunk_begin(int l) {
+    return l == 0 ? 0 : (l < kLayers ? 1 + (l - 1) * kChunksPerHidden : kNumWChunks);
+}
+static_assert(wchunk(kNumWChunks - 1).off + kOutPad * kHidden * 2 == kWImageBytes, "weight image size");
+
+// packs the bf16 weights W_l [N_l][K_l] into the chunk images
+__global__ void k_pack_w(const bf16 *w0, const bf16 *w1, const bf16 *w2, const bf16 *w3, const bf16 *w4,
+                         uint8_t *__restrict__ img) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= kWImageBytes / 16) return;
+    int c = 0;
+    while (c + 1 < kNumWChunks && wchunk(c + 1).off <= 16 * t) ++c;
+    const WChunk ch = wchunk(c);
+    const int v = t - ch.off / 16;
+    const int kv = ch.kc / 8, rr = v & 7, g = v >> 3;
+    const int r = (g / kv) * 8 + rr, k8 = g % kv;
+    const bf16 *W = ch.l == 0 ? w0 : ch.l == 1 ? w1 : ch.l == 2 ? w2 : ch.l == 3 ? w3 : w4;
+    *reinterpret_cast<uint4 *>(img + 16 * static_cast<int64_t>(t)) =
+        *reinterpret_cast<const uint4 *>(W + static_cast<int64_t>(r) * layer_k(ch.l) + ch.k0 + 8 * k8);
+}
+
+// Passed by value and read in place (__grid_constant__): the biases sit in the constant
+// bank, whose cache broadcasts the one column value a warp's lanes read together; with
+// the SM's shared memory taken by tiles and weights, L1 loads of them stall the epilogue.
 struct FusedArgs {
-    const bf16 *w[kLayers];     // [N_l][K_l] row-major bf16
-    const float *b[kLayers];    // [N_l] fp32
+    const uint8_t *wimg;                  // packed weight chunk images
+    float bias[kLayers - 1][kHidden];     // hidden-layer biases
+    float bias_out[kOutPad];              // output-layer bias (first kOut used)
 };
 
-constexpr int kFKC = 32;                    // weight K chunk
-constexpr int kActBytes = 128 * kHidden * 2;
-constexpr int kFeatBytes = 128 * kInPad * 2;
-constexpr int kWBufBytes = kHidden * kFKC * 2;
-constexpr int kFusedSmem = kActBytes + kFeatBytes + 2 * kWBufBytes;
-constexpr int kChunks = 1 + (kLayers - 1) * (kHidden / kFKC);   // 33
+constexpr int kStages = 3;
+constexpr int kActBytes = 128 * kHidden * 2;               // 64 KB per slot
+constexpr int kFusedThreads = 64 + 16 * 32;   // producer, MMA, 2 x 8 epilogue warps
+constexpr int kFusedSmem = 2 * kActBytes + kStages * kStageBytes;   // 224 KB
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// layer and K-chunk of global chunk index g
-__device__ __forceinline__ void chunk_of(int g, int &l, int &kc) {
-    if (g == 0) {
-        l = 0;
-        kc = 0;
-    } else {
-        l = 1 + (g - 1) / (kHidden / kFKC);
-        kc = (g - 1) % (kHidden / kFKC);
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// two fp32 values -> packed bf16 pair (x in the low half), round to nearest even, negatives to 0
+__device__ __forceinline__ uint32_t relu_bf16x2(float x, float y) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(y), "f"(x));
+    return d;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 64 consecutive columns of the warp's 32 lanes, waited for inside the same statement (so
+// no use of r can be scheduled before the load completes)
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
+}
+
+// two fp32 values -> packed bf16 pair (x in the low half), round to nearest even
+__device__ __forceinline__ uint32_t pack_bf16x2(float x, float y) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(y), "f"(x));
+    return d;
+}
+
+// features [sin q, cos q, 0, 0] of one row as bf16, in the order of the layer-0 input
+struct Feat {
+    uint4 lo, hi;
+};
+__device__ __forceinline__ Feat features_of(int row, const float *q, int B) {
+    float sn[7], cs[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        const float x = row < B ? q[static_cast<int64_t>(row) * 7 + j] : 0.f;
+        sn[j] = row < B ? sinf(x) : 0.f;
+        cs[j] = row < B ? cosf(x) : 0.f;
     }
+    Feat f;
+    f.lo = make_uint4(pack_bf16x2(sn[0], sn[1]), pack_bf16x2(sn[2], sn[3]), pack_bf16x2(sn[4], sn[5]),
+                      pack_bf16x2(sn[6], cs[0]));
+    f.hi = make_uint4(pack_bf16x2(cs[1], cs[2]), pack_bf16x2(cs[3], cs[4]), pack_bf16x2(cs[5], cs[6]), 0u);
+    return f;
+}
+// row rl of a slot's layer-0 input tile (K = 16 layout, SBO 256 B)
+__device__ __forceinline__ void store_features(uint8_t *act, int rl, const Feat &f) {
+    const int base = (rl >> 3) * 256 + (rl & 7) * 16;
+    *reinterpret_cast<uint4 *>(act + base) = f.lo;
+    *reinterpret_cast<uint4 *>(act + base + 128) = f.hi;
 }
 
-// stages weight chunk g (rows 0..N_l-1, K columns of the chunk) into buf, canonical layout
-__device__ __forceinline__ void stage_w(const FusedArgs &a, int g, uint8_t *buf) {
-    int l, kc;
-    chunk_of(g, l, kc);
-    const int N = layer_n(l), K = layer_k(l);
-    const int kw = (l == 0) ? kInPad : kFKC;    // chunk width in elements
-    const int kv = kw / 8;
-    const int V = N * kv;
-    const bf16 *W = a.w[l];
-    for (int v = threadIdx.x; v < V; v += kThreads) {
-        const int rr = v & 7, gg = v >> 3;
-        const int r = (gg / kv) * 8 + rr, k8 = gg % kv;
-        cp_async16(buf + 16 * v, W + static_cast<int64_t>(r) * K + kc * kFKC + 8 * k8);
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) k_mlp_fused(const float *__restrict__ q, int B, FusedArgs a,
-                                                        float *__restrict__ out, int32_t *err) {
+// Local tile i of this CTA is global tile blockIdx.x + i * gridDim.x and lives in slot
+// i & 1; local pair p holds tiles 2p and 2p + 1 (the last pair may hold one).  Rows past
+// the batch compute on zero features and store nothing.
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    k_mlp_fused(const float *__restrict__ q, int B, const __grid_constant__ FusedArgs a, float *__restrict__ out,
+                int32_t *err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t full[kStages], empty[kStages], acc_full[2], act_ready[2], fin;
     __shared__ uint32_t tmem_base;
-    uint8_t *act = smem;
-    uint8_t *feat = smem + kActBytes;
-    uint8_t *wbuf[2] = {feat + kFeatBytes, feat + kFeatBytes + kWBufBytes};
+    uint8_t *stage = smem + 2 * kActBytes;    // activation tile of slot s at smem + s * kActBytes
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row = blockIdx.x * 128 + tid;     // feature row of this thread
-    if (warp == 0) tmem_alloc(&tmem_base, 256);
+    const int n_tiles = (B + 127) / 128;
+    const int T = static_cast<int>(blockIdx.x) < n_tiles ? (n_tiles - 1 - static_cast<int>(blockIdx.x)) / gridDim.x + 1 : 0;
+    const int pairs = (T + 1) / 2;
+    auto tile_row0 = [&](int i) { return (static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x)) * 128; };
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-    }
-    // features [sin q, cos q, 0, 0] of row `tid` in the canonical layout (kv = 2)
-    {
-        alignas(16) bf16 f[kInPad];
-        for (int j = 0; j < kInPad; ++j) {
-            float val = 0.f;
-            if (row < B && j < kIn) val = j < 7 ? sinf(q[row * 7 + j]) : cosf(q[row * 7 + j - 7]);
-            f[j] = __float2bfloat16_rn(val);
+        for (int k = 0; k < kStages; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], 1);
         }
-        const int base = (tid >> 3) * 2 * 128 + (tid & 7) * 16;
-        *reinterpret_cast<uint4 *>(feat + base) = *reinterpret_cast<const uint4 *>(f);
-        *reinterpret_cast<uint4 *>(feat + base + 128) = *reinterpret_cast<const uint4 *>(f + 8);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&act_ready[s], 8);        // one arrival per epilogue warp of the slot
+        }
+        mbar_init(&fin, 1);
     }
-    stage_w(a, 0, wbuf[0]);
-    cp_async_commit();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = tmem_base;
-    bool ok = true;
-    for (int g = 0; g < kChunks && ok; ++g) {
-        int l, kc;
-        chunk_of(g, l, kc);
-        const int N = layer_n(l);
-        // refill the other buffer with chunk g+1 once chunk g-1's MMAs released it
-        if (g + 1 < kChunks) {
-            if (g >= 1) ok = mbar_wait_bounded(&mbar[(g + 1) & 1], ((g - 1) >> 1) & 1, err);
-            stage_w(a, g + 1, wbuf[(g + 1) & 1]);
+
+    if (warp == 0 && lane < kStages) {
+        // ---- weight producer: this lane fills stage `lane`, i.e. chunks it = lane (mod kStages)
+        uint32_t last = 0;
+        bool ok = true, any = false;
+        for (uint32_t it = lane; it < static_cast<uint32_t>(pairs * kNumWChunks) && ok; it += kStages) {
+            if (it >= kStages && !(ok = mbar_wait_bounded(&empty[lane], ((it / kStages) - 1) & 1, err))) break;
+            const WChunk ch = wchunk(static_cast<int>(it % kNumWChunks));
+            const uint32_t bytes = static_cast<uint32_t>(ch.n * ch.kc * 2);
+            mbar_arrive_expect_tx(&full[lane], bytes);
+            bulk_load(stage + lane * kStageBytes, a.wimg + ch.off, bytes, &full[lane]);
+            last = it;
+            any = true;
         }
-        cp_async_commit();
-        cp_async_wait_1();                       // chunk g has landed
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+        // the last copy into this stage has landed before the CTA exits (normally consumed)
+        if (any) mbar_wait_bounded(&full[lane], (last / kStages) & 1, err);
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer.  The tensor pipe idles whenever this thread spends time between
+        // MMAs, so descriptors are built once per layer and advanced by constants (the start
+        // address field counts 16-byte units), and the ring index advances without division.
+        const uint32_t id256 = idesc_bf16(128, kHidden), id32 = idesc_bf16(128, kOutPad);
+        const uint32_t stage0 = smem_u32(stage);
+        constexpr uint64_t kStageStep = kStageBytes >> 4;
+        constexpr uint64_t kSlotStep = kActBytes >> 4;
+        const uint64_t a_l0 = smem_desc(smem_u32(smem), 128, 256), a_h = smem_desc(smem_u32(smem), 128, (kHidden / 8) * 128);
+        const uint64_t b_l0 = smem_desc(stage0, 128, 256), b_h = smem_desc(stage0, 128, (kWKC / 8) * 128),
+                       b_out = smem_desc(stage0, 128, (kHidden / 8) * 128);
+        uint32_t k = 0, phase = 0, ready0 = 0, ready1 = 0;
+        bool ok = true;
+        auto next_stage = [&]() {
+            if (++k == kStages) {
+                k = 0;
+                phase ^= 1u;
+            }
+        };
+        auto wait_full = [&]() {
+            ok = mbar_wait_bounded(&full[k], phase, err);
             tc_fence_after();
-            if (l == 0) {
-                const uint64_t da = smem_desc(smem_u32(feat), 128, 256);
-                const uint64_t db = smem_desc(smem_u32(wbuf[0]), 128, 256);
-                mma_bf16(taddr, da, db, idesc_bf16(128, kHidden), 0u);
-            } else {
-                const uint32_t idesc = idesc_bf16(128, N);
-                for (int s = 0; s < kFKC / 16; ++s) {
-                    const int k16 = kc * (kFKC / 16) + s;
-                    const uint64_t da = smem_desc(smem_u32(act + k16 * 256), 128, (kHidden / 8) * 128);
-                    const uint64_t db = smem_desc(smem_u32(wbuf[g & 1] + s * 256), 128, (kFKC / 8) * 128);
-                    mma_bf16(taddr, da, db, idesc, (kc > 0 || s > 0) ? 1u : 0u);
+            return ok;
+        };
+        auto wait_ready = [&](int s) {
+            ok = mbar_wait_bounded(&act_ready[s], (s ? ready1++ : ready0++) & 1, err);
+            tc_fence_after();
+            return ok;
+        };
+        for (int p = 0; p < pairs && ok; ++p) {
+            const int ns = (2 * p + 1 < T) ? 2 : 1;
+            for (int l = 0; l < kLayers && ok; ++l) {
+                if (l == 0) {                           // K = 16: one MMA per slot
+                    if (!wait_full()) break;
+                    for (int s = 0; s < ns; ++s) {
+                        if (!wait_ready(s)) break;
+                        mma_bf16(taddr + s * 256, a_l0 + s * kSlotStep, b_l0 + k * kStageStep, id256, 0u);
+                        mma_commit(&acc_full[s]);
+                    }
+                    if (!ok) break;
+                    mma_commit(&empty[k]);
+                    next_stage();
+                } else if (l < kLayers - 1) {           // four chunks of K = 64, four MMAs per slot each
+                    for (int c = 0; c < kChunksPerHidden; ++c) {
+                        if (!wait_full()) break;
+                        const uint64_t b0 = b_h + k * kStageStep;
+                        for (int s = 0; s < ns; ++s) {
+                            if (c == 0 && !wait_ready(s)) break;
+                            const uint64_t a0 = a_h + s * kSlotStep + static_cast<uint64_t>(c * (kWKC / 16) * 16);
+                            const uint32_t d = taddr + s * 256;
+#pragma unroll
+                            for (int st = 0; st < kWKC / 16; ++st)
+                                mma_bf16(d, a0 + st * 16, b0 + st * 16, id256, (c | st) ? 1u : 0u);
+                            if (c == kChunksPerHidden - 1) mma_commit(&acc_full[s]);
+                        }
+                        if (!ok) break;
+                        mma_commit(&empty[k]);
+                        next_stage();
+                    }
+                } else {                                // N = 32, K = 256 in one chunk
+                    if (!wait_full()) break;
+                    const uint64_t b0 = b_out + k * kStageStep;
+                    for (int s = 0; s < ns; ++s) {
+                        if (!wait_ready(s)) break;
+                        const uint32_t d = taddr + s * 256;
+#pragma unroll
+                        for (int st = 0; st < kHidden / 16; ++st)
+                            mma_bf16(d, a_h + s * kSlotStep + st * 16, b0 + st * 16, id32, st ? 1u : 0u);
+                        mma_commit(&acc_full[s]);
+                    }
+                    if (!ok) break;
+                    mma_commit(&empty[k]);
+                    next_stage();
                 }
             }
-            mma_commit(&mbar[g & 1]);
         }
-        const bool last = (l == 0) || (kc == kHidden / kFKC - 1);
-        if (!last || !ok) continue;
-        // layer done: wait for its MMAs, then epilogue from TMEM
-        ok = mbar_wait_bounded(&mbar[g & 1], (g >> 1) & 1, err);
-        if (!ok) break;
-        tc_fence_after();
-        const int r = blockIdx.x * 128 + warp * 32 + lane;
-        const int rl = warp * 32 + lane;       // row within the tile = TMEM lane
-        if (l < kLayers - 1) {
-            for (int c0 = 0; c0 < kHidden; c0 += 16) {
-                float v[16];
-                tmem_ld16(taddr + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
-                alignas(16) bf16 h[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(fmaxf(v[i] + a.b[l][c0 + i], 0.0f));
-                const int base = ((rl >> 3) * (kHidden / 8) + (c0 >> 3)) * 128 + (rl & 7) * 16;
-                *reinterpret_cast<uint4 *>(act + base) = *reinterpret_cast<const uint4 *>(h);
-                *reinterpret_cast<uint4 *>(act + base + 128) = *reinterpret_cast<const uint4 *>(h + 8);
+        // all MMAs issued by this thread have completed before tensor memory is released
+        mma_commit(&fin);
+        mbar_wait_bounded(&fin, 0, err);
+    } else if (warp >= 2) {
+        // ---- epilogue.  Warps 2..9 serve slot 0 and 10..17 slot 1; in a slot, warps e and
+        // e + 4 share TMEM lane quadrant warp % 4 and take the lower / upper 128 columns.
+        // At the output layer the lower half stores the outputs while the upper half stores
+        // the slot's next tile's features, computed a layer ahead (their global loads and
+        // sin / cos stay off the MMA thread's critical path).
+        const int e = warp - 2;
+        const int s = e >> 3, half = (e >> 2) & 1, quad = warp & 3;
+        const int rl = quad * 32 + lane;
+        const uint32_t tq = taddr + (static_cast<uint32_t>(quad * 32) << 16) + s * 256 + half * 128;
+        uint8_t *my_act = smem + s * kActBytes;
+        const bool vec_out = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+        // a warp's lanes publish their shared-memory writes to the tensor cores' (async)
+        // proxy, the warp converges (ordering the lanes' writes before lane 0), and lane 0
+        // arrives for the warp
+        auto release = [&]() {
+            tc_fence_before();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&act_ready[s]);
+        };
+        // The layer loop is unrolled and the column half is a compile-time constant, so
+        // every bias is a fixed offset into the kernel's constant bank (an FADD operand,
+        // no load instruction).
+        auto run = [&](auto half_c) {
+            constexpr int HALF = decltype(half_c)::value;
+            Feat f{};
+            if (s < T) {
+                if (HALF) store_features(my_act, rl, features_of(tile_row0(s) + rl, q, B));
+                release();
+                if (HALF && s + 2 < T) f = features_of(tile_row0(s + 2) + rl, q, B);
             }
-        } else {
-            for (int c0 = 0; c0 < kOutPad; c0 += 16) {
-                float v[16];
-                tmem_ld16(taddr + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
-                if (r < B) {
+            uint32_t accn = 0;
+            bool ok = true;
+            for (int i = s; i < T && ok; i += 2) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (c0 + i < kOut) out[static_cast<int64_t>(r) * kOut + c0 + i] = v[i] + a.b[l][c0 + i];
+                for (int l = 0; l < kLayers; ++l) {
+                    if (!(ok = mbar_wait_bounded(&acc_full[s], accn++ & 1, err))) break;
+                    tc_fence_after();
+                    if (l < kLayers - 1) {
+#pragma unroll
+                        for (int c0 = 0; c0 < 128; c0 += 64) {
+                            uint32_t r[64];
+                            tmem_ld64(tq + c0, r);
+#pragma unroll
+                            for (int h = 0; h < 8; ++h) {
+                                const int col = HALF * 128 + c0 + 8 * h;
+                                const float *bc = a.bias[l] + col;
+                                uint4 o;
+                                o.x = relu_bf16x2(__uint_as_float(r[8 * h + 0]) + bc[0], __uint_as_float(r[8 * h + 1]) + bc[1]);
+                                o.y = relu_bf16x2(__uint_as_float(r[8 * h + 2]) + bc[2], __uint_as_float(r[8 * h + 3]) + bc[3]);
+                                o.z = relu_bf16x2(__uint_as_float(r[8 * h + 4]) + bc[4], __uint_as_float(r[8 * h + 5]) + bc[5]);
+                                o.w = relu_bf16x2(__uint_as_float(r[8 * h + 6]) + bc[6], __uint_as_float(r[8 * h + 7]) + bc[7]);
+                                const int base = ((rl >> 3) * (kHidden / 8) + (col >> 3)) * 128 + (rl & 7) * 16;
+                                *reinterpret_cast<uint4 *>(my_act + base) = o;
+                            }
+                        }
+                    } else {
+                        if (!HALF) {
+                            uint32_t r[32];
+                            tmem_ld32(tq, r);
+                            const int row = tile_row0(i) + rl;
+                            float v[kOut];
+#pragma unroll
+                            for (int j = 0; j < kOut; ++j) v[j] = __uint_as_float(r[j]) + a.bias_out[j];
+                            if (row < B) {
+                                float *o = out + static_cast<int64_t>(row) * kOut;
+                                if (vec_out) {
+#pragma unroll
+                                    for (int j = 0; j < kOut / 4; ++j)
+                                        reinterpret_cast<float4 *>(o)[j] =
+                                            make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                                } else {
+#pragma unroll
+                                    for (int j = 0; j < kOut; ++j) o[j] = v[j];
+                                }
+                            }
+                        }
+                        if (i + 2 >= T) break;   // this slot has no further tile
+                        if (HALF) store_features(my_act, rl, f);
+                    }
+                    release();
+                    if (l == kLayers - 1 && HALF && i + 4 < T) f = features_of(tile_row0(i + 4) + rl, q, B);
                 }
             }
-        }
-        tc_fence_before();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        tc_fence_after();
+        };
+        if (half)
+            run(std::integral_constant<int, 1>{});
+        else
+            run(std::integral_constant<int, 0>{});
     }
-    cp_async_wait_0();
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(taddr, 256);
+    tc_fence_after();
+    if (warp == 0) {
+        __syncwarp();
+        tmem_dealloc(taddr, 512);
+    }
 }
 
 }  // namespace mlpk
@@ -483,6 +703,10 @@ struct vedt_mlp {
     int64_t offW[kLayers], offB[kLayers];
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // fp32 padded
     bf16 *wb[kLayers] = {}, *wt[kLayers] = {};
+    uint8_t *wimg = nullptr;     // packed weight chunk images of the fused forward
+    FusedArgs fused{};           // fused-forward arguments, biases copied from p
+    bool fused_valid = false;    // fused.bias matches the device parameters
+    int sms = 1;                 // SM count
     bf16 *x0 = nullptr;          // [cap][16]
     bf16 *act[kLayers - 1] = {}; // [cap][256]
     float *out = nullptr;        // [cap][32]
@@ -557,6 +781,9 @@ vedt_status refresh_bf16(vedt_mlp *n) {
         k_to_bf16<<<(N * K + 255) / 256, 256, 0, n->stream>>>(n->p + n->offW[l], N, K, n->wb[l], n->wt[l]);
         MCHECK(cudaGetLastError());
     }
+    k_pack_w<<<(kWImageBytes / 16 + 255) / 256, 256, 0, n->stream>>>(n->wb[0], n->wb[1], n->wb[2], n->wb[3], n->wb[4],
+                                                                     n->wimg);
+    MCHECK(cudaGetLastError());
     return VEDT_OK;
 }
 
@@ -624,6 +851,7 @@ void free_mlp(vedt_mlp *n) {
         cudaFree(n->wb[l]);
         cudaFree(n->wt[l]);
     }
+    cudaFree(n->wimg);
     cudaFree(n->x0);
     for (int l = 0; l < kLayers - 1; ++l) cudaFree(n->act[l]);
     cudaFree(n->out);
@@ -637,6 +865,13 @@ void free_mlp(vedt_mlp *n) {
 }
 
 bool check_rows(const vedt_mlp *n, int B) { return n && B >= 1 && B <= n->cap; }
+
+// persistent grid: one CTA per SM, capped by the number of 128-row tiles
+cudaError_t launch_fused(const vedt_mlp *n, const float *q, int B, const FusedArgs &a, float *out) {
+    const int tiles = (B + 127) / 128;
+    k_mlp_fused<<<std::min(tiles, n->sms), kFusedThreads, kFusedSmem, n->stream>>>(q, B, a, out, n->err);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -665,6 +900,13 @@ vedt_status vedt_mlp_create(int batch_capacity, void *stream, vedt_mlp **out) {
         e = cudaMalloc(&n->wb[l], sizeof(bf16) * layer_n(l) * layer_k(l));
         if (e == cudaSuccess) e = cudaMalloc(&n->wt[l], sizeof(bf16) * layer_n(l) * layer_k(l));
     }
+    if (e == cudaSuccess) e = cudaMalloc(&n->wimg, kWImageBytes);
+    if (e == cudaSuccess) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
     if (e == cudaSuccess) e = cudaMalloc(&n->x0, sizeof(bf16) * cap * kInPad);
     for (int l = 0; l < kLayers - 1 && e == cudaSuccess; ++l) e = cudaMalloc(&n->act[l], sizeof(bf16) * cap * kHidden);
     if (e == cudaSuccess) e = cudaMalloc(&n->out, sizeof(float) * cap * kOutPad);
@@ -711,6 +953,7 @@ vedt_status vedt_mlp_set_params(vedt_mlp *n, const float *params, int64_t count)
     MCHECK(cudaMemsetAsync(n->m, 0, sizeof(float) * n->np, n->stream));
     MCHECK(cudaMemsetAsync(n->v, 0, sizeof(float) * n->np, n->stream));
     n->step = 0;
+    n->fused_valid = false;
     vedt_status st = refresh_bf16(n);
     if (st != VEDT_OK) return st;
     MCHECK(cudaStreamSynchronize(n->stream));
@@ -739,14 +982,17 @@ vedt_status vedt_mlp_get_params(vedt_mlp *n, float *params, int64_t count) {
 
 vedt_status vedt_mlp_forward(vedt_mlp *n, const float *q_dev, int B, float *out_dev) {
     if (!check_rows(n, B) || !q_dev || !out_dev) return VEDT_EINVAL;
-    FusedArgs a{};
-    for (int l = 0; l < kLayers; ++l) {
-        a.w[l] = n->wb[l];
-        a.b[l] = n->p + n->offB[l];
+    if (!n->fused_valid) {   // parameters changed on the device (training): fetch the biases once
+        for (int l = 0; l < kLayers - 1; ++l)
+            MCHECK(cudaMemcpyAsync(n->fused.bias[l], n->p + n->offB[l], sizeof(float) * kHidden, cudaMemcpyDeviceToHost,
+                                   n->stream));
+        MCHECK(cudaMemcpyAsync(n->fused.bias_out, n->p + n->offB[kLayers - 1], sizeof(float) * kOutPad,
+                               cudaMemcpyDeviceToHost, n->stream));
+        MCHECK(cudaStreamSynchronize(n->stream));
+        n->fused.wimg = n->wimg;
+        n->fused_valid = true;
     }
-    MCHECK(cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem));
-    k_mlp_fused<<<(B + 127) / 128, kThreads, kFusedSmem, n->stream>>>(q_dev, B, a, out_dev, n->err);
-    MCHECK(cudaGetLastError());
+    MCHECK(launch_fused(n, q_dev, B, n->fused, out_dev));
     return VEDT_OK;
 }
 
@@ -789,6 +1035,7 @@ vedt_status vedt_mlp_train_step(vedt_mlp *n, const float *q_dev, const float *y_
     if (st == VEDT_OK) st = backward(n, y_dev, mask_dev, B, rows);
     if (st != VEDT_OK) return st;
     n->step += 1;
+    n->fused_valid = false;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - std::pow(b1, static_cast<float>(n->step));
     const float c2 = 1.f - std::pow(b2, static_cast<float>(n->step));

@@ -130,3 +130,48 @@ def test_fused_forward_matches_layer_path(B):
     ref = ref_forward_bf16(theta.astype(np.float32).astype(np.float64), q.cpu().numpy().astype(np.float64))
     assert rel(an, ref) < 1e-2
     net.close()
+
+
+@pytest.mark.parametrize("B", [1, 129, 300, 40000, 65536 + 77])
+def test_fused_forward_ragged_batches(B):
+    """Batches that leave a partial last tile, an odd number of tiles per CTA or fewer
+    tiles than SMs: outputs match the per-layer path and rows past B stay untouched."""
+    v = lib()
+    rng = np.random.default_rng(100 + B)
+    theta = omlp.init_params(4) + rng.normal(scale=0.02, size=omlp.n_params())
+    net = _net(v, B, theta)
+    q = torch.from_numpy(rng.uniform(-np.pi, np.pi, size=(B, 7)).astype(np.float32)).cuda()
+    got = torch.full((B + 1, 24), 7.0, device="cuda")
+    net.forward(q, got)
+    net.check()
+    assert bool((got[B] == 7.0).all())
+    lay = torch.zeros((B, 24), device="cuda")
+    net.forward_layers(q, lay)
+    assert rel(got[:B].cpu().numpy().astype(np.float64), lay.cpu().numpy().astype(np.float64)) < 2e-3
+    again = torch.zeros((B, 24), device="cuda")
+    net.forward(q, again)
+    assert torch.equal(again, got[:B])      # deterministic
+    net.close()
+
+
+def test_fused_forward_follows_training_updates():
+    """After AdamW steps change the parameters on the device, the fused forward uses the
+    new weights and biases (it agrees with the per-layer path that reads them directly)."""
+    v = lib()
+    B = 4096
+    rng = np.random.default_rng(21)
+    net = _net(v, B, omlp.init_params(12))
+    q = torch.from_numpy(rng.uniform(-np.pi, np.pi, size=(B, 7)).astype(np.float32)).cuda()
+    y = torch.from_numpy(rng.uniform(0.1, 0.5, size=(B, 24)).astype(np.float32)).cuda()
+    before = torch.zeros((B, 24), device="cuda")
+    net.forward(q, before)
+    for _ in range(20):
+        net.train_step(q, y, None, lr=1e-2, wd=0.0)
+    got = torch.zeros((B, 24), device="cuda")
+    lay = torch.zeros((B, 24), device="cuda")
+    net.forward(q, got)
+    net.forward_layers(q, lay)
+    net.check()
+    assert not torch.equal(got, before)
+    assert rel(got.cpu().numpy().astype(np.float64), lay.cpu().numpy().astype(np.float64)) < 2e-3
+    net.close()
