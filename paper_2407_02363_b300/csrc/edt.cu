@@ -330,6 +330,635 @@ __device__ __forceinline__ void envelope_two_warps(int n, int tid, typename Env<
     query_merged<SMALL>(M, lo, hi, upper, L, emit);
 }
 
+// ====================================================================================
+// Small mode (every dim <= 256): lean passes.
+//
+// Pass X: one warp per row, lane l owning voxels [8l, 8l + 8).  The row's occupancy
+// becomes one 8-bit mask per lane; a ballot of the non-empty segments and two shuffles
+// give every lane the nearest occupied x left and right of its segment.  A segment with
+// no site splits at the midpoint of those two; a segment with sites takes two register
+// sweeps.  Rows without a site only clear their flag (pass Y never reads their sites).
+//
+// Passes Y and Z: one 64-thread CTA per 32 columns of a line family; warp b owns band b
+// (the lower or upper half of every line), lane l column x0 + l.  The valid positions of
+// a band (rows / slices holding a site, the same for every column) are ballot bitmasks,
+// so the sweep visits only them, uniformly across the warp.  A band's stack of proximate
+// sites lives in place: entry k keeps its staged input word in slot lo + k of the tile
+// (a slot the sweep has already read) and its position in pos[k][tid], so a pop, the
+// junction merge and the query read both words directly.
+// ====================================================================================
+__device__ __forceinline__ uint32_t nz_nibble(uint32_t w) {
+    // bit i = (byte i != 0): set bit 7 of every non-zero byte, then gather bits 7, 15,
+    // 23, 31 into bits 28..31 with one multiply (the partial products never overlap)
+    const uint32_t t = (((w & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u;
+    return (t * 0x00204081u) >> 28;
+}
+
+// occupancy bytes [x0, x0 + 8) of a row, zero beyond X
+__device__ __forceinline__ uint2 row_bytes8(const uint8_t *row, int X, int x0, bool vec) {
+    if (vec) return x0 < X ? __ldcs(reinterpret_cast<const uint2 *>(row + x0)) : make_uint2(0u, 0u);
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int x = x0 + i;
+        const uint32_t b = x < X ? (row[x] != 0) : 0u;
+        if (i < 4) lo |= b << (8 * i);
+        else hi |= b << (8 * (i - 4));
+    }
+    return make_uint2(lo, hi);
+}
+
+__device__ __forceinline__ void pass_x_small_row(const GridDesc &G, int64_t lr, int lane, uint2 w) {
+    constexpr int kNoLeft = -1024, kNoRight = 2048;
+    const uint32_t m = nz_nibble(w.x) | (nz_nibble(w.y) << 4);
+    const uint32_t B = __ballot_sync(0xffffffffu, m != 0);
+    if (B == 0) {
+        if (lane == 0) G.row_has[lr] = 0;
+        return;
+    }
+    const int x0 = 8 * lane;
+    const uint32_t below = B & ((1u << lane) - 1u);
+    const uint32_t above = B & ~((2u << lane) - 1u);
+    const int lastp = x0 + 31 - __clz(m);
+    const int firstp = x0 + __ffs(m) - 1;
+    int L = __shfl_sync(0xffffffffu, lastp, (31 - __clz(below)) & 31);
+    int R = __shfl_sync(0xffffffffu, firstp, (__ffs(above) - 1) & 31);
+    if (!below) L = kNoLeft;
+    if (!above) R = kNoRight;
+    uint32_t lo32, hi32;
+    if (m == 0) {
+        // voxels x <= floor((L + R) / 2) take L (ties go left), the rest R
+        int nl = ((L + R) >> 1) - x0 + 1;
+        nl = min(max(nl, 0), 8);
+        const uint32_t rl = static_cast<uint32_t>(L & 0xFF) * 0x01010101u;
+        const uint32_t rr = static_cast<uint32_t>(R & 0xFF) * 0x01010101u;
+        const uint32_t ml = nl >= 4 ? 0xFFFFFFFFu : ((1u << (8 * nl)) - 1u);
+        const uint32_t mh = nl >= 8 ? 0xFFFFFFFFu : (nl <= 4 ? 0u : ((1u << (8 * (nl - 4))) - 1u));
+        lo32 = (rl & ml) | (rr & ~ml);
+        hi32 = (rl & mh) | (rr & ~mh);
+    } else {
+        int left[8], best[8];
+        int cur = L;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if ((m >> i) & 1u) cur = x0 + i;
+            left[i] = cur;
+        }
+        cur = R;
+#pragma unroll
+        for (int i = 7; i >= 0; --i) {
+            if ((m >> i) & 1u) cur = x0 + i;
+            best[i] = (2 * (x0 + i) <= left[i] + cur) ? left[i] : cur;
+        }
+        lo32 = __byte_perm(__byte_perm(best[0], best[1], 0x0040), __byte_perm(best[2], best[3], 0x0040), 0x5410);
+        hi32 = __byte_perm(__byte_perm(best[4], best[5], 0x0040), __byte_perm(best[6], best[7], 0x0040), 0x5410);
+    }
+    if (x0 < G.Xp) *reinterpret_cast<uint2 *>(static_cast<uint8_t *>(G.xs) + lr * G.Xp + x0) = make_uint2(lo32, hi32);
+    if (lane == 0) G.row_has[lr] = 1;
+}
+
+// Grid-stride over rows with the next row's bytes loaded before the current row is
+// processed, so every warp keeps two rows in flight.
+__global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict__ gd, int ng, int64_t rows_total) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (r >= rows_total) return;
+    int g = 0;
+    while (g + 1 < ng && gd[g + 1].row_begin <= r) ++g;
+    auto load = [&](int gg, int64_t rr) {
+        const GridDesc &G = gd[gg];
+        const bool vec = (G.X & 7) == 0 && (reinterpret_cast<uintptr_t>(G.occ) & 7) == 0;
+        return row_bytes8(G.occ + (rr - G.row_begin) * G.X, G.X, 8 * lane, vec);
+    };
+    uint2 w = load(g, r);
+    for (;;) {
+        const int64_t rn = r + nwarps;
+        int gn = g;
+        uint2 wn = make_uint2(0u, 0u);
+        if (rn < rows_total) {
+            while (gn + 1 < ng && gd[gn + 1].row_begin <= rn) ++gn;
+            wn = load(gn, rn);
+        }
+        pass_x_small_row(gd[g], r - gd[g].row_begin, lane, w);
+        if (rn >= rows_total) break;
+        r = rn;
+        g = gn;
+        w = wn;
+    }
+}
+
+// in[] element of a staged tile; h(raw, p) = f(p) + p^2 for the site word raw at p
+struct PolY {
+    using In = uint8_t;   // pass-X site x' of row p
+    int x;
+    __device__ __forceinline__ int h(uint32_t r, int p) const {
+        const int d = x - static_cast<int>(r);
+        return d * d + p * p;
+    }
+};
+
+struct PolZ {
+    using In = uint16_t;  // pass-Y 2-D site x' | y' << 8 of slice p
+    int x, y;
+    __device__ __forceinline__ int h(uint32_t r, int p) const {
+        const int dx = x - static_cast<int>(r & 0xFFu), dy = y - static_cast<int>(r >> 8);
+        return dx * dx + dy * dy + p * p;
+    }
+};
+
+// Banded line geometry of a small-mode tile: NB warps, warp b owns band
+// [b * bl, min(n, (b + 1) * bl)) of every line, bl = ceil(n / NB).
+template <int NB>
+struct Bands {
+    static constexpr int kWords = (kSmallMax / NB + 31) / 32;   // valid-mask words per band
+    static __host__ __device__ constexpr int len(int n) { return (n + NB - 1) / NB; }
+};
+
+// b dropped between a and c (positions a < b < c, h = f + p^2): c overtakes b no later
+// than b overtakes a.  All products stay below 2^31 in small mode.
+__device__ __forceinline__ bool dominated(int ca, int ha, int cb, int hb, int cc, int hc) {
+    return (hc - hb) * (cb - ca) <= (hb - ha) * (cc - cb);
+}
+
+// Stack of proximate sites of one band (Steps 2 and 4) over its valid positions
+// lo + 32 w + (bit of vm[w]), ascending.  `col` = this column's input (stride kCols), the
+// stack's input words are written back in place from slot lo; `mypos` = this thread's
+// position stack (stride NB * 32).
+template <int NB, class P>
+__device__ __forceinline__ int small_build(const P &pol, typename P::In *col, uint8_t *mypos, int lo,
+                                           const uint32_t (&vm)[Bands<NB>::kWords]) {
+    constexpr int kS = NB * kTile;
+    int k = 0, a = 0, b = 0, ha = 0, hb = 0, dab = 0, wab = 0;
+    auto step = [&](int c) {
+        const uint32_t r = col[c * kCols];
+        const int hc = pol.h(r, c);
+        while (k >= 2 && (hc - hb) * wab <= dab * (c - b)) {
+            --k;
+            b = a;
+            hb = ha;
+            if (k >= 2) {
+                a = mypos[(k - 2) * kS];
+                ha = pol.h(col[(lo + k - 2) * kCols], a);
+                dab = hb - ha;
+                wab = b - a;
+            }
+        }
+        col[(lo + k) * kCols] = static_cast<typename P::In>(r);
+        mypos[k * kS] = static_cast<uint8_t>(c);
+        dab = hc - hb;
+        wab = c - b;
+        a = b;
+        ha = hb;
+        b = c;
+        hb = hc;
+        ++k;
+    };
+#pragma unroll
+    for (int w = 0; w < Bands<NB>::kWords; ++w) {
+        uint32_t bits = vm[w];
+        const int base = lo + 32 * w;
+        if (bits == 0xFFFFFFFFu) {   // a run of 32 valid positions (warp-uniform)
+#pragma unroll 2
+            for (int c = base; c < base + 32; ++c) step(c);
+        } else {
+            while (bits) {
+                const int c = base + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                step(c);
+            }
+        }
+    }
+    return k;
+}
+
+// a[b] for a band index known only at run time (selects; no local memory)
+template <int NB>
+__device__ __forceinline__ int pick(const int (&a)[NB], int b) {
+    int v = a[0];
+#pragma unroll
+    for (int u = 1; u < NB; ++u)
+        if (b == u) v = a[u];
+    return v;
+}
+
+// Merged envelope of a line's NB bands: band b keeps its stack entries j[b]..i[b] (none
+// if j[b] > i[b]); the envelope is their concatenation in band order.
+template <int NB, class P>
+struct SmallMerged {
+    typename P::In *in;         // this column's slots (stride kCols)
+    const uint8_t *pos;         // this column's band-0 positions (stride NB * 32)
+    int bl;                     // band length
+    int j[NB], i[NB];
+    int last;                   // last non-empty band
+    __device__ __forceinline__ void at(int b, int t, int &c, uint32_t &r) const {
+        c = pos[t * (NB * kTile) + b * kTile];
+        r = in[(b * bl + t) * kCols];
+    }
+    // largest non-empty band below b, or -1
+    __device__ __forceinline__ int prev_band(int b) const {
+        int s = -1;
+#pragma unroll
+        for (int u = 0; u < NB; ++u)
+            if (u < b && j[u] <= i[u]) s = u;
+        return s;
+    }
+    // smallest non-empty band above b, or -1
+    __device__ __forceinline__ int next_band(int b) const {
+        int s = -1;
+#pragma unroll
+        for (int u = NB - 1; u >= 0; --u)
+            if (u > b && j[u] <= i[u]) s = u;
+        return s;
+    }
+    // Bands are joined left to right by the junction repair: the current top T is
+    // popped while the entry S below it and the next band's first entry F dominate it,
+    // and F is dropped while T and the entry G above F dominate it.  The four entries'
+    // positions and h stay in registers, so each step loads one new entry.
+    // entry below (sb, si + 1): (sb, si) itself if inside band sb's kept range, else the
+    // top of the nearest earlier non-empty band; sb = -1 if there is none
+    __device__ __forceinline__ void below(int &sb, int &si) const {
+        if (si < pick<NB>(j, sb)) {
+            sb = prev_band(sb);
+            si = sb >= 0 ? pick<NB>(i, sb) : 0;
+        }
+    }
+    __device__ __forceinline__ int hat(const P &pol, int b, int t, int &c) const {
+        uint32_t r;
+        at(b, t, c, r);
+        return pol.h(r, c);
+    }
+    __device__ __forceinline__ void merge(const P &pol, const int (&k)[NB]) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            j[b] = 0;
+            i[b] = k[b] - 1;
+        }
+        int tb = -1;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (k[b] == 0) continue;
+            if (tb >= 0) {
+                int jb = 0;
+                const int ib = k[b] - 1;
+                for (;;) {
+                    const int ti = pick<NB>(i, tb), tj = pick<NB>(j, tb);
+                    int sb = tb, si = ti - 1;
+                    if (si < tj) {
+                        sb = prev_band(tb);
+                        si = sb >= 0 ? pick<NB>(i, sb) : 0;
+                    }
+                    int ca, cb, cc;
+                    uint32_t ra, rb, rc;
+                    at(tb, ti, cb, rb);
+                    at(b, jb, cc, rc);
+                    const int hb = pol.h(rb, cb), hc = pol.h(rc, cc);
+                    if (sb >= 0) {
+                        at(sb, si, ca, ra);
+                        if (dominated(ca, pol.h(ra, ca), cb, hb, cc, hc)) {
+                            // pop the top; an emptied band hands the top to the band below
+#pragma unroll
+                            for (int u = 0; u < NB; ++u)
+                                if (u == tb) i[u] = ti - 1;
+                            if (ti - 1 < tj) tb = sb;
+                            continue;
+                        }
+                    }
+                    if (jb + 1 <= ib) {
+                        at(b, jb + 1, ca, ra);
+                        if (dominated(cb, hb, cc, hc, ca, pol.h(ra, ca))) {
+                            ++jb;
+                            continue;
+                        }
+                    }
+                    break;
+                }
+                j[b] = jb;
+            }
+            tb = b;   // a band's last entry can only be dropped by a later band
+        }
+        last = tb;
+    }
+    // last non-empty band from the ranges
+    __device__ __forceinline__ void find_last() {
+        last = -1;
+#pragma unroll
+        for (int u = 0; u < NB; ++u)
+            if (j[u] <= i[u]) last = u;
+    }
+};
+
+// Cursor over the merged envelope: entry (b, t) with its band's last kept index.
+template <int NB, class P>
+struct Cursor {
+    int b, t, tend;
+    __device__ __forceinline__ void set(const SmallMerged<NB, P> &M, int bb, int tt) {
+        b = bb;
+        t = tt;
+        tend = pick<NB>(M.i, bb);
+    }
+    // next entry; false at the end of the envelope
+    __device__ __forceinline__ bool next(const SmallMerged<NB, P> &M) {
+        if (t < tend) {
+            ++t;
+            return true;
+        }
+        const int nb = M.next_band(b);
+        if (nb < 0) return false;
+        set(M, nb, pick<NB>(M.j, nb));
+        return true;
+    }
+};
+
+// Walks the merged envelope over voxels [lo, hi) of band `band`: emit.start(j, c, raw, h)
+// whenever the nearest proximate site changes (and at lo), emit.put() once per voxel.
+// Entry q+1 is strictly nearer to voxel j iff h1 - h0 < 2 j (c1 - c0), ties keeping the
+// lower site.  The walk starts at the band's first entry (or the next band's), steps down
+// while the entry below is no worse at lo (the values at lo are unimodal along the
+// envelope), then moves up as the voxels advance, one entry ahead.
+template <int NB, class P, class E>
+__device__ __forceinline__ void small_query(const P &pol, const SmallMerged<NB, P> &M, int lo, int hi, int band,
+                                            E &emit) {
+    if (lo >= hi) return;
+    int cb = (M.j[0] <= M.i[0] && band == 0) ? 0 : -1;
+    if (cb < 0) cb = (pick<NB>(M.j, band) <= pick<NB>(M.i, band)) ? band : M.next_band(band);
+    Cursor<NB, P> cur;
+    if (cb < 0) cur.set(M, M.last, pick<NB>(M.i, M.last));
+    else cur.set(M, cb, pick<NB>(M.j, cb));
+    int c0;
+    uint32_t r0;
+    M.at(cur.b, cur.t, c0, r0);
+    int h0 = pol.h(r0, c0);
+    for (;;) {
+        int pb = cur.b, pt = cur.t - 1;
+        if (pt < pick<NB>(M.j, cur.b)) {
+            pb = M.prev_band(cur.b);
+            if (pb < 0) break;
+            pt = pick<NB>(M.i, pb);
+        }
+        int c;
+        uint32_t r;
+        M.at(pb, pt, c, r);
+        const int hb = pol.h(r, c);
+        if (hb - 2 * lo * c > h0 - 2 * lo * c0) break;
+        cur.set(M, pb, pt);
+        c0 = c;
+        r0 = r;
+        h0 = hb;
+    }
+    Cursor<NB, P> nxt = cur;
+    int c1 = 0, h1 = 0, dc2 = 0, dh = INT_MAX;
+    uint32_t r1 = 0;
+    auto fetch = [&]() {
+        if (nxt.next(M)) {
+            M.at(nxt.b, nxt.t, c1, r1);
+            h1 = pol.h(r1, c1);
+            dc2 = 2 * (c1 - c0);
+            dh = h1 - h0;
+        } else {
+            dh = INT_MAX;
+            dc2 = 0;
+        }
+    };
+    fetch();
+    int thr = lo * dc2;
+    emit.start(lo, c0, r0, h0);
+    for (int j = lo; j < hi; ++j) {
+        if (dh < thr) {
+            do {
+                c0 = c1;
+                r0 = r1;
+                h0 = h1;
+                fetch();
+                thr = j * dc2;
+            } while (dh < thr);
+            emit.start(j, c0, r0, h0);
+        }
+        emit.put();
+        thr += dc2;
+    }
+}
+
+__device__ __forceinline__ int align16(int n) { return (n + 15) & ~15; }
+
+// valid-position bitmask of band [lo, hi) from per-position flags (warp-uniform)
+template <int W>
+__device__ __forceinline__ void band_mask(const uint8_t *flags, int lo, int hi, int lane, uint32_t (&vm)[W]) {
+    uint8_t f[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int q = lo + 32 * w + lane;
+        f[w] = q < hi ? flags[q] : 0;
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) vm[w] = __ballot_sync(0xffffffffu, f[w] != 0);
+}
+
+struct EmitYs {
+    uint16_t *s2;
+    uint32_t off, Xp;
+    uint16_t v;
+    __device__ __forceinline__ void start(int, int c, uint32_t r, int) {
+        v = static_cast<uint16_t>(r | (static_cast<uint32_t>(c) << 8));
+    }
+    __device__ __forceinline__ void put() {
+        s2[off] = v;
+        off += Xp;
+    }
+};
+
+struct EmitZs {
+    int32_t *sq, *ix;
+    uint32_t off, plane;
+    int X, XY;
+    bool live;
+    int val, inc, id;
+    __device__ __forceinline__ void start(int j, int c, uint32_t r, int h) {
+        val = h - 2 * j * c + j * j;
+        inc = 2 * (j - c) + 1;
+        id = static_cast<int>(r & 0xFFu) + X * static_cast<int>(r >> 8) + XY * c;
+    }
+    __device__ __forceinline__ void put() {
+        if (live) {
+            sq[off] = val;
+            ix[off] = id;
+        }
+        off += plane;
+        val += inc;
+        inc += 2;
+    }
+};
+
+// shared memory of a small-mode tile: staged line tile, position stacks, stack sizes
+template <int NB>
+__host__ __device__ constexpr int small_smem(int n, int elem) {
+    return ((n * kCols * elem + 15) & ~15) + ((Bands<NB>::len(n) * NB * kTile + 15) & ~15) + NB * kTile * 4 +
+           2 * NB * kTile * 2;
+}
+
+constexpr int kNBY = 4;   // bands per line in the standalone small-mode passes
+constexpr int kNBZ = 4;
+
+// One small-mode envelope tile over the staged line tile `in` (n positions x 32 columns),
+// after the TMA load was issued: builds the bands, merges, walks.  `flags` = validity of
+// each position; `emit` starts at the thread's first voxel.  Returns the total stack
+// size of the column (0 iff no valid position), identical for every column.
+template <int NB, class P, class E>
+__device__ __forceinline__ int small_envelope(typename P::In *in, uint8_t *pos, int *ks, const uint8_t *flags,
+                                              int n, const P &pol, E &emit, uint64_t *bar, uint32_t phase,
+                                              int32_t *err, bool &ok) {
+    const int tid = threadIdx.x, lane = tid & (kTile - 1), band = tid >> 5;
+    const int bl = Bands<NB>::len(n);
+    const int lo = band * bl, hi = min(n, lo + bl);
+    uint32_t vm[Bands<NB>::kWords];
+    band_mask(flags, lo, hi, lane, vm);
+    ok = mbar_wait_bounded(bar, phase, err);
+    if (!ok) return 0;
+    const int k = small_build<NB>(pol, in + lane, pos + tid, lo, vm);
+    ks[tid] = k;
+    __syncthreads();
+    int total = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) total += ks[b * kTile + lane];
+    if (total == 0) return 0;   // the same for every column
+    SmallMerged<NB, P> M;
+    M.in = in + lane;
+    M.pos = pos + lane;
+    M.bl = bl;
+    int16_t *rng = reinterpret_cast<int16_t *>(ks + NB * kTile);   // [2][NB][32]
+    if (band == 0) {   // one merge per column, published to the other bands
+        int kk[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) kk[b] = ks[b * kTile + lane];
+        M.merge(pol, kk);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            rng[b * kTile + lane] = static_cast<int16_t>(M.j[b]);
+            rng[(NB + b) * kTile + lane] = static_cast<int16_t>(M.i[b]);
+        }
+    }
+    __syncthreads();
+    if (band != 0) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            M.j[b] = rng[b * kTile + lane];
+            M.i[b] = rng[(NB + b) * kTile + lane];
+        }
+        M.find_last();
+    }
+    small_query<NB>(pol, M, lo, hi, band, emit);
+    return total;
+}
+
+// One pass-Y tile (grid g, slice z, columns x0..x0+31) in small mode with NB * 32
+// threads.  Same contract as tile_y: `phase` is the barrier's current parity; ends with
+// a CTA barrier so the caller may reuse shared memory.
+template <int NB>
+__device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
+                                             int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
+                                             int32_t *err) {
+    const int tid = threadIdx.x, lane = tid & (kTile - 1);
+    const int Y = gd[g].Y, Xp = gd[g].Xp;
+    const int tiles_x = Xp / kCols;
+    const int z = static_cast<int>(lt / tiles_x);
+    const int x0 = static_cast<int>(lt % tiles_x) * kCols;
+    uint8_t *in = smem;                                                  // [Y][32]
+    uint8_t *pos = smem + align16(Y * kCols);                            // [bl][NB * 32]
+    int *ks = reinterpret_cast<int *>(pos + align16(Bands<NB>::len(Y) * NB * kTile));
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(Y * kCols));
+        tma_load_3d(in, &tm[2 * g], x0, 0, z, bar);
+    }
+    const int lo = (tid >> 5) * Bands<NB>::len(Y);
+    const PolY pol{x0 + lane};
+    EmitYs e{static_cast<uint16_t *>(gd[g].s2), static_cast<uint32_t>((z * Y + lo) * Xp + x0 + lane),
+             static_cast<uint32_t>(Xp), 0};
+    bool ok;
+    const int total = small_envelope<NB>(in, pos, ks, gd[g].row_has + static_cast<int64_t>(z) * Y, Y, pol, e, bar,
+                                         phase, err, ok);
+    if (!ok) {
+        drain_after_timeout(bar, phase);
+        __syncthreads();
+        return false;
+    }
+    // an empty slice (the same for every column) writes no sites: pass Z skips it
+    if (x0 == 0 && tid == 0) gd[g].slice_has[z] = total > 0 ? 1 : 0;
+    __syncthreads();
+    return true;
+}
+
+// One pass-Z tile (grid g, row y, columns x0..x0+31) in small mode with NB * 32 threads.
+template <int NB>
+__device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
+                                             int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
+                                             int32_t *err) {
+    const int tid = threadIdx.x, lane = tid & (kTile - 1);
+    const int X = gd[g].X, Y = gd[g].Y, Z = gd[g].Z, Xp = gd[g].Xp;
+    const int tiles_x = Xp / kCols;
+    const int y = static_cast<int>(lt / tiles_x);
+    const int x0 = static_cast<int>(lt % tiles_x) * kCols;
+    uint16_t *in = reinterpret_cast<uint16_t *>(smem);                   // [Z][32]
+    uint8_t *pos = smem + align16(Z * kCols * 2);                        // [bl][NB * 32]
+    int *ks = reinterpret_cast<int *>(pos + align16(Bands<NB>::len(Z) * NB * kTile));
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(Z * kCols * 2));
+        tma_load_3d(in, &tm[2 * g + 1], x0, y, 0, bar);
+    }
+    const int bl = Bands<NB>::len(Z);
+    const int lo = (tid >> 5) * bl, hi = min(Z, lo + bl);
+    const int x = x0 + lane;
+    const bool live = x < X;
+    const uint32_t plane = static_cast<uint32_t>(X * Y);
+    const PolZ pol{x, y};
+    EmitZs e{gd[g].sqdist, gd[g].idx,
+             static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(y * X + (live ? x : 0)), plane, X, X * Y, live,
+             0, 0, 0};
+    bool ok;
+    const int total = small_envelope<NB>(in, pos, ks, gd[g].slice_has, Z, pol, e, bar, phase, err, ok);
+    if (!ok) {
+        drain_after_timeout(bar, phase);
+        __syncthreads();
+        return false;
+    }
+    if (total == 0) {   // empty grid
+        for (int j = lo; j < hi; ++j) {
+            if (live) {
+                e.sq[e.off] = INT_MAX;
+                e.ix[e.off] = -1;
+            }
+            e.off += plane;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(NB * kTile) k_pass_y_small(const GridDesc *__restrict__ gd,
+                                                             const CUtensorMap *__restrict__ tm, int ng,
+                                                             int32_t *err) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ uint64_t bar;
+    const int64_t t = blockIdx.x;
+    const int g = find_grid(gd, ng, t, 0);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    tile_y_small<NB>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, 0, err);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(NB * kTile) k_pass_z_small(const GridDesc *__restrict__ gd,
+                                                             const CUtensorMap *__restrict__ tm, int ng,
+                                                             int32_t *err) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ uint64_t bar;
+    const int64_t t = blockIdx.x;
+    const int g = find_grid(gd, ng, t, 1);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    tile_z_small<NB>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, 0, err);
+}
+
 // ------------------------------------------------------------------------------------
 // pass Y: tile = (grid, slice z, 16 columns x0..x0+15), line along y
 // ------------------------------------------------------------------------------------
@@ -365,8 +994,9 @@ struct EmitY {
 // barrier's current phase; the barrier must have been initialised.  Returns false if
 // the staging wait timed out.  Ends with a CTA barrier so the caller may reuse smem.
 template <bool SMALL>
-__device__ __forceinline__ bool tile_y(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
-                                       int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
+__device__ __forceinline__ bool tile_y_generic(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
+                                               int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
+                                               int32_t *err) {
     using E = Env<SMALL>;
     using Link = typename E::Link;
     using XS = typename E::XS;
@@ -412,9 +1042,16 @@ __device__ __forceinline__ bool tile_y(const GridDesc *__restrict__ gd, const CU
 }
 
 template <bool SMALL>
+__device__ __forceinline__ bool tile_y(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
+                                       int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
+    if constexpr (SMALL) return tile_y_small<2>(gd, tm, g, lt, smem, bar, phase, err);
+    else return tile_y_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
+}
+
+template <bool SMALL>
 __global__ void __launch_bounds__(kLanes) k_pass_y(const GridDesc *__restrict__ gd,
                                                    const CUtensorMap *__restrict__ tm, int ng, int32_t *err) {
-    extern __shared__ __align__(1024) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint64_t bar;
     const int64_t t = blockIdx.x;
     const int g = find_grid(gd, ng, t, 0);
@@ -461,8 +1098,9 @@ struct EmitZ {
 };
 
 template <bool SMALL>
-__device__ __forceinline__ bool tile_z(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
-                                       int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
+__device__ __forceinline__ bool tile_z_generic(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
+                                               int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
+                                               int32_t *err) {
     using E = Env<SMALL>;
     using Link = typename E::Link;
     using Site = typename E::Site;
@@ -507,9 +1145,16 @@ __device__ __forceinline__ bool tile_z(const GridDesc *__restrict__ gd, const CU
 }
 
 template <bool SMALL>
+__device__ __forceinline__ bool tile_z(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
+                                       int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
+    if constexpr (SMALL) return tile_z_small<2>(gd, tm, g, lt, smem, bar, phase, err);
+    else return tile_z_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
+}
+
+template <bool SMALL>
 __global__ void __launch_bounds__(kLanes) k_pass_z(const GridDesc *__restrict__ gd,
                                                    const CUtensorMap *__restrict__ tm, int ng, int32_t *err) {
-    extern __shared__ __align__(1024) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint64_t bar;
     const int64_t t = blockIdx.x;
     const int g = find_grid(gd, ng, t, 1);
@@ -557,7 +1202,7 @@ template <int S, bool SMALL>
 __global__ void __launch_bounds__(kLanes) k_edt_persistent(const GridDesc *__restrict__ gd,
                                                            const CUtensorMap *__restrict__ tm, int ng,
                                                            PersistCounters cnt, int rows_per_item, int32_t *err) {
-    extern __shared__ __align__(1024) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint64_t bar;
     __shared__ unsigned item_s;
     __shared__ int ok_s;
@@ -583,7 +1228,15 @@ __global__ void __launch_bounds__(kLanes) k_edt_persistent(const GridDesc *__res
             const int64_t rows = static_cast<int64_t>(gd[g].Y) * gd[g].Z;
             const int64_t r0 = static_cast<int64_t>(it - gd[g].xi_begin) * rows_per_item;
             const int64_t r1 = min(rows, r0 + rows_per_item);
-            for (int64_t r = r0 + warp; r < r1; r += kLanes / 32) pass_x_row<S, SMALL>(gd[g], r, lane);
+            for (int64_t r = r0 + warp; r < r1; r += kLanes / 32) {
+                if constexpr (SMALL) {
+                    const GridDesc &G = gd[g];
+                    const bool vec = (G.X & 7) == 0 && (reinterpret_cast<uintptr_t>(G.occ) & 7) == 0;
+                    pass_x_small_row(G, r, lane, row_bytes8(G.occ + r * G.X, G.X, 8 * lane, vec));
+                } else {
+                    pass_x_row<S, SMALL>(gd[g], r, lane);
+                }
+            }
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
@@ -637,6 +1290,7 @@ static int sm_count() {
 }
 
 static size_t smem_y(const GridTable &t) {
+    if (!t.large) return static_cast<size_t>(small_smem<2>(t.maxY, 1));
     const int by = t.maxY > kBox ? kBox : t.maxY;
     const size_t rows = static_cast<size_t>((t.maxY + by - 1) / by) * by;
     const size_t xs = t.large ? 2 : 1, link = t.large ? 2 : 1;
@@ -644,6 +1298,7 @@ static size_t smem_y(const GridTable &t) {
 }
 
 static size_t smem_z(const GridTable &t) {
+    if (!t.large) return static_cast<size_t>(small_smem<2>(t.maxZ, 2));
     const int bz = t.maxZ > kBox ? kBox : t.maxZ;
     const size_t rows = static_cast<size_t>((t.maxZ + bz - 1) / bz) * bz;
     const size_t site = t.large ? 4 : 2, link = t.large ? 2 : 1;
@@ -656,7 +1311,17 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s) {
     const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
     const int blocks = static_cast<int>(want < cap ? want : cap);
     if (!t.large) {
-        k_pass_x<8, true><<<blocks, 256, 0, s>>>(t.desc, t.n, t.rows);
+        // one resident wave of warps, each keeping two rows in flight
+        static int per_sm = 0;
+        if (per_sm == 0) {
+            int occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass_x_small, 256, 0) != cudaSuccess || occ < 1)
+                occ = 1;
+            per_sm = occ;
+        }
+        const int64_t cap_small = static_cast<int64_t>(sm_count()) * per_sm;
+        const int nb = static_cast<int>(want < cap_small ? want : cap_small);
+        k_pass_x_small<<<nb, 256, 0, s>>>(t.desc, t.n, t.rows);
     } else if (t.maxXp <= 256) {
         k_pass_x<8, false><<<blocks, 256, 0, s>>>(t.desc, t.n, t.rows);
     } else if (t.maxXp <= 512) {
@@ -714,14 +1379,24 @@ cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int 
     return launch_persistent_impl<32, false>(t, c, ctas_per_sm, rows_per_item, s);
 }
 
+template <int NB, class K>
+static cudaError_t launch_small(K kernel, int64_t tiles, int sm, const GridTable &t, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    kernel<<<static_cast<unsigned>(tiles), NB * kTile, sm, s>>>(t.desc, t.tmaps, t.n, t.err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) {
     if (t.tiles_y == 0) return cudaSuccess;
-    return t.large ? launch_y_impl<false>(t, s) : launch_y_impl<true>(t, s);
+    if (!t.large) return launch_small<kNBY>(k_pass_y_small<kNBY>, t.tiles_y, small_smem<kNBY>(t.maxY, 1), t, s);
+    return launch_y_impl<false>(t, s);
 }
 
 cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s) {
     if (t.tiles_z == 0) return cudaSuccess;
-    return t.large ? launch_z_impl<false>(t, s) : launch_z_impl<true>(t, s);
+    if (!t.large) return launch_small<kNBZ>(k_pass_z_small<kNBZ>, t.tiles_z, small_smem<kNBZ>(t.maxZ, 2), t, s);
+    return launch_z_impl<false>(t, s);
 }
 
 }  // namespace vedt
