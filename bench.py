@@ -186,7 +186,7 @@ def _isnum(s):
 def algorithmic_bytes(kind, n_vox_per_grid, n_grids, n_points, n_link_pts):
     N = n_vox_per_grid * n_grids
     return {
-        "clear": n_vox_per_grid,                 # one grid per launch, 1 B written per voxel
+        "clear": n_vox_per_grid * n_grids,       # both grids in one launch, 1 B written per voxel
         "insert_points": n_points * 12,          # 12 B of xyz read per point
         "insert_links": n_link_pts * 12,         # 12 B of xyz read per link point
         "edt_x": N * (1 + 2),                    # uint8 occupancy in, uint16 row site out

@@ -137,7 +137,7 @@ namespace {
 
 void free_map(vedt_map *m) {
     for (int i = 0; i < 2; ++i) {
-        cudaFree(m->occ[i]);
+        if (i == 0) cudaFree(m->occ[0]);   // both grids share one allocation
         cudaFree(m->sq[i]);
         cudaFree(m->ix[i]);
         cudaFree(m->xs[i]);
@@ -218,8 +218,12 @@ vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float
     const int64_t Np = static_cast<int64_t>(m->Xp) * m->Y * m->Z;
     const size_t s2b = m->large ? 4 : 2;
     cudaError_t e = cudaSuccess;
+    // both occupancy grids in one allocation, M_S 256-byte aligned right after M_I, so a
+    // frame's ClearMap of both is a single launch
+    const int64_t n_al = (m->N + 255) / 256 * 256;
+    e = cudaMalloc(&m->occ[0], 2 * n_al);
+    if (e == cudaSuccess) m->occ[1] = m->occ[0] + n_al;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        if (e == cudaSuccess) e = cudaMalloc(&m->occ[i], m->N);
         if (e == cudaSuccess) e = cudaMalloc(&m->sq[i], m->N * 4);
         if (e == cudaSuccess) e = cudaMalloc(&m->ix[i], m->N * 4);
         if (e == cudaSuccess) e = cudaMalloc(&m->xs[i], Np * (m->large ? 2 : 1));
@@ -290,12 +294,13 @@ vedt_status vedt_map_info(const vedt_map *m, int32_t dims_out[3], float *vs, flo
 
 vedt_status vedt_clear(vedt_map *m, int which) {
     if (!m || !valid_which(which)) return VEDT_EINVAL;
-    for (int i = 0; i < 2; ++i) {
-        if (!(which & (1 << i))) continue;
-        const int slot = timing_begin(m, VEDT_K_CLEAR);
-        VCHECK(launch_clear(m->occ[i], m->N, m->stream));
-        timing_end(m, slot);
+    const int slot = timing_begin(m, VEDT_K_CLEAR);
+    if (which == VEDT_MAP_BOTH) {
+        VCHECK(launch_clear(m->occ[0], m->occ[1] - m->occ[0] + m->N, m->stream));
+    } else {
+        VCHECK(launch_clear(m->occ[which == VEDT_MAP_ENV ? 0 : 1], m->N, m->stream));
     }
+    timing_end(m, slot);
     return VEDT_OK;
 }
 

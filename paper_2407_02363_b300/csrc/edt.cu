@@ -417,34 +417,48 @@ __device__ __forceinline__ void pass_x_small_row(const GridDesc &G, int64_t lr, 
     if (lane == 0) G.row_has[lr] = 1;
 }
 
-// Grid-stride over rows with the next row's bytes loaded before the current row is
-// processed, so every warp keeps two rows in flight.
+// Grid-stride over rows in batches of kXRows rows per warp, the next batch's bytes
+// loaded before the current batch is processed, so every warp keeps 2 * kXRows rows in
+// flight (the pass is bound by load latency otherwise).
+constexpr int kXRows = 4;
+
 __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict__ gd, int ng, int64_t rows_total) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int64_t stride = nwarps * kXRows;
     int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     if (r >= rows_total) return;
-    int g = 0;
-    while (g + 1 < ng && gd[g + 1].row_begin <= r) ++g;
-    auto load = [&](int gg, int64_t rr) {
-        const GridDesc &G = gd[gg];
+    auto grid_of = [&](int64_t rr) {
+        int g = 0;
+        while (g + 1 < ng && gd[g + 1].row_begin <= rr) ++g;
+        return g;
+    };
+    auto load = [&](int64_t rr) {
+        if (rr >= rows_total) return make_uint2(0u, 0u);
+        const GridDesc &G = gd[grid_of(rr)];
         const bool vec = (G.X & 7) == 0 && (reinterpret_cast<uintptr_t>(G.occ) & 7) == 0;
         return row_bytes8(G.occ + (rr - G.row_begin) * G.X, G.X, 8 * lane, vec);
     };
-    uint2 w = load(g, r);
+    uint2 w[kXRows];
+#pragma unroll
+    for (int q = 0; q < kXRows; ++q) w[q] = load(r + q * nwarps);
     for (;;) {
-        const int64_t rn = r + nwarps;
-        int gn = g;
-        uint2 wn = make_uint2(0u, 0u);
-        if (rn < rows_total) {
-            while (gn + 1 < ng && gd[gn + 1].row_begin <= rn) ++gn;
-            wn = load(gn, rn);
+        const int64_t rn = r + stride;
+        uint2 wn[kXRows];
+#pragma unroll
+        for (int q = 0; q < kXRows; ++q) wn[q] = load(rn + q * nwarps);
+#pragma unroll
+        for (int q = 0; q < kXRows; ++q) {
+            const int64_t rr = r + q * nwarps;
+            if (rr < rows_total) {
+                const int g = grid_of(rr);
+                pass_x_small_row(gd[g], rr - gd[g].row_begin, lane, w[q]);
+            }
         }
-        pass_x_small_row(gd[g], r - gd[g].row_begin, lane, w);
         if (rn >= rows_total) break;
         r = rn;
-        g = gn;
-        w = wn;
+#pragma unroll
+        for (int q = 0; q < kXRows; ++q) w[q] = wn[q];
     }
 }
 
@@ -1320,7 +1334,8 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s) {
             per_sm = occ;
         }
         const int64_t cap_small = static_cast<int64_t>(sm_count()) * per_sm;
-        const int nb = static_cast<int>(want < cap_small ? want : cap_small);
+        const int64_t want_small = (t.rows + 8 * kXRows - 1) / (8 * kXRows);
+        const int nb = static_cast<int>(want_small < cap_small ? want_small : cap_small);
         k_pass_x_small<<<nb, 256, 0, s>>>(t.desc, t.n, t.rows);
     } else if (t.maxXp <= 256) {
         k_pass_x<8, false><<<blocks, 256, 0, s>>>(t.desc, t.n, t.rows);

@@ -19,7 +19,14 @@ __global__ void __launch_bounds__(256) k_clear(uint8_t *__restrict__ p, int64_t 
     const int64_t h = head < n ? head : n;
     const int64_t nvec = (n - h) >> 4;
     uint4 *v = reinterpret_cast<uint4 *>(p + h);
-    for (int64_t i = tid; i < nvec; i += stride) v[i] = make_uint4(0, 0, 0, 0);
+    int64_t i = tid;
+    for (; i + 3 * stride < nvec; i += 4 * stride) {   // four independent 16-byte stores in flight
+        v[i] = make_uint4(0, 0, 0, 0);
+        v[i + stride] = make_uint4(0, 0, 0, 0);
+        v[i + 2 * stride] = make_uint4(0, 0, 0, 0);
+        v[i + 3 * stride] = make_uint4(0, 0, 0, 0);
+    }
+    for (; i < nvec; i += stride) v[i] = make_uint4(0, 0, 0, 0);
     for (int64_t i = tid; i < h; i += stride) p[i] = 0;
     for (int64_t i = h + (nvec << 4) + tid; i < n; i += stride) p[i] = 0;
 }
@@ -139,7 +146,7 @@ static int sm_count() {
 cudaError_t launch_clear(uint8_t *p, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int64_t want = (n / 16 + 255) / 256;
-    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
     const int blocks = static_cast<int>(want < 1 ? 1 : (want < cap ? want : cap));
     k_clear<<<blocks, 256, 0, s>>>(p, n);
     return cudaGetLastError();

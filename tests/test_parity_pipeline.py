@@ -147,7 +147,8 @@ def test_timing_api_counts_launches():
         m.clear(v.MAP_BOTH)
         m.compute_edt(v.MAP_BOTH)
     t = m.kernel_times()
-    assert t["edt_x"][1] == 3 and t["edt_y"][1] == 3 and t["edt_z"][1] == 3 and t["clear"][1] == 6
+    # ClearMap of both grids is one launch (the two grids share one allocation)
+    assert t["edt_x"][1] == 3 and t["edt_y"][1] == 3 and t["edt_z"][1] == 3 and t["clear"][1] == 3
     assert all(ms >= 0 for ms, _ in t.values())
     m.close()
 
