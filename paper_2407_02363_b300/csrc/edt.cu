@@ -368,12 +368,13 @@ __device__ __forceinline__ uint2 row_bytes8(const uint8_t *row, int X, int x0, b
     return make_uint2(lo, hi);
 }
 
-__device__ __forceinline__ void pass_x_small_row(const GridDesc &G, int64_t lr, int lane, uint2 w) {
+__device__ __forceinline__ void pass_x_small_row(uint8_t *xs, uint8_t *row_has, int Xp, int64_t lr, int lane,
+                                                 uint2 w) {
     constexpr int kNoLeft = -1024, kNoRight = 2048;
     const uint32_t m = nz_nibble(w.x) | (nz_nibble(w.y) << 4);
     const uint32_t B = __ballot_sync(0xffffffffu, m != 0);
     if (B == 0) {
-        if (lane == 0) G.row_has[lr] = 0;
+        if (lane == 0) row_has[lr] = 0;
         return;
     }
     const int x0 = 8 * lane;
@@ -413,14 +414,38 @@ __device__ __forceinline__ void pass_x_small_row(const GridDesc &G, int64_t lr, 
         lo32 = __byte_perm(__byte_perm(best[0], best[1], 0x0040), __byte_perm(best[2], best[3], 0x0040), 0x5410);
         hi32 = __byte_perm(__byte_perm(best[4], best[5], 0x0040), __byte_perm(best[6], best[7], 0x0040), 0x5410);
     }
-    if (x0 < G.Xp) *reinterpret_cast<uint2 *>(static_cast<uint8_t *>(G.xs) + lr * G.Xp + x0) = make_uint2(lo32, hi32);
-    if (lane == 0) G.row_has[lr] = 1;
+    if (x0 < Xp) *reinterpret_cast<uint2 *>(xs + lr * Xp + x0) = make_uint2(lo32, hi32);
+    if (lane == 0) row_has[lr] = 1;
 }
 
 // Grid-stride over rows in batches of kXRows rows per warp, the next batch's bytes
 // loaded before the current batch is processed, so every warp keeps 2 * kXRows rows in
-// flight (the pass is bound by load latency otherwise).
+// flight.  The descriptor of the grid being swept stays in registers and is reloaded
+// only when a row falls in another grid of the table.
 constexpr int kXRows = 4;
+
+struct RowGrid {
+    const uint8_t *occ;
+    uint8_t *xs, *row_has;
+    int64_t begin, end;
+    int X, Xp;
+    bool vec;
+    int g = 0;
+    // rows visited by one warp only increase, so the scan resumes from the current grid
+    __device__ __forceinline__ void load(const GridDesc *__restrict__ gd, int ng, int64_t r) {
+        while (g + 1 < ng && gd[g + 1].row_begin <= r) ++g;
+        const GridDesc &G = gd[g];
+        occ = G.occ;
+        xs = static_cast<uint8_t *>(G.xs);
+        row_has = G.row_has;
+        begin = G.row_begin;
+        end = G.row_begin + static_cast<int64_t>(G.Y) * G.Z;
+        X = G.X;
+        Xp = G.Xp;
+        vec = (X & 7) == 0 && (reinterpret_cast<uintptr_t>(occ) & 7) == 0;
+    }
+    __device__ __forceinline__ bool has(int64_t r) const { return r >= begin && r < end; }
+};
 
 __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict__ gd, int ng, int64_t rows_total) {
     const int lane = threadIdx.x & 31;
@@ -428,16 +453,15 @@ __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict
     const int64_t stride = nwarps * kXRows;
     int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     if (r >= rows_total) return;
-    auto grid_of = [&](int64_t rr) {
-        int g = 0;
-        while (g + 1 < ng && gd[g + 1].row_begin <= rr) ++g;
-        return g;
-    };
+    // one descriptor cache for the loads and one for the sweeps: each visits rows in
+    // increasing order
+    RowGrid Gl, Gp;
+    Gl.load(gd, ng, r);
+    Gp.load(gd, ng, r);
     auto load = [&](int64_t rr) {
         if (rr >= rows_total) return make_uint2(0u, 0u);
-        const GridDesc &G = gd[grid_of(rr)];
-        const bool vec = (G.X & 7) == 0 && (reinterpret_cast<uintptr_t>(G.occ) & 7) == 0;
-        return row_bytes8(G.occ + (rr - G.row_begin) * G.X, G.X, 8 * lane, vec);
+        if (!Gl.has(rr)) Gl.load(gd, ng, rr);
+        return row_bytes8(Gl.occ + (rr - Gl.begin) * Gl.X, Gl.X, 8 * lane, Gl.vec);
     };
     uint2 w[kXRows];
 #pragma unroll
@@ -451,8 +475,8 @@ __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict
         for (int q = 0; q < kXRows; ++q) {
             const int64_t rr = r + q * nwarps;
             if (rr < rows_total) {
-                const int g = grid_of(rr);
-                pass_x_small_row(gd[g], rr - gd[g].row_begin, lane, w[q]);
+                if (!Gp.has(rr)) Gp.load(gd, ng, rr);
+                pass_x_small_row(Gp.xs, Gp.row_has, Gp.Xp, rr - Gp.begin, lane, w[q]);
             }
         }
         if (rn >= rows_total) break;
@@ -874,8 +898,8 @@ __device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, co
     const int tid = threadIdx.x, lane = tid & (kTile - 1);
     const int Y = gd[g].Y, Xp = gd[g].Xp;
     const int tiles_x = Xp / kCols;
-    const int z = static_cast<int>(lt / tiles_x);
-    const int x0 = static_cast<int>(lt % tiles_x) * kCols;
+    const int z = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x));
+    const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
     uint8_t *in = smem;                                                  // [Y][32]
     uint8_t *pos = smem + align16(Y * kCols);                            // [bl][NB * 32]
     int *ks = reinterpret_cast<int *>(pos + align16(Bands<NB>::len(Y) * NB * kTile));
@@ -909,8 +933,8 @@ __device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, co
     const int tid = threadIdx.x, lane = tid & (kTile - 1);
     const int X = gd[g].X, Y = gd[g].Y, Z = gd[g].Z, Xp = gd[g].Xp;
     const int tiles_x = Xp / kCols;
-    const int y = static_cast<int>(lt / tiles_x);
-    const int x0 = static_cast<int>(lt % tiles_x) * kCols;
+    const int y = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x));
+    const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
     uint16_t *in = reinterpret_cast<uint16_t *>(smem);                   // [Z][32]
     uint8_t *pos = smem + align16(Z * kCols * 2);                        // [bl][NB * 32]
     int *ks = reinterpret_cast<int *>(pos + align16(Bands<NB>::len(Z) * NB * kTile));
@@ -1018,8 +1042,8 @@ __device__ __forceinline__ bool tile_y_generic(const GridDesc *__restrict__ gd, 
     const int tid = threadIdx.x;
     const int Y = gd[g].Y, Xp = gd[g].Xp;
     const int tiles_x = Xp / kCols;
-    const int z = static_cast<int>(lt / tiles_x);
-    const int x0 = static_cast<int>(lt % tiles_x) * kCols;
+    const int z = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x));
+    const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
     const int by = min(Y, kBox);
     const int nbox = (Y + by - 1) / by;
     const int half = (Y + 1) >> 1;
@@ -1121,8 +1145,8 @@ __device__ __forceinline__ bool tile_z_generic(const GridDesc *__restrict__ gd, 
     const int tid = threadIdx.x;
     const int X = gd[g].X, Y = gd[g].Y, Z = gd[g].Z, Xp = gd[g].Xp;
     const int tiles_x = Xp / kCols;
-    const int y = static_cast<int>(lt / tiles_x);
-    const int x0 = static_cast<int>(lt % tiles_x) * kCols;
+    const int y = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x));
+    const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
     const int bz = min(Z, kBox);
     const int nbox = (Z + bz - 1) / bz;
     const int half = (Z + 1) >> 1;
@@ -1246,7 +1270,8 @@ __global__ void __launch_bounds__(kLanes) k_edt_persistent(const GridDesc *__res
                 if constexpr (SMALL) {
                     const GridDesc &G = gd[g];
                     const bool vec = (G.X & 7) == 0 && (reinterpret_cast<uintptr_t>(G.occ) & 7) == 0;
-                    pass_x_small_row(G, r, lane, row_bytes8(G.occ + r * G.X, G.X, 8 * lane, vec));
+                    pass_x_small_row(static_cast<uint8_t *>(G.xs), G.row_has, G.Xp, r, lane,
+                                     row_bytes8(G.occ + r * G.X, G.X, 8 * lane, vec));
                 } else {
                     pass_x_row<S, SMALL>(gd[g], r, lane);
                 }
