@@ -152,7 +152,12 @@ void free_map(vedt_map *m) {
     cudaFree(m->q_out);
     cudaFree(m->link_pts);
     cudaFree(m->link_of);
-    cudaFree(m->stage);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(m->stage[b]);
+        if (m->copied[b]) cudaEventDestroy(m->copied[b]);
+        if (m->consumed[b]) cudaEventDestroy(m->consumed[b]);
+    }
+    if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
     if (m->done) cudaEventDestroy(m->done);
     for (auto &p : m->pending) {
         cudaEventDestroy(p.a);
@@ -473,30 +478,65 @@ vedt_status vedt_frame(vedt_map *m, const float *xyz, int64_t n, const float *T,
     return st;
 }
 
-vedt_status vedt_frame_host(vedt_map *m, const float *xyz, int64_t n, const float *T, const vedt_chain *chain,
-                            const double *q, uint32_t mask, const float *centres, const float *radii, int nq,
-                            vedt_sphere_result *out) {
-    if (!m || n < 0 || (n > 0 && !xyz) || nq < 0 || nq > kMaxQuery) return VEDT_EINVAL;
-    if (nq > 0 && (!centres || !radii || !out)) return VEDT_EINVAL;
-    if (n > m->stage_cap) {
+namespace {
+
+// Queues one cycle from host buffers on the map's stream.  The cloud goes to staging
+// buffer `parity` on the copy stream, after the frame that last read that buffer has
+// finished, so the upload overlaps the previous frame's kernels; the map's stream waits
+// for the upload before the frame's kernels.
+vedt_status queue_host_frame(vedt_map *m, const float *xyz, int64_t n, const float *T, const vedt_chain *chain,
+                             const double *q, uint32_t mask, const float *centres, const float *radii, int nq,
+                             vedt_sphere_result *out) {
+    if (!m->copy_stream) {
+        VCHECK(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            VCHECK(cudaEventCreateWithFlags(&m->copied[b], cudaEventDisableTiming));
+            VCHECK(cudaEventCreateWithFlags(&m->consumed[b], cudaEventDisableTiming));
+        }
+    }
+    if (n > m->stage_cap) {   // grow both buffers once nothing reads or writes them
+        VCHECK(cudaStreamSynchronize(m->copy_stream));
         VCHECK(cudaStreamSynchronize(m->stream));
-        cudaFree(m->stage);
-        m->stage = nullptr;
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(m->stage[b]);
+            m->stage[b] = nullptr;
+        }
         m->stage_cap = 0;
-        VCHECK(cudaMalloc(&m->stage, sizeof(float) * 3 * n));
+        for (int b = 0; b < 2; ++b) VCHECK(cudaMalloc(&m->stage[b], sizeof(float) * 3 * n));
         m->stage_cap = n;
     }
-    if (n > 0) VCHECK(cudaMemcpyAsync(m->stage, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->stream));
+    const int b = m->parity;
+    m->parity ^= 1;
+    if (n > 0) {
+        VCHECK(cudaStreamWaitEvent(m->copy_stream, m->consumed[b], 0));
+        VCHECK(cudaMemcpyAsync(m->stage[b], xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->copy_stream));
+        VCHECK(cudaEventRecord(m->copied[b], m->copy_stream));
+        VCHECK(cudaStreamWaitEvent(m->stream, m->copied[b], 0));
+    }
     if (nq > 0) {
         VCHECK(cudaMemcpyAsync(m->q_in, centres, sizeof(float) * 3 * nq, cudaMemcpyHostToDevice, m->stream));
         VCHECK(cudaMemcpyAsync(m->q_in + 3 * kMaxQuery, radii, sizeof(float) * nq, cudaMemcpyHostToDevice,
                                m->stream));
     }
-    vedt_status st = vedt_frame(m, m->stage, n, T, chain, q, mask, m->q_in, m->q_in + 3 * kMaxQuery, nq, m->q_out);
+    vedt_status st = vedt_frame(m, m->stage[b], n, T, chain, q, mask, m->q_in, m->q_in + 3 * kMaxQuery, nq,
+                                m->q_out);
     if (st != VEDT_OK) return st;
+    VCHECK(cudaEventRecord(m->consumed[b], m->stream));
     if (nq > 0)
         VCHECK(cudaMemcpyAsync(out, m->q_out, sizeof(vedt_sphere_result) * 2 * nq, cudaMemcpyDeviceToHost,
                                m->stream));
+    return VEDT_OK;
+}
+
+}  // namespace
+
+vedt_status vedt_frame_host(vedt_map *m, const float *xyz, int64_t n, const float *T, const vedt_chain *chain,
+                            const double *q, uint32_t mask, const float *centres, const float *radii, int nq,
+                            vedt_sphere_result *out) {
+    if (!m || n < 0 || (n > 0 && !xyz) || nq < 0 || nq > kMaxQuery) return VEDT_EINVAL;
+    if (nq > 0 && (!centres || !radii || !out)) return VEDT_EINVAL;
+    const vedt_status st = queue_host_frame(m, xyz, n, T, chain, q, mask, centres, radii, nq, out);
+    if (st != VEDT_OK) return st;
     return vedt_check(m);
 }
 
@@ -506,25 +546,8 @@ vedt_status vedt_frame_host_async(vedt_map *m, const float *xyz, int64_t n, cons
     if (!m || n < 0 || (n > 0 && !xyz) || nq < 0 || nq > kMaxQuery) return VEDT_EINVAL;
     if (nq > 0 && (!centres || !radii || !out)) return VEDT_EINVAL;
     if (!m->done) VCHECK(cudaEventCreateWithFlags(&m->done, cudaEventDisableTiming));
-    if (n > m->stage_cap) {
-        VCHECK(cudaStreamSynchronize(m->stream));
-        cudaFree(m->stage);
-        m->stage = nullptr;
-        m->stage_cap = 0;
-        VCHECK(cudaMalloc(&m->stage, sizeof(float) * 3 * n));
-        m->stage_cap = n;
-    }
-    if (n > 0) VCHECK(cudaMemcpyAsync(m->stage, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->stream));
-    if (nq > 0) {
-        VCHECK(cudaMemcpyAsync(m->q_in, centres, sizeof(float) * 3 * nq, cudaMemcpyHostToDevice, m->stream));
-        VCHECK(cudaMemcpyAsync(m->q_in + 3 * kMaxQuery, radii, sizeof(float) * nq, cudaMemcpyHostToDevice,
-                               m->stream));
-    }
-    vedt_status st = vedt_frame(m, m->stage, n, T, chain, q, mask, m->q_in, m->q_in + 3 * kMaxQuery, nq, m->q_out);
+    const vedt_status st = queue_host_frame(m, xyz, n, T, chain, q, mask, centres, radii, nq, out);
     if (st != VEDT_OK) return st;
-    if (nq > 0)
-        VCHECK(cudaMemcpyAsync(out, m->q_out, sizeof(vedt_sphere_result) * 2 * nq, cudaMemcpyDeviceToHost,
-                               m->stream));
     VCHECK(cudaEventRecord(m->done, m->stream));
     return VEDT_OK;
 }

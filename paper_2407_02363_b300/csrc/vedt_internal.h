@@ -9,7 +9,7 @@
 namespace vedt {
 
 constexpr int kTile = 32;            // lanes per warp
-constexpr int kEnvCols = 32;         // columns per pass-Y/Z tile (two warps: lower / upper half)
+constexpr int kEnvCols = 32;         // columns per pass-Y/Z tile (one warp per band of the lines)
 constexpr int kBox = 256;            // max TMA box extent along one dimension
 constexpr uint16_t kNoX = 0xFFFF;    // pass-X "row has no site"
 constexpr int kSmallMax = 256;       // all dims <= 256: 16-bit packed 2-D sites, 8-bit links
@@ -123,9 +123,15 @@ struct vedt_map {
     // links
     float *link_pts = nullptr;
     uint8_t *link_of = nullptr;
-    float *stage = nullptr;        // device staging for host point clouds
+    // host frames: two device staging buffers for point clouds, filled on a copy stream
+    // so that the next frame's upload overlaps this frame's kernels
+    float *stage[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr};    // upload into stage[b] finished
+    cudaEvent_t consumed[2] = {nullptr, nullptr};  // frame reading stage[b] finished
+    int parity = 0;                // staging buffer of the next host frame
     cudaEvent_t done = nullptr;    // completion of the last asynchronous host frame
-    int64_t stage_cap = 0;         // points
+    int64_t stage_cap = 0;         // points per staging buffer
     int64_t n_link_pts = 0;
     int n_links = 0;
     // timing
