@@ -708,8 +708,8 @@ struct Cursor {
     }
 };
 
-// Walks the merged envelope over voxels [lo, hi) of band `band`: emit.start(j, c, raw, h)
-// whenever the nearest proximate site changes (and at lo), emit.put() once per voxel.
+// Walks the merged envelope over voxels [lo, hi) of band `band`: emit.start(c, raw)
+// whenever the nearest proximate site changes (and at lo), emit.put(value) once per voxel.
 // Entry q+1 is strictly nearer to voxel j iff h1 - h0 < 2 j (c1 - c0), ties keeping the
 // lower site.  The walk starts at the band's first entry (or the next band's), steps down
 // while the entry below is no worse at lo (the values at lo are unimodal along the
@@ -745,35 +745,76 @@ __device__ __forceinline__ void small_query(const P &pol, const SmallMerged<NB, 
         h0 = hb;
     }
     Cursor<NB, P> nxt = cur;
-    int c1 = 0, h1 = 0, dc2 = 0, dh = INT_MAX;
-    uint32_t r1 = 0;
-    auto fetch = [&]() {
-        if (nxt.next(M)) {
-            M.at(nxt.b, nxt.t, c1, r1);
-            h1 = pol.h(r1, c1);
-            dc2 = 2 * (c1 - c0);
-            dh = h1 - h0;
-        } else {
-            dh = INT_MAX;
-            dc2 = 0;
+    if constexpr (E::kValues) {
+        // Values at the current voxel j of the current entry (v0 = h0 - 2 j c0 + j^2, step
+        // i0) and of the next one (v1, i1; 2^30 when there is none, above any value reached
+        // here): the next entry is strictly nearer iff v1 < v0.  The emitter writes v0.
+        constexpr int kNone = 1 << 30;
+        int c1 = 0, v1 = kNone, i1 = 0;
+        uint32_t r1 = 0;
+        int v0 = h0 - 2 * lo * c0 + lo * lo, i0 = 2 * (lo - c0) + 1;
+        auto fetch = [&](int j) {
+            if (nxt.next(M)) {
+                M.at(nxt.b, nxt.t, c1, r1);
+                v1 = pol.h(r1, c1) + j * (j - 2 * c1);
+                i1 = 2 * (j - c1) + 1;
+            } else {
+                v1 = kNone;
+                i1 = 0;
+            }
+        };
+        fetch(lo);
+        emit.start(c0, r0);
+        for (int j = lo; j < hi; ++j) {
+            if (v1 < v0) {
+                do {
+                    c0 = c1;
+                    r0 = r1;
+                    v0 = v1;
+                    i0 = i1;
+                    fetch(j);
+                } while (v1 < v0);
+                emit.start(c0, r0);
+            }
+            emit.put(v0);
+            v0 += i0;
+            i0 += 2;
+            v1 += i1;
+            i1 += 2;
         }
-    };
-    fetch();
-    int thr = lo * dc2;
-    emit.start(lo, c0, r0, h0);
-    for (int j = lo; j < hi; ++j) {
-        if (dh < thr) {
-            do {
-                c0 = c1;
-                r0 = r1;
-                h0 = h1;
-                fetch();
-                thr = j * dc2;
-            } while (dh < thr);
-            emit.start(j, c0, r0, h0);
+    } else {
+        // Only the nearest site is emitted: the next entry is strictly nearer to voxel j
+        // iff h1 - h0 < 2 j (c1 - c0), the right side kept incrementally.
+        int c1 = 0, h1 = 0, dc2 = 0, dh = INT_MAX;
+        uint32_t r1 = 0;
+        auto fetch = [&]() {
+            if (nxt.next(M)) {
+                M.at(nxt.b, nxt.t, c1, r1);
+                h1 = pol.h(r1, c1);
+                dc2 = 2 * (c1 - c0);
+                dh = h1 - h0;
+            } else {
+                dh = INT_MAX;
+                dc2 = 0;
+            }
+        };
+        fetch();
+        int thr = lo * dc2;
+        emit.start(c0, r0);
+        for (int j = lo; j < hi; ++j) {
+            if (dh < thr) {
+                do {
+                    c0 = c1;
+                    r0 = r1;
+                    h0 = h1;
+                    fetch();
+                    thr = j * dc2;
+                } while (dh < thr);
+                emit.start(c0, r0);
+            }
+            emit.put(0);
+            thr += dc2;
         }
-        emit.put();
-        thr += dc2;
     }
 }
 
@@ -796,10 +837,11 @@ struct EmitYs {
     uint16_t *s2;
     uint32_t off, Xp;
     uint16_t v;
-    __device__ __forceinline__ void start(int, int c, uint32_t r, int) {
+    static constexpr bool kValues = false;   // emits the 2-D site only
+    __device__ __forceinline__ void start(int c, uint32_t r) {
         v = static_cast<uint16_t>(r | (static_cast<uint32_t>(c) << 8));
     }
-    __device__ __forceinline__ void put() {
+    __device__ __forceinline__ void put(int) {
         s2[off] = v;
         off += Xp;
     }
@@ -810,20 +852,17 @@ struct EmitZs {
     uint32_t off, plane;
     int X, XY;
     bool live;
-    int val, inc, id;
-    __device__ __forceinline__ void start(int j, int c, uint32_t r, int h) {
-        val = h - 2 * j * c + j * j;
-        inc = 2 * (j - c) + 1;
+    int id;
+    static constexpr bool kValues = true;    // emits the squared distance too
+    __device__ __forceinline__ void start(int c, uint32_t r) {
         id = static_cast<int>(r & 0xFFu) + X * static_cast<int>(r >> 8) + XY * c;
     }
-    __device__ __forceinline__ void put() {
+    __device__ __forceinline__ void put(int val) {
         if (live) {
             sq[off] = val;
             ix[off] = id;
         }
         off += plane;
-        val += inc;
-        inc += 2;
     }
 };
 
@@ -950,7 +989,7 @@ __device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, co
     const PolZ pol{x, y};
     EmitZs e{gd[g].sqdist, gd[g].idx,
              static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(y * X + (live ? x : 0)), plane, X, X * Y, live,
-             0, 0, 0};
+             0};
     bool ok;
     const int total = small_envelope<NB>(in, pos, ks, gd[g].slice_has, Z, pol, e, bar, phase, err, ok);
     if (!ok) {
