@@ -105,6 +105,7 @@ __device__ __forceinline__ void pass_x_row(const GridDesc &G, int64_t lr, int la
 #pragma unroll
             for (int q = 0; q < S / 2; q += 4)
                 *reinterpret_cast<uint4 *>(o + q) = make_uint4(wv[q], wv[q + 1], wv[q + 2], wv[q + 3]);
+            if (lane == 0) G.row_has[lr] = any ? 1 : 0;
         }
     }
 }
@@ -486,9 +487,16 @@ __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict
     }
 }
 
-// in[] element of a staged tile; h(raw, p) = f(p) + p^2 for the site word raw at p
+// Policies of the two envelope passes, for grids with every dim <= 256 (L = false: 8-bit
+// positions, 8-bit row sites, 16-bit 2-D sites x' | y' << 8, 32-bit products) and up to
+// 1024 (L = true: 16-bit positions, 16-bit row sites, 32-bit 2-D sites x' | y' << 16,
+// 64-bit products).  In = staged input word; h(raw, p) = f(p) + p^2 for that word at p.
+template <bool L>
 struct PolY {
-    using In = uint8_t;   // pass-X site x' of row p
+    using In = typename std::conditional<L, uint16_t, uint8_t>::type;   // pass-X site x' of row p
+    using Pos = typename std::conditional<L, uint16_t, uint8_t>::type;
+    using Prod = typename std::conditional<L, long long, int>::type;
+    static constexpr int kMax = L ? 1024 : 256;
     int x;
     __device__ __forceinline__ int h(uint32_t r, int p) const {
         const int d = x - static_cast<int>(r);
@@ -496,27 +504,34 @@ struct PolY {
     }
 };
 
+template <bool L>
 struct PolZ {
-    using In = uint16_t;  // pass-Y 2-D site x' | y' << 8 of slice p
+    using In = typename std::conditional<L, uint32_t, uint16_t>::type;  // pass-Y 2-D site of slice p
+    using Pos = typename std::conditional<L, uint16_t, uint8_t>::type;
+    using Prod = typename std::conditional<L, long long, int>::type;
+    static constexpr int kMax = L ? 1024 : 256;
+    static constexpr int kShift = L ? 16 : 8;
+    static constexpr uint32_t kMask = L ? 0xFFFFu : 0xFFu;
     int x, y;
     __device__ __forceinline__ int h(uint32_t r, int p) const {
-        const int dx = x - static_cast<int>(r & 0xFFu), dy = y - static_cast<int>(r >> 8);
+        const int dx = x - static_cast<int>(r & kMask), dy = y - static_cast<int>(r >> kShift);
         return dx * dx + dy * dy + p * p;
     }
 };
 
-// Banded line geometry of a small-mode tile: NB warps, warp b owns band
-// [b * bl, min(n, (b + 1) * bl)) of every line, bl = ceil(n / NB).
-template <int NB>
+// Banded line geometry of a tile: NB warps, warp b owns band [b * bl, min(n, (b + 1) * bl))
+// of every line, bl = ceil(n / NB); lines are at most MAX long.
+template <int NB, int MAX>
 struct Bands {
-    static constexpr int kWords = (kSmallMax / NB + 31) / 32;   // valid-mask words per band
+    static constexpr int kWords = (MAX / NB + 31) / 32;   // valid-mask words per band
     static __host__ __device__ constexpr int len(int n) { return (n + NB - 1) / NB; }
 };
 
 // b dropped between a and c (positions a < b < c, h = f + p^2): c overtakes b no later
-// than b overtakes a.  All products stay below 2^31 in small mode.
+// than b overtakes a.  Products in Prod (64-bit once dims exceed 256).
+template <class Prod>
 __device__ __forceinline__ bool dominated(int ca, int ha, int cb, int hb, int cc, int hc) {
-    return (hc - hb) * (cb - ca) <= (hb - ha) * (cc - cb);
+    return static_cast<Prod>(hc - hb) * (cb - ca) <= static_cast<Prod>(hb - ha) * (cc - cb);
 }
 
 // Stack of proximate sites of one band (Steps 2 and 4) over its valid positions
@@ -524,14 +539,15 @@ __device__ __forceinline__ bool dominated(int ca, int ha, int cb, int hb, int cc
 // stack's input words are written back in place from slot lo; `mypos` = this thread's
 // position stack (stride NB * 32).
 template <int NB, class P>
-__device__ __forceinline__ int small_build(const P &pol, typename P::In *col, uint8_t *mypos, int lo,
-                                           const uint32_t (&vm)[Bands<NB>::kWords]) {
+__device__ __forceinline__ int small_build(const P &pol, typename P::In *col, typename P::Pos *mypos, int lo,
+                                           const uint32_t (&vm)[Bands<NB, P::kMax>::kWords]) {
+    using Prod = typename P::Prod;
     constexpr int kS = NB * kTile;
     int k = 0, a = 0, b = 0, ha = 0, hb = 0, dab = 0, wab = 0;
     auto step = [&](int c) {
         const uint32_t r = col[c * kCols];
         const int hc = pol.h(r, c);
-        while (k >= 2 && (hc - hb) * wab <= dab * (c - b)) {
+        while (k >= 2 && static_cast<Prod>(hc - hb) * wab <= static_cast<Prod>(dab) * (c - b)) {
             --k;
             b = a;
             hb = ha;
@@ -543,7 +559,7 @@ __device__ __forceinline__ int small_build(const P &pol, typename P::In *col, ui
             }
         }
         col[(lo + k) * kCols] = static_cast<typename P::In>(r);
-        mypos[k * kS] = static_cast<uint8_t>(c);
+        mypos[k * kS] = static_cast<typename P::Pos>(c);
         dab = hc - hb;
         wab = c - b;
         a = b;
@@ -553,7 +569,7 @@ __device__ __forceinline__ int small_build(const P &pol, typename P::In *col, ui
         ++k;
     };
 #pragma unroll
-    for (int w = 0; w < Bands<NB>::kWords; ++w) {
+    for (int w = 0; w < Bands<NB, P::kMax>::kWords; ++w) {
         uint32_t bits = vm[w];
         const int base = lo + 32 * w;
         if (bits == 0xFFFFFFFFu) {   // a run of 32 valid positions (warp-uniform)
@@ -585,7 +601,7 @@ __device__ __forceinline__ int pick(const int (&a)[NB], int b) {
 template <int NB, class P>
 struct SmallMerged {
     typename P::In *in;         // this column's slots (stride kCols)
-    const uint8_t *pos;         // this column's band-0 positions (stride NB * 32)
+    const typename P::Pos *pos; // this column's band-0 positions (stride NB * 32)
     int bl;                     // band length
     int j[NB], i[NB];
     int last;                   // last non-empty band
@@ -653,7 +669,7 @@ struct SmallMerged {
                     const int hb = pol.h(rb, cb), hc = pol.h(rc, cc);
                     if (sb >= 0) {
                         at(sb, si, ca, ra);
-                        if (dominated(ca, pol.h(ra, ca), cb, hb, cc, hc)) {
+                        if (dominated<typename P::Prod>(ca, pol.h(ra, ca), cb, hb, cc, hc)) {
                             // pop the top; an emptied band hands the top to the band below
 #pragma unroll
                             for (int u = 0; u < NB; ++u)
@@ -664,7 +680,7 @@ struct SmallMerged {
                     }
                     if (jb + 1 <= ib) {
                         at(b, jb + 1, ca, ra);
-                        if (dominated(cb, hb, cc, hc, ca, pol.h(ra, ca))) {
+                        if (dominated<typename P::Prod>(cb, hb, cc, hc, ca, pol.h(ra, ca))) {
                             ++jb;
                             continue;
                         }
@@ -833,13 +849,15 @@ __device__ __forceinline__ void band_mask(const uint8_t *flags, int lo, int hi, 
     for (int w = 0; w < W; ++w) vm[w] = __ballot_sync(0xffffffffu, f[w] != 0);
 }
 
+template <bool L>
 struct EmitYs {
-    uint16_t *s2;
-    uint32_t off, Xp;
-    uint16_t v;
+    using Site = typename std::conditional<L, uint32_t, uint16_t>::type;
     static constexpr bool kValues = false;   // emits the 2-D site only
+    Site *s2;
+    uint32_t off, Xp;
+    Site v;
     __device__ __forceinline__ void start(int c, uint32_t r) {
-        v = static_cast<uint16_t>(r | (static_cast<uint32_t>(c) << 8));
+        v = static_cast<Site>(r | (static_cast<uint32_t>(c) << (L ? 16 : 8)));
     }
     __device__ __forceinline__ void put(int) {
         s2[off] = v;
@@ -847,15 +865,16 @@ struct EmitYs {
     }
 };
 
+template <bool L>
 struct EmitZs {
+    static constexpr bool kValues = true;    // emits the squared distance too
     int32_t *sq, *ix;
     uint32_t off, plane;
     int X, XY;
     bool live;
     int id;
-    static constexpr bool kValues = true;    // emits the squared distance too
     __device__ __forceinline__ void start(int c, uint32_t r) {
-        id = static_cast<int>(r & 0xFFu) + X * static_cast<int>(r >> 8) + XY * c;
+        id = static_cast<int>(r & PolZ<L>::kMask) + X * static_cast<int>(r >> PolZ<L>::kShift) + XY * c;
     }
     __device__ __forceinline__ void put(int val) {
         if (live) {
@@ -866,28 +885,39 @@ struct EmitZs {
     }
 };
 
-// shared memory of a small-mode tile: staged line tile, position stacks, stack sizes
-template <int NB>
-__host__ __device__ constexpr int small_smem(int n, int elem) {
-    return ((n * kCols * elem + 15) & ~15) + ((Bands<NB>::len(n) * NB * kTile + 15) & ~15) + NB * kTile * 4 +
+// Shared memory of an envelope tile over lines of n positions: the staged line tile
+// (whole TMA boxes of up to kBox positions x 32 columns), the position stacks, the stack
+// sizes and the published kept ranges.
+template <int NB, class P>
+__host__ __device__ constexpr int tile_in_bytes(int n) {
+    return ((n + kBox - 1) / kBox) * (n < kBox ? n : kBox) * kCols * static_cast<int>(sizeof(typename P::In));
+}
+template <int NB, class P>
+__host__ __device__ constexpr int tile_pos_bytes(int n) {
+    return Bands<NB, P::kMax>::len(n) * NB * kTile * static_cast<int>(sizeof(typename P::Pos));
+}
+template <int NB, class P>
+__host__ __device__ constexpr int small_smem(int n) {
+    return ((tile_in_bytes<NB, P>(n) + 15) & ~15) + ((tile_pos_bytes<NB, P>(n) + 15) & ~15) + NB * kTile * 4 +
            2 * NB * kTile * 2;
 }
 
-constexpr int kNBY = 4;   // bands per line in the standalone small-mode passes
+constexpr int kNBY = 4;   // bands per line in the standalone passes, dims <= 256
 constexpr int kNBZ = 4;
+constexpr int kNBL = 8;   // bands per line once some dim exceeds 256
 
-// One small-mode envelope tile over the staged line tile `in` (n positions x 32 columns),
-// after the TMA load was issued: builds the bands, merges, walks.  `flags` = validity of
-// each position; `emit` starts at the thread's first voxel.  Returns the total stack
-// size of the column (0 iff no valid position), identical for every column.
+// One envelope tile over the staged line tile `in` (n positions x 32 columns), after
+// its TMA loads were issued: builds the bands, merges, walks.  `flags` = validity of each
+// position; `emit` starts at the thread's first voxel.  Returns the total stack size of
+// the column (0 iff no valid position), identical for every column.
 template <int NB, class P, class E>
-__device__ __forceinline__ int small_envelope(typename P::In *in, uint8_t *pos, int *ks, const uint8_t *flags,
-                                              int n, const P &pol, E &emit, uint64_t *bar, uint32_t phase,
-                                              int32_t *err, bool &ok) {
+__device__ __forceinline__ int small_envelope(typename P::In *in, typename P::Pos *pos, int *ks,
+                                              const uint8_t *flags, int n, const P &pol, E &emit, uint64_t *bar,
+                                              uint32_t phase, int32_t *err, bool &ok) {
     const int tid = threadIdx.x, lane = tid & (kTile - 1), band = tid >> 5;
-    const int bl = Bands<NB>::len(n);
+    const int bl = Bands<NB, P::kMax>::len(n);
     const int lo = band * bl, hi = min(n, lo + bl);
-    uint32_t vm[Bands<NB>::kWords];
+    uint32_t vm[Bands<NB, P::kMax>::kWords];
     band_mask(flags, lo, hi, lane, vm);
     ok = mbar_wait_bounded(bar, phase, err);
     if (!ok) return 0;
@@ -927,29 +957,42 @@ __device__ __forceinline__ int small_envelope(typename P::In *in, uint8_t *pos, 
     return total;
 }
 
-// One pass-Y tile (grid g, slice z, columns x0..x0+31) in small mode with NB * 32
-// threads.  Same contract as tile_y: `phase` is the barrier's current parity; ends with
-// a CTA barrier so the caller may reuse shared memory.
-template <int NB>
+// Issues the TMA loads of a line tile: boxes of up to kBox positions along the line.
+template <class In>
+__device__ __forceinline__ void load_line_tile(In *in, const CUtensorMap *map, int n, int x0, int c1, bool along_y,
+                                               uint64_t *bar) {
+    const int bb = n < kBox ? n : kBox;
+    const int nbox = (n + bb - 1) / bb;
+    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(nbox * bb * kCols * sizeof(In)));
+    for (int b = 0; b < nbox; ++b) {
+        if (along_y) tma_load_3d(in + static_cast<size_t>(b) * bb * kCols, map, x0, b * bb, c1, bar);
+        else tma_load_3d(in + static_cast<size_t>(b) * bb * kCols, map, x0, c1, b * bb, bar);
+    }
+}
+
+// One pass-Y tile (grid g, slice z, columns x0..x0+31) with NB * 32 threads.  Same
+// contract as tile_y: `phase` is the barrier's current parity; ends with a CTA barrier
+// so the caller may reuse shared memory.
+template <int NB, bool L>
 __device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
                                              int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
                                              int32_t *err) {
+    using P = PolY<L>;
+    using In = typename P::In;
     const int tid = threadIdx.x, lane = tid & (kTile - 1);
     const int Y = gd[g].Y, Xp = gd[g].Xp;
     const int tiles_x = Xp / kCols;
     const int z = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x));
     const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
-    uint8_t *in = smem;                                                  // [Y][32]
-    uint8_t *pos = smem + align16(Y * kCols);                            // [bl][NB * 32]
-    int *ks = reinterpret_cast<int *>(pos + align16(Bands<NB>::len(Y) * NB * kTile));
-    if (tid == 0) {
-        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(Y * kCols));
-        tma_load_3d(in, &tm[2 * g], x0, 0, z, bar);
-    }
-    const int lo = (tid >> 5) * Bands<NB>::len(Y);
-    const PolY pol{x0 + lane};
-    EmitYs e{static_cast<uint16_t *>(gd[g].s2), static_cast<uint32_t>((z * Y + lo) * Xp + x0 + lane),
-             static_cast<uint32_t>(Xp), 0};
+    In *in = reinterpret_cast<In *>(smem);                                        // [Y][32]
+    auto *pos = reinterpret_cast<typename P::Pos *>(smem + align16(tile_in_bytes<NB, P>(Y)));
+    int *ks = reinterpret_cast<int *>(reinterpret_cast<uint8_t *>(pos) + align16(tile_pos_bytes<NB, P>(Y)));
+    if (tid == 0) load_line_tile(in, &tm[2 * g], Y, x0, z, true, bar);
+    const int lo = (tid >> 5) * Bands<NB, P::kMax>::len(Y);
+    const P pol{x0 + lane};
+    EmitYs<L> e{static_cast<typename EmitYs<L>::Site *>(gd[g].s2),
+                static_cast<uint32_t>((static_cast<int64_t>(z) * Y + lo) * Xp + x0 + lane), static_cast<uint32_t>(Xp),
+                0};
     bool ok;
     const int total = small_envelope<NB>(in, pos, ks, gd[g].row_has + static_cast<int64_t>(z) * Y, Y, pol, e, bar,
                                          phase, err, ok);
@@ -964,32 +1007,31 @@ __device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, co
     return true;
 }
 
-// One pass-Z tile (grid g, row y, columns x0..x0+31) in small mode with NB * 32 threads.
-template <int NB>
+// One pass-Z tile (grid g, row y, columns x0..x0+31) with NB * 32 threads.
+template <int NB, bool L>
 __device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
                                              int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
                                              int32_t *err) {
+    using P = PolZ<L>;
+    using In = typename P::In;
     const int tid = threadIdx.x, lane = tid & (kTile - 1);
     const int X = gd[g].X, Y = gd[g].Y, Z = gd[g].Z, Xp = gd[g].Xp;
     const int tiles_x = Xp / kCols;
     const int y = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x));
     const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
-    uint16_t *in = reinterpret_cast<uint16_t *>(smem);                   // [Z][32]
-    uint8_t *pos = smem + align16(Z * kCols * 2);                        // [bl][NB * 32]
-    int *ks = reinterpret_cast<int *>(pos + align16(Bands<NB>::len(Z) * NB * kTile));
-    if (tid == 0) {
-        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(Z * kCols * 2));
-        tma_load_3d(in, &tm[2 * g + 1], x0, y, 0, bar);
-    }
-    const int bl = Bands<NB>::len(Z);
+    In *in = reinterpret_cast<In *>(smem);                                        // [Z][32]
+    auto *pos = reinterpret_cast<typename P::Pos *>(smem + align16(tile_in_bytes<NB, P>(Z)));
+    int *ks = reinterpret_cast<int *>(reinterpret_cast<uint8_t *>(pos) + align16(tile_pos_bytes<NB, P>(Z)));
+    if (tid == 0) load_line_tile(in, &tm[2 * g + 1], Z, x0, y, false, bar);
+    const int bl = Bands<NB, P::kMax>::len(Z);
     const int lo = (tid >> 5) * bl, hi = min(Z, lo + bl);
     const int x = x0 + lane;
     const bool live = x < X;
     const uint32_t plane = static_cast<uint32_t>(X * Y);
-    const PolZ pol{x, y};
-    EmitZs e{gd[g].sqdist, gd[g].idx,
-             static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(y * X + (live ? x : 0)), plane, X, X * Y, live,
-             0};
+    const P pol{x, y};
+    EmitZs<L> e{gd[g].sqdist, gd[g].idx,
+                static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(y * X + (live ? x : 0)), plane, X, X * Y,
+                live, 0};
     bool ok;
     const int total = small_envelope<NB>(in, pos, ks, gd[g].slice_has, Z, pol, e, bar, phase, err, ok);
     if (!ok) {
@@ -1010,7 +1052,7 @@ __device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, co
     return true;
 }
 
-template <int NB>
+template <int NB, bool L>
 __global__ void __launch_bounds__(NB * kTile) k_pass_y_small(const GridDesc *__restrict__ gd,
                                                              const CUtensorMap *__restrict__ tm, int ng,
                                                              int32_t *err) {
@@ -1020,10 +1062,10 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_y_small(const GridDesc *__r
     const int g = find_grid(gd, ng, t, 0);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
-    tile_y_small<NB>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, 0, err);
+    tile_y_small<NB, L>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, 0, err);
 }
 
-template <int NB>
+template <int NB, bool L>
 __global__ void __launch_bounds__(NB * kTile) k_pass_z_small(const GridDesc *__restrict__ gd,
                                                              const CUtensorMap *__restrict__ tm, int ng,
                                                              int32_t *err) {
@@ -1033,7 +1075,7 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_z_small(const GridDesc *__r
     const int g = find_grid(gd, ng, t, 1);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
-    tile_z_small<NB>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, 0, err);
+    tile_z_small<NB, L>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, 0, err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1121,7 +1163,7 @@ __device__ __forceinline__ bool tile_y_generic(const GridDesc *__restrict__ gd, 
 template <bool SMALL>
 __device__ __forceinline__ bool tile_y(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
                                        int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
-    if constexpr (SMALL) return tile_y_small<2>(gd, tm, g, lt, smem, bar, phase, err);
+    if constexpr (SMALL) return tile_y_small<2, false>(gd, tm, g, lt, smem, bar, phase, err);
     else return tile_y_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
 }
 
@@ -1224,7 +1266,7 @@ __device__ __forceinline__ bool tile_z_generic(const GridDesc *__restrict__ gd, 
 template <bool SMALL>
 __device__ __forceinline__ bool tile_z(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
                                        int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
-    if constexpr (SMALL) return tile_z_small<2>(gd, tm, g, lt, smem, bar, phase, err);
+    if constexpr (SMALL) return tile_z_small<2, false>(gd, tm, g, lt, smem, bar, phase, err);
     else return tile_z_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
 }
 
@@ -1368,7 +1410,7 @@ static int sm_count() {
 }
 
 static size_t smem_y(const GridTable &t) {
-    if (!t.large) return static_cast<size_t>(small_smem<2>(t.maxY, 1));
+    if (!t.large) return static_cast<size_t>(small_smem<2, PolY<false>>(t.maxY));
     const int by = t.maxY > kBox ? kBox : t.maxY;
     const size_t rows = static_cast<size_t>((t.maxY + by - 1) / by) * by;
     const size_t xs = t.large ? 2 : 1, link = t.large ? 2 : 1;
@@ -1376,7 +1418,7 @@ static size_t smem_y(const GridTable &t) {
 }
 
 static size_t smem_z(const GridTable &t) {
-    if (!t.large) return static_cast<size_t>(small_smem<2>(t.maxZ, 2));
+    if (!t.large) return static_cast<size_t>(small_smem<2, PolZ<false>>(t.maxZ));
     const int bz = t.maxZ > kBox ? kBox : t.maxZ;
     const size_t rows = static_cast<size_t>((t.maxZ + bz - 1) / bz) * bz;
     const size_t site = t.large ? 4 : 2, link = t.large ? 2 : 1;
@@ -1408,24 +1450,6 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s) {
     } else {
         k_pass_x<32, false><<<blocks, 256, 0, s>>>(t.desc, t.n, t.rows);
     }
-    return cudaGetLastError();
-}
-
-template <bool SMALL>
-static cudaError_t launch_y_impl(const GridTable &t, cudaStream_t s) {
-    const size_t sm = smem_y(t);
-    cudaError_t e = cudaFuncSetAttribute(k_pass_y<SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
-    if (e != cudaSuccess) return e;
-    k_pass_y<SMALL><<<static_cast<unsigned>(t.tiles_y), kLanes, sm, s>>>(t.desc, t.tmaps, t.n, t.err);
-    return cudaGetLastError();
-}
-
-template <bool SMALL>
-static cudaError_t launch_z_impl(const GridTable &t, cudaStream_t s) {
-    const size_t sm = smem_z(t);
-    cudaError_t e = cudaFuncSetAttribute(k_pass_z<SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
-    if (e != cudaSuccess) return e;
-    k_pass_z<SMALL><<<static_cast<unsigned>(t.tiles_z), kLanes, sm, s>>>(t.desc, t.tmaps, t.n, t.err);
     return cudaGetLastError();
 }
 
@@ -1468,14 +1492,16 @@ static cudaError_t launch_small(K kernel, int64_t tiles, int sm, const GridTable
 
 cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) {
     if (t.tiles_y == 0) return cudaSuccess;
-    if (!t.large) return launch_small<kNBY>(k_pass_y_small<kNBY>, t.tiles_y, small_smem<kNBY>(t.maxY, 1), t, s);
-    return launch_y_impl<false>(t, s);
+    if (!t.large)
+        return launch_small<kNBY>(k_pass_y_small<kNBY, false>, t.tiles_y, small_smem<kNBY, PolY<false>>(t.maxY), t, s);
+    return launch_small<kNBL>(k_pass_y_small<kNBL, true>, t.tiles_y, small_smem<kNBL, PolY<true>>(t.maxY), t, s);
 }
 
 cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s) {
     if (t.tiles_z == 0) return cudaSuccess;
-    if (!t.large) return launch_small<kNBZ>(k_pass_z_small<kNBZ>, t.tiles_z, small_smem<kNBZ>(t.maxZ, 2), t, s);
-    return launch_z_impl<false>(t, s);
+    if (!t.large)
+        return launch_small<kNBZ>(k_pass_z_small<kNBZ, false>, t.tiles_z, small_smem<kNBZ, PolZ<false>>(t.maxZ), t, s);
+    return launch_small<kNBL>(k_pass_z_small<kNBL, true>, t.tiles_z, small_smem<kNBL, PolZ<true>>(t.maxZ), t, s);
 }
 
 }  // namespace vedt
