@@ -112,6 +112,8 @@ __device__ __forceinline__ void pass_x_row(const GridDesc &G, int64_t lr, int la
 
 template <int S, bool SMALL>
 __global__ void __launch_bounds__(256) k_pass_x(const GridDesc *__restrict__ gd, int ng, int64_t rows_total) {
+    pdl_trigger();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -453,12 +455,14 @@ __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     const int64_t stride = nwarps * kXRows;
     int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    pdl_trigger();
     if (r >= rows_total) return;
     // one descriptor cache for the loads and one for the sweeps: each visits rows in
     // increasing order
     RowGrid Gl, Gp;
     Gl.load(gd, ng, r);
     Gp.load(gd, ng, r);
+    pdl_wait();   // the occupancy comes from the previous kernels
     auto load = [&](int64_t rr) {
         if (rr >= rows_total) return make_uint2(0u, 0u);
         if (!Gl.has(rr)) Gl.load(gd, ng, rr);
@@ -1058,10 +1062,12 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_y_small(const GridDesc *__r
                                                              int32_t *err) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint64_t bar;
+    pdl_trigger();
     const int64_t t = blockIdx.x;
     const int g = find_grid(gd, ng, t, 0);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
+    pdl_wait();   // the staged tile and the validity flags come from the previous pass
     tile_y_small<NB, L>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, 0, err);
 }
 
@@ -1071,10 +1077,12 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_z_small(const GridDesc *__r
                                                              int32_t *err) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint64_t bar;
+    pdl_trigger();
     const int64_t t = blockIdx.x;
     const int g = find_grid(gd, ng, t, 1);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
+    pdl_wait();   // the staged tile and the validity flags come from the previous pass
     tile_z_small<NB, L>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, 0, err);
 }
 
@@ -1442,15 +1450,14 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s) {
         const int64_t cap_small = static_cast<int64_t>(sm_count()) * per_sm;
         const int64_t want_small = (t.rows + 8 * kXRows - 1) / (8 * kXRows);
         const int nb = static_cast<int>(want_small < cap_small ? want_small : cap_small);
-        k_pass_x_small<<<nb, 256, 0, s>>>(t.desc, t.n, t.rows);
+        return launch_pdl(k_pass_x_small, dim3(nb), dim3(256), 0, s, t.desc, t.n, t.rows);
     } else if (t.maxXp <= 256) {
-        k_pass_x<8, false><<<blocks, 256, 0, s>>>(t.desc, t.n, t.rows);
+        return launch_pdl(k_pass_x<8, false>, dim3(blocks), dim3(256), 0, s, t.desc, t.n, t.rows);
     } else if (t.maxXp <= 512) {
-        k_pass_x<16, false><<<blocks, 256, 0, s>>>(t.desc, t.n, t.rows);
+        return launch_pdl(k_pass_x<16, false>, dim3(blocks), dim3(256), 0, s, t.desc, t.n, t.rows);
     } else {
-        k_pass_x<32, false><<<blocks, 256, 0, s>>>(t.desc, t.n, t.rows);
+        return launch_pdl(k_pass_x<32, false>, dim3(blocks), dim3(256), 0, s, t.desc, t.n, t.rows);
     }
-    return cudaGetLastError();
 }
 
 template <int S, bool SMALL>
@@ -1486,8 +1493,8 @@ template <int NB, class K>
 static cudaError_t launch_small(K kernel, int64_t tiles, int sm, const GridTable &t, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    kernel<<<static_cast<unsigned>(tiles), NB * kTile, sm, s>>>(t.desc, t.tmaps, t.n, t.err);
-    return cudaGetLastError();
+    return launch_pdl(kernel, dim3(static_cast<unsigned>(tiles)), dim3(NB * kTile), static_cast<size_t>(sm), s, t.desc,
+                      t.tmaps, t.n, t.err);
 }
 
 cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) {

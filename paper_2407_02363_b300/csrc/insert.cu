@@ -12,6 +12,8 @@ struct Origin { float o[3]; };
 
 // ClearMap (Alg. 2 line 4): 16-byte stores over the byte grid, byte tail.
 __global__ void __launch_bounds__(256) k_clear(uint8_t *__restrict__ p, int64_t n) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     const uintptr_t a = reinterpret_cast<uintptr_t>(p);
@@ -38,6 +40,8 @@ __global__ void __launch_bounds__(256) k_insert_points(uint8_t *__restrict__ env
                                                        int X, int Y, int Z, float vs, Origin org,
                                                        const float *__restrict__ xyz, int64_t n, Pose12 T, int use_T,
                                                        int filter_self, unsigned long long *counts) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     unsigned long long written = 0, outside = 0, filtered = 0;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -78,6 +82,8 @@ __global__ void __launch_bounds__(256) k_insert_links(uint8_t *__restrict__ self
                                                       Origin org, const float *__restrict__ pts,
                                                       const uint8_t *__restrict__ link_of, int64_t n,
                                                       LinkPose poses, uint32_t mask) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int k = link_of[i];
@@ -97,6 +103,8 @@ __global__ void __launch_bounds__(128) k_query(const QueryGrid *__restrict__ gri
                                                float vs, Origin org, const float *__restrict__ centres,
                                                const float *__restrict__ radii, int m,
                                                vedt_sphere_result *__restrict__ out) {
+    pdl_trigger();
+    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m * ng) return;
     const int g = t / m, i = t - g * m;
@@ -148,8 +156,7 @@ cudaError_t launch_clear(uint8_t *p, int64_t n, cudaStream_t s) {
     const int64_t want = (n / 16 + 255) / 256;
     const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
     const int blocks = static_cast<int>(want < 1 ? 1 : (want < cap ? want : cap));
-    k_clear<<<blocks, 256, 0, s>>>(p, n);
-    return cudaGetLastError();
+    return launch_pdl(k_clear, dim3(blocks), dim3(256), 0, s, p, n);
 }
 
 cudaError_t launch_insert_points(uint8_t *env, const uint8_t *self, int X, int Y, int Z, float vs,
@@ -163,9 +170,8 @@ cudaError_t launch_insert_points(uint8_t *env, const uint8_t *self, int X, int Y
     const int64_t want = (n + 255) / 256;
     const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
     const int blocks = static_cast<int>(want < cap ? want : cap);
-    k_insert_points<<<blocks, 256, 0, s>>>(env, self, X, Y, Z, vs, o, xyz, n, P, T != nullptr, filter_self,
-                                           reinterpret_cast<unsigned long long *>(counts));
-    return cudaGetLastError();
+    return launch_pdl(k_insert_points, dim3(blocks), dim3(256), 0, s, env, self, X, Y, Z, vs, o, xyz, n, P,
+                      T != nullptr ? 1 : 0, filter_self, reinterpret_cast<unsigned long long *>(counts));
 }
 
 cudaError_t launch_insert_links(uint8_t *self, int X, int Y, int Z, float vs, const float *origin,
@@ -176,8 +182,8 @@ cudaError_t launch_insert_links(uint8_t *self, int X, int Y, int Z, float vs, co
     const int64_t want = (n + 255) / 256;
     const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
     const int blocks = static_cast<int>(want < cap ? want : cap);
-    k_insert_links<<<blocks, 256, 0, s>>>(self, X, Y, Z, vs, o, pts, link_of, n, poses, mask);
-    return cudaGetLastError();
+    return launch_pdl(k_insert_links, dim3(blocks), dim3(256), 0, s, self, X, Y, Z, vs, o, pts, link_of, n, poses,
+                      mask);
 }
 
 cudaError_t launch_query(const QueryGrid *g, int ng, int X, int Y, int Z, float vs, const float *origin,
@@ -186,8 +192,8 @@ cudaError_t launch_query(const QueryGrid *g, int ng, int X, int Y, int Z, float 
     if (m <= 0 || ng <= 0) return cudaSuccess;
     Origin o{{origin[0], origin[1], origin[2]}};
     const int n = m * ng;
-    k_query<<<(n + 127) / 128, 128, 0, s>>>(g, ng, X, Y, Z, vs, o, centres, radii, m, out);
-    return cudaGetLastError();
+    return launch_pdl(k_query, dim3((n + 127) / 128), dim3(128), 0, s, g, ng, X, Y, Z, vs, o, centres, radii, m,
+                      out);
 }
 
 }  // namespace vedt

@@ -54,6 +54,25 @@ struct GridTable {
     int32_t *err;                // device error word
 };
 
+// Launch with programmatic stream serialization: the kernel may start while the previous
+// kernel on the stream finishes, and orders itself with pdl_wait() (griddepcontrol.wait)
+// before touching anything that kernel reads or writes.
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // host-side helpers (api.cu)
 CUresult encode_tmap(CUtensorMap *m, CUtensorMapDataType t, int elem, void *base,
                      uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1, uint32_t b2);
@@ -164,6 +183,13 @@ __device__ __forceinline__ void rigid(const float *T, float px, float py, float 
     wy = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[4], px), __fmul_rn(T[5], py)), __fmul_rn(T[6], pz)), T[7]);
     wz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T[8], px), __fmul_rn(T[9], py)), __fmul_rn(T[10], pz)), T[11]);
 }
+
+// Programmatic dependent launch: let the next kernel on the stream start launching (every
+// block calls it first thing; the dependent still waits for this grid to finish), and wait
+// for the previous kernel's grid to complete with its memory visible.  Both are no-ops in
+// a launch without programmatic serialization.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
