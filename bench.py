@@ -70,6 +70,7 @@ def parse():
     p.add_argument("--sur-train", type=int, default=2 * 1024 * 1024, help="surrogate training configurations (0: skip)")
     p.add_argument("--sur-steps", type=int, default=20000, help="surrogate AdamW steps (batch 8192)")
     p.add_argument("--serve-frames", type=int, default=80, help="frames per arrival rate in the serving leg (0: skip)")
+    p.add_argument("--paper-reps", type=int, default=50, help="EDT launches per map size in the paper-sizes leg (0: skip)")
     return p.parse_args()
 
 
@@ -386,6 +387,7 @@ def run_vedt(args):
     batched = run_batched(args, v, dev) if args.batch_steps > 0 else None
     sur = run_surrogate(args, v, dev) if (args.sur_train > 0 and rank == 0) else None
     srv = run_serving(args, v, dev) if (args.serve_frames > 0 and rank == 0) else None
+    paper = run_paper_sizes(args, v) if (args.paper_reps > 0 and rank == 0) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -403,13 +405,58 @@ def run_vedt(args):
                                                                                      int(0.99 * len(frame_ms)))],
                            "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
             "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
-            "batched": batched, "surrogate": sur, "serving": srv,
+            "batched": batched, "surrogate": sur, "serving": srv, "paper_sizes": paper,
             "gpu_launches": int(round(sum(k["launches"] for k in kernels.values()) / kernel_frames * args.steps)),
             "kernels_from": f"{kernel_frames} frames right after the timed region, CUDA events around each launch "
                             "on the library's stream",
             "clocks": clk,
         }
         print(json.dumps(line))
+
+
+# The paper's map sizes (X x Y x Z, 2 cm voxels) with its GTX 1080 Ti PBA EDT times, for
+# context only (another machine, another EDT implementation): the per-stage timing table
+# (EDT column, 2 cm rows, with that scene's occupied-voxel count) and, where given, the
+# EDT comparison table.
+PAPER_SIZES = (((192, 192, 128), 6214, 1.7601, None),
+               ((256, 256, 128), 9080, 3.2475, 3.18),
+               ((512, 512, 128), 12274, 8.1972, 7.782))
+
+
+def run_paper_sizes(args, v):
+    """EDT of one map at each of the paper's map sizes: a seeded camera cloud sized so that
+    its occupied-voxel count is close to the paper's scene at that size, device time of
+    compute_edt on the environment grid over `paper_reps` back-to-back launches."""
+    import torch
+    from paper_2407_02363_b300 import synth
+    out = []
+    for dims, paper_occ, paper_ms, paper_cmp_ms in PAPER_SIZES:
+        grid = synth.GridSpec(dims, 0.02)
+        cloud = torch.from_numpy(synth.CameraScene(SEED + 7, grid, n_points=paper_occ * 9 // 8).frame(0)).cuda()
+        stream = torch.cuda.Stream()
+        m = v.Map(dims, 0.02, stream=stream)
+        m.clear(v.MAP_ENV)
+        m.insert_pointcloud(cloud)
+        occupied = int(m.occupancy(v.MAP_ENV).sum().item())
+        for _ in range(5):
+            m.compute_edt(v.MAP_ENV)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.paper_reps):
+            m.compute_edt(v.MAP_ENV)
+        b.record(stream)
+        torch.cuda.synchronize()
+        m.check()
+        ms = a.elapsed_time(b) / args.paper_reps
+        n = dims[0] * dims[1] * dims[2]
+        out.append({"dims": list(dims), "occupied_voxels": occupied, "edt_ms": ms,
+                    "gvoxel_s": n / (ms * 1e-3) / 1e9,
+                    "paper": {"occupied_voxels": paper_occ, "pba_ms_stage_table": paper_ms,
+                              "pba_ms_edt_table": paper_cmp_ms, "gpu": "GTX 1080 Ti"}})
+        m.close()
+    return {"what": "exact EDT of one map (environment grid) at the paper's 2 cm map sizes; "
+                    "the paper's times are context only", "sizes": out}
 
 
 def run_batched(args, v, dev):

@@ -501,11 +501,14 @@ struct PolY {
     using Pos = typename std::conditional<L, uint16_t, uint8_t>::type;
     using Prod = typename std::conditional<L, long long, int>::type;
     static constexpr int kMax = L ? 1024 : 256;
+    static constexpr bool kPacked = false;   // stack positions in a separate array
     int x;
     __device__ __forceinline__ int h(uint32_t r, int p) const {
         const int d = x - static_cast<int>(r);
         return d * d + p * p;
     }
+    static __device__ __forceinline__ uint32_t pack(uint32_t r, int) { return r; }
+    static __device__ __forceinline__ int pos_of(uint32_t) { return 0; }
 };
 
 template <bool L>
@@ -515,11 +518,21 @@ struct PolZ {
     using Prod = typename std::conditional<L, long long, int>::type;
     static constexpr int kMax = L ? 1024 : 256;
     static constexpr int kShift = L ? 16 : 8;
-    static constexpr uint32_t kMask = L ? 0xFFFFu : 0xFFu;
+    static constexpr uint32_t kMask = L ? 0x3FFu : 0xFFu;
+    // Large mode keeps a stack entry's position (< 1024) in the bits its site leaves free
+    // (10-15 and 26-29 of x' | y' << 16, x', y' < 1024), so the tile needs no position
+    // array; small mode's 16-bit site has no free bits.
+    static constexpr bool kPacked = L;
     int x, y;
     __device__ __forceinline__ int h(uint32_t r, int p) const {
-        const int dx = x - static_cast<int>(r & kMask), dy = y - static_cast<int>(r >> kShift);
+        const int dx = x - static_cast<int>(r & kMask), dy = y - static_cast<int>((r >> kShift) & kMask);
         return dx * dx + dy * dy + p * p;
+    }
+    static __device__ __forceinline__ uint32_t pack(uint32_t r, int c) {
+        return r | (static_cast<uint32_t>(c & 63) << 10) | (static_cast<uint32_t>(c >> 6) << 26);
+    }
+    static __device__ __forceinline__ int pos_of(uint32_t r) {
+        return static_cast<int>(((r >> 10) & 63u) | ((r >> 26) << 6));
     }
 };
 
@@ -556,14 +569,20 @@ __device__ __forceinline__ int small_build(const P &pol, typename P::In *col, ty
             b = a;
             hb = ha;
             if (k >= 2) {
-                a = mypos[(k - 2) * kS];
-                ha = pol.h(col[(lo + k - 2) * kCols], a);
+                const uint32_t ra = col[(lo + k - 2) * kCols];
+                if constexpr (P::kPacked) a = P::pos_of(ra);
+                else a = mypos[(k - 2) * kS];
+                ha = pol.h(ra, a);
                 dab = hb - ha;
                 wab = b - a;
             }
         }
-        col[(lo + k) * kCols] = static_cast<typename P::In>(r);
-        mypos[k * kS] = static_cast<typename P::Pos>(c);
+        if constexpr (P::kPacked) {
+            col[(lo + k) * kCols] = static_cast<typename P::In>(P::pack(r, c));
+        } else {
+            col[(lo + k) * kCols] = static_cast<typename P::In>(r);
+            mypos[k * kS] = static_cast<typename P::Pos>(c);
+        }
         dab = hc - hb;
         wab = c - b;
         a = b;
@@ -610,8 +629,9 @@ struct SmallMerged {
     int j[NB], i[NB];
     int last;                   // last non-empty band
     __device__ __forceinline__ void at(int b, int t, int &c, uint32_t &r) const {
-        c = pos[t * (NB * kTile) + b * kTile];
         r = in[(b * bl + t) * kCols];
+        if constexpr (P::kPacked) c = P::pos_of(r);
+        else c = pos[t * (NB * kTile) + b * kTile];
     }
     // largest non-empty band below b, or -1
     __device__ __forceinline__ int prev_band(int b) const {
@@ -878,7 +898,8 @@ struct EmitZs {
     bool live;
     int id;
     __device__ __forceinline__ void start(int c, uint32_t r) {
-        id = static_cast<int>(r & PolZ<L>::kMask) + X * static_cast<int>(r >> PolZ<L>::kShift) + XY * c;
+        id = static_cast<int>(r & PolZ<L>::kMask) + X * static_cast<int>((r >> PolZ<L>::kShift) & PolZ<L>::kMask) +
+             XY * c;
     }
     __device__ __forceinline__ void put(int val) {
         if (live) {
@@ -898,6 +919,7 @@ __host__ __device__ constexpr int tile_in_bytes(int n) {
 }
 template <int NB, class P>
 __host__ __device__ constexpr int tile_pos_bytes(int n) {
+    if (P::kPacked) return 0;
     return Bands<NB, P::kMax>::len(n) * NB * kTile * static_cast<int>(sizeof(typename P::Pos));
 }
 template <int NB, class P>
@@ -908,7 +930,8 @@ __host__ __device__ constexpr int small_smem(int n) {
 
 constexpr int kNBY = 4;   // bands per line in the standalone passes, dims <= 256
 constexpr int kNBZ = 4;
-constexpr int kNBL = 8;   // bands per line once some dim exceeds 256
+constexpr int kNBL = 8;   // bands per line once some dim exceeds 256, lines over 256 long
+constexpr int kNBLs = 4;  // bands per line once some dim exceeds 256, lines up to 256 long
 
 // One envelope tile over the staged line tile `in` (n positions x 32 columns), after
 // its TMA loads were issued: builds the bands, merges, walks.  `flags` = validity of each
@@ -1501,6 +1524,8 @@ cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) {
     if (t.tiles_y == 0) return cudaSuccess;
     if (!t.large)
         return launch_small<kNBY>(k_pass_y_small<kNBY, false>, t.tiles_y, small_smem<kNBY, PolY<false>>(t.maxY), t, s);
+    if (t.maxY <= 256)
+        return launch_small<kNBLs>(k_pass_y_small<kNBLs, true>, t.tiles_y, small_smem<kNBLs, PolY<true>>(t.maxY), t, s);
     return launch_small<kNBL>(k_pass_y_small<kNBL, true>, t.tiles_y, small_smem<kNBL, PolY<true>>(t.maxY), t, s);
 }
 
@@ -1508,6 +1533,8 @@ cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s) {
     if (t.tiles_z == 0) return cudaSuccess;
     if (!t.large)
         return launch_small<kNBZ>(k_pass_z_small<kNBZ, false>, t.tiles_z, small_smem<kNBZ, PolZ<false>>(t.maxZ), t, s);
+    if (t.maxZ <= 256)
+        return launch_small<kNBLs>(k_pass_z_small<kNBLs, true>, t.tiles_z, small_smem<kNBLs, PolZ<true>>(t.maxZ), t, s);
     return launch_small<kNBL>(k_pass_z_small<kNBL, true>, t.tiles_z, small_smem<kNBL, PolZ<true>>(t.maxZ), t, s);
 }
 

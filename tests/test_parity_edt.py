@@ -97,7 +97,8 @@ def test_edt_max_int_range_corners():
 
 
 def test_edt_full_size_256_and_512():
-    for dims, dens in (((256, 256, 256), 0.02), ((512, 512, 512), 0.003)):
+    for dims, dens in (((256, 256, 256), 0.02), ((512, 512, 512), 0.003), ((512, 512, 128), 0.0005),
+                       ((192, 192, 128), 0.002)):
         occ = synth.random_occupancy(5, dims, dens)
         (sq, ix), = run_gpu_edt(occ)
         assert_parity(occ, sq, ix)
