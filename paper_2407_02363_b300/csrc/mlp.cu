@@ -320,10 +320,9 @@ __global__ void k_to_bf16(const float *__restrict__ w, int N, int K, bf16 *__res
 // tiles ("slots") at once: each slot has its activation tile (128 x 256 bf16, canonical
 // K-major layout, SBO 4096 B) in shared memory and its own 256-column fp32 accumulator
 // in tensor memory (the two fill all 512 columns).  Warp roles:
-//   warp 0           streams weight chunks into a ring of kStages shared-memory stages
+//   warp 0, lane 0   streams weight chunks into a ring of kStages shared-memory stages
 //                    with bulk asynchronous copies (cp.async.bulk, mbarrier completion),
-//                    lane k filling stage k (one copy stream per lane: a single issuing
-//                    thread serialises the ring's round trips);
+//                    in the order the MMA thread consumes them;
 //   warp 1, lane 0   issues the tcgen05.mma: every weight chunk feeds both slots;
 //   warps 2..9       epilogue of slot 0, warps 10..17 of slot 1 (two warps per TMEM lane
 //                    quadrant, one per column half): read the finished accumulator from
@@ -496,21 +495,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     tc_fence_after();
     const uint32_t taddr = tmem_base;
 
-    if (warp == 0 && lane < kStages) {
-        // ---- weight producer: this lane fills stage `lane`, i.e. chunks it = lane (mod kStages)
-        uint32_t last = 0;
-        bool ok = true, any = false;
-        for (uint32_t it = lane; it < static_cast<uint32_t>(pairs * kNumWChunks) && ok; it += kStages) {
-            if (it >= kStages && !(ok = mbar_wait_bounded(&empty[lane], ((it / kStages) - 1) & 1, err))) break;
+    if (warp == 0 && lane == 0) {
+        // ---- weight producer: one thread fills the ring in consumption order (chunk it goes
+        // to stage it mod kStages once the chunk kStages before it is consumed).  One thread,
+        // not one lane per stage: lanes of a warp spinning on different barriers take turns,
+        // and a stage whose barrier completed waits for another lane's spin.
+        const uint32_t total = static_cast<uint32_t>(pairs * kNumWChunks);
+        bool ok = true;
+        uint32_t it = 0;
+        for (; it < total && ok; ++it) {
+            const uint32_t k = it % kStages;
+            if (it >= kStages && !(ok = mbar_wait_bounded(&empty[k], ((it / kStages) - 1) & 1, err))) break;
             const WChunk ch = wchunk(static_cast<int>(it % kNumWChunks));
             const uint32_t bytes = static_cast<uint32_t>(ch.n * ch.kc * 2);
-            mbar_arrive_expect_tx(&full[lane], bytes);
-            bulk_load(stage + lane * kStageBytes, a.wimg + ch.off, bytes, &full[lane]);
-            last = it;
-            any = true;
+            mbar_arrive_expect_tx(&full[k], bytes);
+            bulk_load(stage + k * kStageBytes, a.wimg + ch.off, bytes, &full[k]);
         }
-        // the last copy into this stage has landed before the CTA exits (normally consumed)
-        if (any) mbar_wait_bounded(&full[lane], (last / kStages) & 1, err);
+        // the last copy into each stage has landed before the CTA exits (normally consumed)
+        for (uint32_t j = it > kStages ? it - kStages : 0; j < it; ++j)
+            mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1, err);
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer.  The tensor pipe idles whenever this thread spends time between
         // MMAs, so descriptors are built once per layer and advanced by constants (the start
