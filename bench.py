@@ -426,7 +426,9 @@ PAPER_SIZES = (((192, 192, 128), 6214, 1.7601, None),
 def run_paper_sizes(args, v):
     """EDT of one map at each of the paper's map sizes: a seeded camera cloud sized so that
     its occupied-voxel count is close to the paper's scene at that size, device time of
-    compute_edt on the environment grid over `paper_reps` back-to-back launches."""
+    compute_edt on the environment grid over `paper_reps` back-to-back launches.  The band
+    ablation of Tab. 2 (PBA with m3 = 8 against PBA-naive, m = 1) is the same timing at each
+    admitted number of bands per line (vedt_map_set_bands)."""
     import torch
     from paper_2407_02363_b300 import synth
     out = []
@@ -438,25 +440,34 @@ def run_paper_sizes(args, v):
         m.clear(v.MAP_ENV)
         m.insert_pointcloud(cloud)
         occupied = int(m.occupancy(v.MAP_ENV).sum().item())
-        for _ in range(5):
-            m.compute_edt(v.MAP_ENV)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(args.paper_reps):
-            m.compute_edt(v.MAP_ENV)
-        b.record(stream)
-        torch.cuda.synchronize()
-        m.check()
-        ms = a.elapsed_time(b) / args.paper_reps
         n = dims[0] * dims[1] * dims[2]
+
+        def time_edt():
+            for _ in range(5):
+                m.compute_edt(v.MAP_ENV)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(args.paper_reps):
+                m.compute_edt(v.MAP_ENV)
+            b.record(stream)
+            torch.cuda.synchronize()
+            m.check()
+            return a.elapsed_time(b) / args.paper_reps
+
+        ms = time_edt()
+        by_bands = {}
+        for nb in ((1, 2, 4, 8) if max(dims) <= 256 else (4, 8)):
+            m.set_bands(nb)
+            by_bands[str(nb)] = time_edt()
+        m.set_bands(0)
         out.append({"dims": list(dims), "occupied_voxels": occupied, "edt_ms": ms,
-                    "gvoxel_s": n / (ms * 1e-3) / 1e9,
+                    "gvoxel_s": n / (ms * 1e-3) / 1e9, "edt_ms_by_bands": by_bands,
                     "paper": {"occupied_voxels": paper_occ, "pba_ms_stage_table": paper_ms,
                               "pba_ms_edt_table": paper_cmp_ms, "gpu": "GTX 1080 Ti"}})
         m.close()
-    return {"what": "exact EDT of one map (environment grid) at the paper's 2 cm map sizes; "
-                    "the paper's times are context only", "sizes": out}
+    return {"what": "exact EDT of one map (environment grid) at the paper's 2 cm map sizes, default "
+                    "bands and each band count; the paper's times are context only", "sizes": out}
 
 
 def run_batched(args, v, dev):

@@ -98,6 +98,15 @@ vedt_status vedt_map_destroy(vedt_map *map);
 /* Rebinds the map to another stream (cudaStream_t); later calls are ordered there. */
 vedt_status vedt_map_set_stream(vedt_map *map, void *stream);
 
+/* Bands per line of EDT passes Y and Z: the m2 / m3 banding of Alg. 1 (Sec. III-C), and
+ * the band ablation of Tab. 2 (PBA with m3 = 8 against PBA-naive, one band).  Each line
+ * of a 32-column tile is cut into `bands` equal bands, each built by its own warp, then
+ * joined.  Results do not depend on it; speed does.  0 restores the default (4 bands;
+ * once a dim exceeds 256, 4 bands for lines up to 256 and 8 above).  Grids with every dim
+ * <= 256 take 1, 2, 4 or 8, larger grids 4 or 8.  Applies to both grids from the next
+ * vedt_compute_edt on.  Errors: EINVAL (NULL map, other values). */
+vedt_status vedt_map_set_bands(vedt_map *map, int bands);
+
 /* Reports dims, voxel size and origin (any output may be NULL). */
 vedt_status vedt_map_info(const vedt_map *map, int32_t dims_out[3], float *voxel_size_out,
                           float origin_out[3]);

@@ -284,6 +284,15 @@ vedt_status vedt_map_set_stream(vedt_map *m, void *stream) {
     return VEDT_OK;
 }
 
+vedt_status vedt_map_set_bands(vedt_map *m, int bands) {
+    if (!m) return VEDT_EINVAL;
+    const bool large = m->tab[0].large != 0;
+    const bool ok = bands == 0 || bands == 4 || bands == 8 || (!large && (bands == 1 || bands == 2));
+    if (!ok) return VEDT_EINVAL;
+    for (GridTable &t : m->tab) t.bands = bands;
+    return VEDT_OK;
+}
+
 vedt_status vedt_map_info(const vedt_map *m, int32_t dims_out[3], float *vs, float origin_out[3]) {
     if (!m) return VEDT_EINVAL;
     if (dims_out) {

@@ -928,8 +928,7 @@ __host__ __device__ constexpr int small_smem(int n) {
            2 * NB * kTile * 2;
 }
 
-constexpr int kNBY = 4;   // bands per line in the standalone passes, dims <= 256
-constexpr int kNBZ = 4;
+constexpr int kNBY = 4;   // default bands per line in the standalone passes, dims <= 256
 constexpr int kNBL = 8;   // bands per line once some dim exceeds 256, lines over 256 long
 constexpr int kNBLs = 4;  // bands per line once some dim exceeds 256, lines up to 256 long
 
@@ -1520,22 +1519,43 @@ static cudaError_t launch_small(K kernel, int64_t tiles, int sm, const GridTable
                       t.tmaps, t.n, t.err);
 }
 
+// Bands per line (the m2 / m3 banding of Alg. 1): the table's `bands` if set, else four
+// (small mode) or four / eight by line length (large mode).  Small mode takes 1, 2, 4 or
+// 8 bands, large mode 4 or 8; vedt_map_set_bands admits no other value.
+static int bands_for(const GridTable &t, int line) {
+    if (t.bands) return t.bands;
+    if (!t.large) return kNBY;
+    return line <= 256 ? kNBLs : kNBL;
+}
+
 cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) {
     if (t.tiles_y == 0) return cudaSuccess;
-    if (!t.large)
-        return launch_small<kNBY>(k_pass_y_small<kNBY, false>, t.tiles_y, small_smem<kNBY, PolY<false>>(t.maxY), t, s);
-    if (t.maxY <= 256)
-        return launch_small<kNBLs>(k_pass_y_small<kNBLs, true>, t.tiles_y, small_smem<kNBLs, PolY<true>>(t.maxY), t, s);
-    return launch_small<kNBL>(k_pass_y_small<kNBL, true>, t.tiles_y, small_smem<kNBL, PolY<true>>(t.maxY), t, s);
+    const int nb = bands_for(t, t.maxY);
+    if (!t.large) {
+        switch (nb) {
+            case 1: return launch_small<1>(k_pass_y_small<1, false>, t.tiles_y, small_smem<1, PolY<false>>(t.maxY), t, s);
+            case 2: return launch_small<2>(k_pass_y_small<2, false>, t.tiles_y, small_smem<2, PolY<false>>(t.maxY), t, s);
+            case 8: return launch_small<8>(k_pass_y_small<8, false>, t.tiles_y, small_smem<8, PolY<false>>(t.maxY), t, s);
+            default: return launch_small<4>(k_pass_y_small<4, false>, t.tiles_y, small_smem<4, PolY<false>>(t.maxY), t, s);
+        }
+    }
+    if (nb == 4) return launch_small<4>(k_pass_y_small<4, true>, t.tiles_y, small_smem<4, PolY<true>>(t.maxY), t, s);
+    return launch_small<8>(k_pass_y_small<8, true>, t.tiles_y, small_smem<8, PolY<true>>(t.maxY), t, s);
 }
 
 cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s) {
     if (t.tiles_z == 0) return cudaSuccess;
-    if (!t.large)
-        return launch_small<kNBZ>(k_pass_z_small<kNBZ, false>, t.tiles_z, small_smem<kNBZ, PolZ<false>>(t.maxZ), t, s);
-    if (t.maxZ <= 256)
-        return launch_small<kNBLs>(k_pass_z_small<kNBLs, true>, t.tiles_z, small_smem<kNBLs, PolZ<true>>(t.maxZ), t, s);
-    return launch_small<kNBL>(k_pass_z_small<kNBL, true>, t.tiles_z, small_smem<kNBL, PolZ<true>>(t.maxZ), t, s);
+    const int nb = bands_for(t, t.maxZ);
+    if (!t.large) {
+        switch (nb) {
+            case 1: return launch_small<1>(k_pass_z_small<1, false>, t.tiles_z, small_smem<1, PolZ<false>>(t.maxZ), t, s);
+            case 2: return launch_small<2>(k_pass_z_small<2, false>, t.tiles_z, small_smem<2, PolZ<false>>(t.maxZ), t, s);
+            case 8: return launch_small<8>(k_pass_z_small<8, false>, t.tiles_z, small_smem<8, PolZ<false>>(t.maxZ), t, s);
+            default: return launch_small<4>(k_pass_z_small<4, false>, t.tiles_z, small_smem<4, PolZ<false>>(t.maxZ), t, s);
+        }
+    }
+    if (nb == 4) return launch_small<4>(k_pass_z_small<4, true>, t.tiles_z, small_smem<4, PolZ<true>>(t.maxZ), t, s);
+    return launch_small<8>(k_pass_z_small<8, true>, t.tiles_z, small_smem<8, PolZ<true>>(t.maxZ), t, s);
 }
 
 }  // namespace vedt

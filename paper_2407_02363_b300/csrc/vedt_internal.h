@@ -52,6 +52,7 @@ struct GridTable {
     int maxY, maxZ, maxXp;
     int64_t rows, tiles_y, tiles_z;
     int32_t *err;                // device error word
+    int bands;                   // bands per line in passes Y and Z (0: the default)
 };
 
 // Launch with programmatic stream serialization: the kernel may start while the previous

@@ -47,6 +47,7 @@ _sig = {
     "vedt_map_create": [_P, _F32, _P, _P, _P],
     "vedt_map_destroy": [_P],
     "vedt_map_set_stream": [_P, _P],
+    "vedt_map_set_bands": [_P, _I32],
     "vedt_map_info": [_P, _P, _P, _P],
     "vedt_clear": [_P, _I32],
     "vedt_insert_pointcloud": [_P, _P, _I64, _P, _I32, _P],
@@ -219,6 +220,11 @@ class Map:
 
     def set_stream(self, stream):
         _chk(_lib.vedt_map_set_stream(self._h, stream_handle(stream)), "vedt_map_set_stream")
+
+    def set_bands(self, bands=0):
+        """Bands per line of EDT passes Y and Z (0: default; 1/2/4/8 for dims <= 256, 4/8
+        above)."""
+        _chk(_lib.vedt_map_set_bands(self._h, int(bands)), "vedt_map_set_bands")
 
     def clear(self, which=MAP_BOTH):
         _chk(_lib.vedt_clear(self._h, which), "vedt_clear")

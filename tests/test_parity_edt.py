@@ -11,10 +11,11 @@ from gpu_helpers import INT32_MAX, check_idx_valid, lib
 pytestmark = pytest.mark.gpu
 
 
-def run_gpu_edt(occ_env, occ_self=None, which=None):
+def run_gpu_edt(occ_env, occ_self=None, which=None, bands=0):
     v = lib()
     Z, Y, X = occ_env.shape
     m = v.Map((X, Y, Z), 0.01)
+    m.set_bands(bands)
     m.upload_occupancy(v.MAP_ENV, occ_env)
     if occ_self is not None:
         m.upload_occupancy(v.MAP_SELF, occ_self)
@@ -63,6 +64,38 @@ def test_edt_large_mode(dims, density):
     occ = synth.random_occupancy(7 + sum(dims), dims, density)
     (sq, ix), = run_gpu_edt(occ)
     assert_parity(occ, sq, ix)
+
+
+@pytest.mark.parametrize("bands", [1, 2, 4, 8])
+def test_edt_band_count_does_not_change_the_field(bands):
+    """Bands per line (Alg. 1's m2 / m3, the ablation of Tab. 2) change speed only: lines
+    shorter than, equal to and longer than a band multiple, sparse and dense, ragged x."""
+    for dims, dens in (((96, 70, 37), 0.01), ((256, 33, 256), 0.002), ((45, 256, 129), 0.3), ((7, 5, 3), 0.2)):
+        occ = synth.random_occupancy(31 + bands + sum(dims), dims, dens)
+        (sq, ix), = run_gpu_edt(occ, bands=bands)
+        assert_parity(occ, sq, ix)
+
+
+@pytest.mark.parametrize("bands", [4, 8])
+def test_edt_band_count_large_mode(bands):
+    for dims, dens in (((300, 40, 250), 0.002), ((40, 513, 20), 0.01)):
+        occ = synth.random_occupancy(41 + bands + sum(dims), dims, dens)
+        (sq, ix), = run_gpu_edt(occ, bands=bands)
+        assert_parity(occ, sq, ix)
+
+
+def test_set_bands_rejects_values_outside_the_mode():
+    v = lib()
+    small, large = v.Map((64, 64, 64), 0.01), v.Map((300, 8, 8), 0.01)
+    for m, bad in ((small, (3, 16, -1)), (large, (1, 2, 3, 16))):
+        for b in bad:
+            with pytest.raises(v.VedtError):
+                m.set_bands(b)
+    small.set_bands(1)
+    large.set_bands(8)
+    small.set_bands(0)
+    small.close()
+    large.close()
 
 
 @pytest.mark.parametrize("dims", [(16, 16, 16), (300, 20, 10)])
