@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--sur-steps", type=int, default=20000, help="surrogate AdamW steps (batch 8192)")
     p.add_argument("--serve-frames", type=int, default=80, help="frames per arrival rate in the serving leg (0: skip)")
     p.add_argument("--paper-reps", type=int, default=50, help="EDT launches per map size in the paper-sizes leg (0: skip)")
+    p.add_argument("--static-frames", type=int, default=200,
+                   help="frames of the static-scene leg, incremental EDT off and on (0: skip)")
     return p.parse_args()
 
 
@@ -383,6 +385,9 @@ def run_vedt(args):
     if args.e2e_steps > 0:
         e2e = run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream)
     m.close()
+    static = None
+    if args.static_frames > 0 and rank == 0:
+        static = run_static_scene(args, v, W, clouds[0], centres, radii, m_sph, cchain, dev)
 
     batched = run_batched(args, v, dev) if args.batch_steps > 0 else None
     sur = run_surrogate(args, v, dev) if (args.sur_train > 0 and rank == 0) else None
@@ -406,12 +411,61 @@ def run_vedt(args):
                            "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
             "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
             "batched": batched, "surrogate": sur, "serving": srv, "paper_sizes": paper,
+            "static_scene": static,
             "gpu_launches": int(round(sum(k["launches"] for k in kernels.values()) / kernel_frames * args.steps)),
             "kernels_from": f"{kernel_frames} frames right after the timed region, CUDA events around each launch "
                             "on the library's stream",
             "clocks": clk,
         }
         print(json.dumps(line))
+
+
+def run_static_scene(args, v, W, cloud, centres, radii, m_sph, cchain, dev):
+    """The frame256 workload with the scene frozen (the first frame's cloud every frame,
+    the arm still moving): full frames through vedt_frame with the incremental EDT off and
+    on.  With it on, the environment EDT reruns only when the arm's robot-point removal
+    changes the environment occupancy.  Both runs end with bit-equal fields."""
+    import torch
+    grid = W["grid"]
+    n_traj = len(W["traj"])
+    out = torch.empty(2 * m_sph * 32, dtype=torch.uint8, device=dev)
+    res = {}
+    fields = {}
+    for mode in ("off", "on"):
+        stream = torch.cuda.Stream(device=dev)
+        m = v.Map(grid.dims, grid.voxel_size, grid.origin, stream=stream)
+        m.register_links(W["links"])
+        m.set_incremental(mode == "on")
+
+        def step(i):
+            k = i % n_traj
+            m.frame(cloud, cloud.shape[0], cchain, W["traj"][k], SELF_MASK, centres[k], radii, m_sph, out)
+
+        for i in range(5):
+            step(i)
+        torch.cuda.synchronize()
+        env_runs = 0
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(args.static_frames):
+            step(5 + i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        m.check()
+        ms = a.elapsed_time(b) / args.static_frames
+        # recompute count of the environment grid, frame by frame (untimed)
+        for i in range(min(args.static_frames, 60)):
+            step(5 + args.static_frames + i)
+            env_runs += int(m.edt_recomputed(v.MAP_ENV)[0])
+        fields[mode] = [t.clone() for t in m.field_view(v.MAP_ENV) + m.field_view(v.MAP_SELF)]
+        torch.cuda.synchronize()
+        res[mode] = {"ms_per_frame": ms, "env_edt_runs_per_60_frames": env_runs if mode == "on" else 60}
+        m.close()
+    equal = all(torch.equal(x, y) for x, y in zip(fields["off"], fields["on"]))
+    return {"what": "frame256 with a frozen scene and the moving arm, incremental EDT off / on "
+                    "(vedt_map_set_incremental), device time per frame", "frames": args.static_frames,
+            "off": res["off"], "on": res["on"], "speedup": res["off"]["ms_per_frame"] / res["on"]["ms_per_frame"],
+            "fields_bit_equal": bool(equal)}
 
 
 # The paper's map sizes (X x Y x Z, 2 cm voxels) with its GTX 1080 Ti PBA EDT times, for

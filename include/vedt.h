@@ -107,6 +107,23 @@ vedt_status vedt_map_set_stream(vedt_map *map, void *stream);
  * vedt_compute_edt on.  Errors: EINVAL (NULL map, other values). */
 vedt_status vedt_map_set_bands(vedt_map *map, int bands);
 
+/* Incremental EDT (on = 1): vedt_compute_edt first compares each selected grid's
+ * occupancy with a device snapshot taken at that grid's last EDT (one extra read of the
+ * grid and of the snapshot, a write of the snapshot where they differ) and skips all
+ * three passes of a grid whose occupancy is unchanged, leaving its fields as they are.
+ * The fields are then still exact: the EDT is a function of the occupancy alone.  This
+ * is the static-scene reuse of Sec. IV (a static scene needs one EDT while the arm
+ * moves), decided on the device each call.  Enabling allocates the snapshots (2 x the
+ * occupancy bytes) and the next EDT of each grid recomputes; on = 0 frees them.  A batch
+ * EDT over the map also forces the next incremental EDT to recompute.  Synchronises the
+ * map's stream.  Errors: EINVAL, ENOMEM, ECUDA. */
+vedt_status vedt_map_set_incremental(vedt_map *map, int on);
+
+/* After the map's stream drains: out[0] (and out[1] for VEDT_MAP_BOTH, env first) = 1
+ * if the last vedt_compute_edt of that grid recomputed it, 0 if it was skipped as
+ * unchanged (always 1 when the map is not incremental).  Synchronises.  Errors: EINVAL. */
+vedt_status vedt_map_edt_recomputed(vedt_map *map, int which, int32_t *out);
+
 /* Reports dims, voxel size and origin (any output may be NULL). */
 vedt_status vedt_map_info(const vedt_map *map, int32_t dims_out[3], float *voxel_size_out,
                           float origin_out[3]);

@@ -137,7 +137,11 @@ namespace {
 
 void free_map(vedt_map *m) {
     for (int i = 0; i < 2; ++i) {
-        if (i == 0) cudaFree(m->occ[0]);   // both grids share one allocation
+        if (i == 0) {
+            cudaFree(m->occ[0]);   // both grids share one allocation
+            cudaFree(m->snap);
+            cudaFree(m->changed);
+        }
         cudaFree(m->sq[i]);
         cudaFree(m->ix[i]);
         cudaFree(m->xs[i]);
@@ -180,6 +184,7 @@ GridDesc grid_of(const vedt_map *m, int i) {
     g.Y = m->Y;
     g.Z = m->Z;
     g.Xp = m->Xp;
+    g.changed = m->changed + i;
     return g;
 }
 
@@ -237,6 +242,7 @@ vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float
         if (e == cudaSuccess) e = cudaMalloc(&m->slice_has[i], m->Z);
     }
     if (e == cudaSuccess) e = cudaMalloc(&m->err, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&m->changed, 2 * sizeof(uint32_t));
     const size_t desc_bytes = sizeof(GridDesc) * 4, tm_bytes = sizeof(CUtensorMap) * 8;
     if (e == cudaSuccess) e = cudaMalloc(&m->tab_mem, desc_bytes + tm_bytes + 256);
     if (e == cudaSuccess) e = cudaMalloc(&m->qgrids, sizeof(QueryGrid) * 4);
@@ -247,6 +253,7 @@ vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float
         return from_cuda(e);
     }
     e = cudaMemset(m->err, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(m->changed, 1, 2 * sizeof(uint32_t));   // nonzero: recompute
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMemset(m->occ[i], 0, m->N);
     if (e != cudaSuccess) {
         free_map(m);
@@ -281,6 +288,39 @@ vedt_status vedt_map_destroy(vedt_map *m) {
 vedt_status vedt_map_set_stream(vedt_map *m, void *stream) {
     if (!m) return VEDT_EINVAL;
     m->stream = static_cast<cudaStream_t>(stream);
+    return VEDT_OK;
+}
+
+vedt_status vedt_map_set_incremental(vedt_map *m, int on) {
+    if (!m) return VEDT_EINVAL;
+    VCHECK(cudaStreamSynchronize(m->stream));
+    const int64_t n_al = m->occ[1] - m->occ[0];
+    if (on && !m->snap) {
+        const cudaError_t e = cudaMalloc(&m->snap, 2 * n_al);
+        if (e != cudaSuccess) {
+            m->snap = nullptr;
+            return from_cuda(e);
+        }
+    }
+    if (!on && m->snap) {
+        cudaFree(m->snap);
+        m->snap = nullptr;
+    }
+    m->incremental = on ? 1 : 0;
+    m->snap_valid[0] = m->snap_valid[1] = false;   // the first EDT after a switch recomputes
+    for (GridTable &t : m->tab) t.incr = m->incremental;
+    VCHECK(cudaMemset(m->changed, 1, 2 * sizeof(uint32_t)));
+    return VEDT_OK;
+}
+
+vedt_status vedt_map_edt_recomputed(vedt_map *m, int which, int32_t *out) {
+    if (!m || !out || !valid_which(which)) return VEDT_EINVAL;
+    VCHECK(cudaStreamSynchronize(m->stream));
+    uint32_t c[2] = {1, 1};
+    VCHECK(cudaMemcpy(c, m->changed, sizeof(c), cudaMemcpyDeviceToHost));
+    int k = 0;
+    if (which & VEDT_MAP_ENV) out[k++] = c[0] != 0;
+    if (which & VEDT_MAP_SELF) out[k++] = c[1] != 0;
     return VEDT_OK;
 }
 
@@ -428,6 +468,17 @@ vedt_status vedt_compute_edt(vedt_map *m, int which) {
     if (!m || !valid_which(which)) return VEDT_EINVAL;
     const GridTable &t = m->tab[which - 1];
     int slot = timing_begin(m, VEDT_K_EDT_X);
+    if (m->incremental) {
+        // per grid: changed = 0, then the diff kernel sets it if the occupancy differs from
+        // the snapshot of the last EDT; a grid whose fields are not known to match its
+        // snapshot is recomputed regardless
+        const int g0 = which == VEDT_MAP_SELF ? 1 : 0, ng = which == VEDT_MAP_BOTH ? 2 : 1;
+        const int64_t n_al = m->occ[1] - m->occ[0];
+        for (int g = g0; g < g0 + ng; ++g)
+            VCHECK(cudaMemsetAsync(m->changed + g, m->snap_valid[g] ? 0 : 1, sizeof(uint32_t), m->stream));
+        VCHECK(launch_occ_diff(m->occ[g0], m->snap + g0 * n_al, m->changed + g0, n_al, ng, m->stream));
+        for (int g = g0; g < g0 + ng; ++g) m->snap_valid[g] = true;
+    }
     VCHECK(launch_pass_x(t, m->stream));
     timing_end(m, slot);
     slot = timing_begin(m, VEDT_K_EDT_Y);

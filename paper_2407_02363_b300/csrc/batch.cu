@@ -334,8 +334,15 @@ vedt_status vedt_batch_set_grids(vedt_batch *b, int which) {
     return build_tables(b);
 }
 
+// A batch writes its maps' fields without their incremental snapshots: the next EDT of
+// an incremental map recomputes.
+static void invalidate_snapshots(vedt_batch *b) {
+    for (vedt_map *m : b->maps) m->snap_valid[0] = m->snap_valid[1] = false;
+}
+
 vedt_status vedt_batch_compute_edt(vedt_batch *b) {
     if (!b) return VEDT_EINVAL;
+    invalidate_snapshots(b);
     for (int md = 0; md < 2; ++md) {
         if (b->ngrid[md] == 0) continue;
         const GridTable &t = b->tab[md];
@@ -493,6 +500,7 @@ vedt_status vedt_batch_capture(vedt_batch *b) {
 
 vedt_status vedt_batch_replay(vedt_batch *b) {
     if (!b || !b->exec) return VEDT_EINVAL;
+    invalidate_snapshots(b);
     BCHECK(cudaGraphLaunch(b->exec, b->stream));
     return VEDT_OK;
 }

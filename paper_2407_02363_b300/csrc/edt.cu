@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) k_pass_x(const GridDesc *__restrict__ gd,
     int g = 0;
     for (int64_t r = warp; r < rows_total; r += nwarps) {
         while (g + 1 < ng && gd[g + 1].row_begin <= r) ++g;
+        if (gd[g].changed && *gd[g].changed == 0) continue;   // unchanged since its last EDT
         pass_x_row<S, SMALL>(gd[g], r - gd[g].row_begin, lane);
     }
 }
@@ -427,12 +428,14 @@ __device__ __forceinline__ void pass_x_small_row(uint8_t *xs, uint8_t *row_has, 
 // only when a row falls in another grid of the table.
 constexpr int kXRows = 4;
 
+template <bool INCR>
 struct RowGrid {
     const uint8_t *occ;
     uint8_t *xs, *row_has;
     int64_t begin, end;
     int X, Xp;
     bool vec;
+    bool skip = false;   // incremental map whose occupancy is unchanged since its last EDT
     int g = 0;
     // rows visited by one warp only increase, so the scan resumes from the current grid
     __device__ __forceinline__ void load(const GridDesc *__restrict__ gd, int ng, int64_t r) {
@@ -446,10 +449,14 @@ struct RowGrid {
         X = G.X;
         Xp = G.Xp;
         vec = (X & 7) == 0 && (reinterpret_cast<uintptr_t>(occ) & 7) == 0;
+        if constexpr (INCR) skip = G.changed && *G.changed == 0;
     }
     __device__ __forceinline__ bool has(int64_t r) const { return r >= begin && r < end; }
 };
 
+// INCR: the table's grids may be incremental maps; rows of a grid whose occupancy is
+// unchanged since its last EDT are skipped (the flag is read after the dependency wait).
+template <bool INCR>
 __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict__ gd, int ng, int64_t rows_total) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -459,13 +466,20 @@ __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict
     if (r >= rows_total) return;
     // one descriptor cache for the loads and one for the sweeps: each visits rows in
     // increasing order
-    RowGrid Gl, Gp;
-    Gl.load(gd, ng, r);
-    Gp.load(gd, ng, r);
-    pdl_wait();   // the occupancy comes from the previous kernels
+    RowGrid<INCR> Gl, Gp;
+    if constexpr (!INCR) {
+        Gl.load(gd, ng, r);
+        Gp.load(gd, ng, r);
+    }
+    pdl_wait();   // the occupancy (and the change flags) come from the previous kernels
+    if constexpr (INCR) {
+        Gl.load(gd, ng, r);
+        Gp.load(gd, ng, r);
+    }
     auto load = [&](int64_t rr) {
         if (rr >= rows_total) return make_uint2(0u, 0u);
         if (!Gl.has(rr)) Gl.load(gd, ng, rr);
+        if (INCR && Gl.skip) return make_uint2(0u, 0u);
         return row_bytes8(Gl.occ + (rr - Gl.begin) * Gl.X, Gl.X, 8 * lane, Gl.vec);
     };
     uint2 w[kXRows];
@@ -481,7 +495,7 @@ __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict
             const int64_t rr = r + q * nwarps;
             if (rr < rows_total) {
                 if (!Gp.has(rr)) Gp.load(gd, ng, rr);
-                pass_x_small_row(Gp.xs, Gp.row_has, Gp.Xp, rr - Gp.begin, lane, w[q]);
+                if (!(INCR && Gp.skip)) pass_x_small_row(Gp.xs, Gp.row_has, Gp.Xp, rr - Gp.begin, lane, w[q]);
             }
         }
         if (rn >= rows_total) break;
@@ -1090,6 +1104,7 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_y_small(const GridDesc *__r
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     pdl_wait();   // the staged tile and the validity flags come from the previous pass
+    if (gd[g].changed && *gd[g].changed == 0) return;   // unchanged since its last EDT
     tile_y_small<NB, L>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, 0, err);
 }
 
@@ -1105,6 +1120,7 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_z_small(const GridDesc *__r
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     pdl_wait();   // the staged tile and the validity flags come from the previous pass
+    if (gd[g].changed && *gd[g].changed == 0) return;   // unchanged since its last EDT
     tile_z_small<NB, L>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, 0, err);
 }
 
@@ -1465,14 +1481,16 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s) {
         static int per_sm = 0;
         if (per_sm == 0) {
             int occ = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass_x_small, 256, 0) != cudaSuccess || occ < 1)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass_x_small<false>, 256, 0) != cudaSuccess ||
+                occ < 1)
                 occ = 1;
             per_sm = occ;
         }
         const int64_t cap_small = static_cast<int64_t>(sm_count()) * per_sm;
         const int64_t want_small = (t.rows + 8 * kXRows - 1) / (8 * kXRows);
         const int nb = static_cast<int>(want_small < cap_small ? want_small : cap_small);
-        return launch_pdl(k_pass_x_small, dim3(nb), dim3(256), 0, s, t.desc, t.n, t.rows);
+        if (t.incr) return launch_pdl(k_pass_x_small<true>, dim3(nb), dim3(256), 0, s, t.desc, t.n, t.rows);
+        return launch_pdl(k_pass_x_small<false>, dim3(nb), dim3(256), 0, s, t.desc, t.n, t.rows);
     } else if (t.maxXp <= 256) {
         return launch_pdl(k_pass_x<8, false>, dim3(blocks), dim3(256), 0, s, t.desc, t.n, t.rows);
     } else if (t.maxXp <= 512) {

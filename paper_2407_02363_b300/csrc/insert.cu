@@ -33,6 +33,29 @@ __global__ void __launch_bounds__(256) k_clear(uint8_t *__restrict__ p, int64_t 
     for (int64_t i = h + (nvec << 4) + tid; i < n; i += stride) p[i] = 0;
 }
 
+// Change detection of incremental maps: compares grid blockIdx.y's occupancy (n_al bytes,
+// 16-byte words) with the snapshot taken at its last EDT, refreshes the snapshot where
+// they differ and sets changed[grid] (zeroed before the launch) if any byte differed.
+__global__ void __launch_bounds__(256) k_occ_diff(const uint8_t *__restrict__ occ, uint8_t *__restrict__ snap,
+                                                  uint32_t *__restrict__ changed, int64_t n_al) {
+    pdl_trigger();
+    pdl_wait();
+    const int g = blockIdx.y;
+    const uint4 *o = reinterpret_cast<const uint4 *>(occ + g * n_al);
+    uint4 *sp = reinterpret_cast<uint4 *>(snap + g * n_al);
+    const int64_t nvec = n_al >> 4;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    int diff = 0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nvec; i += stride) {
+        const uint4 a = o[i], b = sp[i];
+        if (a.x != b.x || a.y != b.y || a.z != b.z || a.w != b.w) {
+            sp[i] = a;
+            diff = 1;
+        }
+    }
+    if (__syncthreads_or(diff) && threadIdx.x == 0) changed[g] = 1u;
+}
+
 struct Pose12 { float T[12]; };
 
 // Insert(Point_Cloud) with robot-point removal (Alg. 2 line 7; Sec. III-A).
@@ -157,6 +180,15 @@ cudaError_t launch_clear(uint8_t *p, int64_t n, cudaStream_t s) {
     const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
     const int blocks = static_cast<int>(want < 1 ? 1 : (want < cap ? want : cap));
     return launch_pdl(k_clear, dim3(blocks), dim3(256), 0, s, p, n);
+}
+
+cudaError_t launch_occ_diff(const uint8_t *occ, uint8_t *snap, uint32_t *changed, int64_t n_al, int grids,
+                            cudaStream_t s) {
+    if (n_al <= 0 || grids < 1) return cudaSuccess;
+    const int64_t want = (n_al / 16 + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 8 / grids;
+    const int blocks = static_cast<int>(want < 1 ? 1 : (want < cap ? want : (cap < 1 ? 1 : cap)));
+    return launch_pdl(k_occ_diff, dim3(blocks, grids), dim3(256), 0, s, occ, snap, changed, n_al);
 }
 
 cudaError_t launch_insert_points(uint8_t *env, const uint8_t *self, int X, int Y, int Z, float vs,

@@ -34,6 +34,8 @@ struct GridDesc {
     int64_t ty_begin;       // prefix over pass-Y tiles ((Xp/32)*Z)
     int64_t tz_begin;       // prefix over pass-Z tiles ((Xp/32)*Y)
     int64_t xi_begin;       // prefix over persistent pass-X items (ceil(Y*Z / rows_per_item))
+    const uint32_t *changed;  // NULL, or a device word: 0 = occupancy unchanged since this
+                              // grid's last EDT (incremental maps), so the passes skip it
 };
 
 // Work counters of one persistent EDT launch (device memory, zeroed before the launch).
@@ -53,6 +55,7 @@ struct GridTable {
     int64_t rows, tiles_y, tiles_z;
     int32_t *err;                // device error word
     int bands;                   // bands per line in passes Y and Z (0: the default)
+    int incr;                    // 1: pass X honours GridDesc::changed (incremental maps)
 };
 
 // Launch with programmatic stream serialization: the kernel may start while the previous
@@ -89,6 +92,8 @@ cudaError_t launch_wait_selftest(const unsigned *counter, uint32_t limit, int32_
 // launchers (insert.cu)
 struct LinkPose { float T[VEDT_MAX_LINKS][12]; };
 cudaError_t launch_clear(uint8_t *p, int64_t n, cudaStream_t s);
+cudaError_t launch_occ_diff(const uint8_t *occ, uint8_t *snap, uint32_t *changed, int64_t n_al, int grids,
+                            cudaStream_t s);
 cudaError_t launch_insert_points(uint8_t *env, const uint8_t *self, int X, int Y, int Z, float vs,
                                  const float *origin, const float *xyz, int64_t n, const float *T,
                                  int filter_self, int64_t *counts, cudaStream_t s);
@@ -133,6 +138,13 @@ struct vedt_map {
     void *s2[2] = {nullptr, nullptr};
     uint8_t *slice_has[2] = {nullptr, nullptr};
     int32_t *err = nullptr;
+    // incremental EDT: per grid, 1 iff the last vedt_compute_edt recomputed it (always 1
+    // unless incremental); snapshot of each grid's occupancy at its last EDT (both grids
+    // in one allocation, same layout as occ)
+    uint32_t *changed = nullptr;
+    uint8_t *snap = nullptr;
+    int incremental = 0;
+    bool snap_valid[2] = {false, false};   // fields match the snapshot (host view)
     // EDT launch tables for which = ENV (0), SELF (1), BOTH (2)
     GridTable tab[3];
     void *tab_mem = nullptr;

@@ -48,6 +48,8 @@ _sig = {
     "vedt_map_destroy": [_P],
     "vedt_map_set_stream": [_P, _P],
     "vedt_map_set_bands": [_P, _I32],
+    "vedt_map_set_incremental": [_P, _I32],
+    "vedt_map_edt_recomputed": [_P, _I32, _P],
     "vedt_map_info": [_P, _P, _P, _P],
     "vedt_clear": [_P, _I32],
     "vedt_insert_pointcloud": [_P, _P, _I64, _P, _I32, _P],
@@ -225,6 +227,16 @@ class Map:
         """Bands per line of EDT passes Y and Z (0: default; 1/2/4/8 for dims <= 256, 4/8
         above)."""
         _chk(_lib.vedt_map_set_bands(self._h, int(bands)), "vedt_map_set_bands")
+
+    def set_incremental(self, on=True):
+        """Skip the EDT of a grid whose occupancy is unchanged since its last EDT."""
+        _chk(_lib.vedt_map_set_incremental(self._h, 1 if on else 0), "vedt_map_set_incremental")
+
+    def edt_recomputed(self, which=MAP_BOTH):
+        """Per selected grid (env first): did the last compute_edt recompute it?"""
+        out = np.zeros(2, dtype=np.int32)
+        _chk(_lib.vedt_map_edt_recomputed(self._h, int(which), _np_ptr(out)), "vedt_map_edt_recomputed")
+        return [bool(v) for v in out[: 2 if which == MAP_BOTH else 1]]
 
     def clear(self, which=MAP_BOTH):
         _chk(_lib.vedt_clear(self._h, which), "vedt_clear")
