@@ -12,6 +12,8 @@ Contents (each function cites the passage it follows):
   query_spheres   Eq. (dist), Alg. 2 line 10, Alg. 3 lines 3-4        (C, fp32)
   fk, sphere_centres   ForwardKinematics, Alg. 2 lines 5 and 8         (Python, fp64)
   mlp_*           learned surrogate reference (not in the paper)       (numpy, fp64)
+  sor.sor_filter  statistical outlier filter of the raw cloud, Sec. III-A
+                  (oracle/sor.py: numpy brute-force kNN, fp64, exact sums)
 """
 from __future__ import annotations
 
