@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--sur-steps", type=int, default=20000, help="surrogate AdamW steps (batch 8192)")
     p.add_argument("--serve-frames", type=int, default=80, help="frames per arrival rate in the serving leg (0: skip)")
     p.add_argument("--paper-reps", type=int, default=50, help="EDT launches per map size in the paper-sizes leg (0: skip)")
+    p.add_argument("--sor-reps", type=int, default=20,
+                   help="calls per setting of the outlier-filter leg (0: skip)")
     p.add_argument("--static-frames", type=int, default=200,
                    help="frames of the static-scene leg, incremental EDT off and on (0: skip)")
     return p.parse_args()
@@ -385,6 +387,7 @@ def run_vedt(args):
     if args.e2e_steps > 0:
         e2e = run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream)
     m.close()
+    sor_leg = run_outlier_filter(args, v, clouds[0], dev) if (args.sor_reps > 0 and rank == 0) else None
     static = None
     if args.static_frames > 0 and rank == 0:
         static = run_static_scene(args, v, W, clouds[0], centres, radii, m_sph, cchain, dev)
@@ -411,13 +414,39 @@ def run_vedt(args):
                            "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
             "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
             "batched": batched, "surrogate": sur, "serving": srv, "paper_sizes": paper,
-            "static_scene": static,
+            "static_scene": static, "outlier_filter": sor_leg,
             "gpu_launches": int(round(sum(k["launches"] for k in kernels.values()) / kernel_frames * args.steps)),
             "kernels_from": f"{kernel_frames} frames right after the timed region, CUDA events around each launch "
                             "on the library's stream",
             "clocks": clk,
         }
         print(json.dumps(line))
+
+
+def run_outlier_filter(args, v, cloud, dev):
+    """The statistical outlier filter of Sec. III-A (vedt_sor_filter) on the frame256 cloud
+    (300k points): device time per call for k = 10 and k = 50 neighbours, std_mul = 1."""
+    import torch
+    n = int(cloud.shape[0])
+    f = v.OutlierFilter(n, stream=torch.cuda.current_stream(dev))
+    keep = torch.empty(n, dtype=torch.uint8, device=dev)
+    out = {"what": "statistical outlier filter (exact kNN mean distance, mean + 1 std threshold) on the "
+                   "frame256 cloud, device time per call", "points": n, "runs": {}}
+    for k in (10, 50):
+        for _ in range(3):
+            f.filter(cloud, keep, k=k, std_mul=1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(args.sor_reps):
+            f.filter(cloud, keep, k=k, std_mul=1.0)
+        b.record()
+        torch.cuda.synchronize()
+        (mean, std, thr), (valid, kept) = f.stats()
+        out["runs"][str(k)] = {"ms": a.elapsed_time(b) / args.sor_reps, "kept": kept, "valid": valid,
+                               "mean_knn_m": mean, "std_m": std, "threshold_m": thr}
+    f.close()
+    return out
 
 
 def run_static_scene(args, v, W, cloud, centres, radii, m_sph, cchain, dev):

@@ -145,6 +145,13 @@ vedt_status vedt_insert_pointcloud(vedt_map *map, const float *xyz_dev, int64_t 
                                    const float *T_world_sensor_host, int filter_self,
                                    int64_t *counts_dev);
 
+/* As vedt_insert_pointcloud, but point i is inserted only if keep_dev[i] != 0 (device
+ * uint8 per point, e.g. the output of vedt_sor_filter; NULL keeps every point).  Dropped
+ * points are not counted.  Errors: EINVAL. */
+vedt_status vedt_insert_pointcloud_masked(vedt_map *map, const float *xyz_dev, int64_t n_points,
+                                          const float *T_world_sensor_host, int filter_self,
+                                          const uint8_t *keep_dev, int64_t *counts_dev);
+
 /* Registers the offline link voxel models (Sec. III-A): link k's model is
  * link_xyz_host[k], n_vox[k] fp32 xyz points in the link frame.  Copied to the device
  * once (synchronously); replaces any earlier registration.  Link 0 is the static body.
@@ -346,6 +353,38 @@ vedt_status vedt_mlp_train_step(vedt_mlp *net, const float *q_dev, const float *
                                 float lr, float wd, float *loss_sums_dev);
 /* Synchronises; ETIMEOUT if an in-kernel wait expired. */
 vedt_status vedt_mlp_check(vedt_mlp *net);
+
+/* ---- statistical outlier filter of the raw cloud (Sec. III-A) ---------------------------- */
+
+/* Sec. III-A filters the raw cloud by each point's distances to its neighbours before it
+ * is transformed and inserted; the paper gives no parameters.  Here: d_i = mean Euclidean
+ * distance of point i to its k nearest other valid points (valid: all coordinates
+ * finite), and point i is kept iff it is valid and d_i <= mean(d) + std_mul * std(d) over
+ * the valid points (sample standard deviation).  Exact kNN; squared distances in float64
+ * from the float32 coordinates, the k square roots summed in ascending order, the cloud's
+ * sums kept exactly as 128-bit fixed-point integers (units of 2^-80 m), so the decision is
+ * reproducible bit for bit.  Distances must stay below 2^20 (metres) for exact sums. */
+typedef struct vedt_sor vedt_sor;
+
+/* A filter for clouds of up to max_points points (device scratch of about 40 bytes per
+ * point plus a cell grid of up to 2*max_points cells), ordered on `stream` (cudaStream_t).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+vedt_status vedt_sor_create(int64_t max_points, void *stream, vedt_sor **out);
+vedt_status vedt_sor_destroy(vedt_sor *f);   /* synchronises; NULL is a no-op */
+
+/* keep_dev[i] = 1 if point i (xyz_dev: n float32 triples on the device) is kept, else 0.
+ * 1 <= k <= 64, std_mul finite, 0 <= n <= max_points.  Asynchronous on the filter's
+ * stream; xyz_dev and keep_dev must stay valid until it completes.  Errors: EINVAL, ECUDA. */
+vedt_status vedt_sor_filter(vedt_sor *f, const float *xyz_dev, int64_t n, int k, double std_mul,
+                            uint8_t *keep_dev);
+
+/* After the stream drains: stats_out = {mean, std, threshold} of the last filter call,
+ * counts_out = {valid points, kept points} (either may be NULL).  Synchronises. */
+vedt_status vedt_sor_stats(vedt_sor *f, double stats_out[3], int64_t counts_out[2]);
+
+/* Borrowed device pointer to the last call's d_i (float64 per input point; entries of
+ * invalid points are not written).  Valid until the next filter call or destroy. */
+vedt_status vedt_sor_mean_distances(vedt_sor *f, const double **d_dev);
 
 /* ---- EDT without device allocation -------------------------------------------------------- */
 

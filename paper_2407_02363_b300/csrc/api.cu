@@ -358,15 +358,20 @@ vedt_status vedt_clear(vedt_map *m, int which) {
     return VEDT_OK;
 }
 
-vedt_status vedt_insert_pointcloud(vedt_map *m, const float *xyz_dev, int64_t n, const float *T,
-                                   int filter_self, int64_t *counts_dev) {
+vedt_status vedt_insert_pointcloud_masked(vedt_map *m, const float *xyz_dev, int64_t n, const float *T,
+                                          int filter_self, const uint8_t *keep_dev, int64_t *counts_dev) {
     if (!m || n < 0 || (n > 0 && !xyz_dev)) return VEDT_EINVAL;
     if (n == 0) return VEDT_OK;
     const int slot = timing_begin(m, VEDT_K_INSERT_POINTS);
     VCHECK(launch_insert_points(m->occ[0], m->occ[1], m->X, m->Y, m->Z, m->vs, m->origin, xyz_dev, n, T,
-                                filter_self ? 1 : 0, counts_dev, m->stream));
+                                filter_self ? 1 : 0, keep_dev, counts_dev, m->stream));
     timing_end(m, slot);
     return VEDT_OK;
+}
+
+vedt_status vedt_insert_pointcloud(vedt_map *m, const float *xyz_dev, int64_t n, const float *T,
+                                   int filter_self, int64_t *counts_dev) {
+    return vedt_insert_pointcloud_masked(m, xyz_dev, n, T, filter_self, nullptr, counts_dev);
 }
 
 vedt_status vedt_register_links(vedt_map *m, int n_links, const float *const *xyz, const int64_t *n_vox) {

@@ -62,12 +62,14 @@ struct Pose12 { float T[12]; };
 __global__ void __launch_bounds__(256) k_insert_points(uint8_t *__restrict__ env, const uint8_t *__restrict__ self,
                                                        int X, int Y, int Z, float vs, Origin org,
                                                        const float *__restrict__ xyz, int64_t n, Pose12 T, int use_T,
-                                                       int filter_self, unsigned long long *counts) {
+                                                       int filter_self, const uint8_t *__restrict__ keep,
+                                                       unsigned long long *counts) {
     pdl_trigger();
     pdl_wait();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     unsigned long long written = 0, outside = 0, filtered = 0;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (keep && !keep[i]) continue;   // dropped by the outlier filter
         float wx = __ldg(xyz + 3 * i), wy = __ldg(xyz + 3 * i + 1), wz = __ldg(xyz + 3 * i + 2);
         if (use_T) rigid(T.T, wx, wy, wz, wx, wy, wz);
         int vx, vy, vz;
@@ -193,7 +195,7 @@ cudaError_t launch_occ_diff(const uint8_t *occ, uint8_t *snap, uint32_t *changed
 
 cudaError_t launch_insert_points(uint8_t *env, const uint8_t *self, int X, int Y, int Z, float vs,
                                  const float *origin, const float *xyz, int64_t n, const float *T,
-                                 int filter_self, int64_t *counts, cudaStream_t s) {
+                                 int filter_self, const uint8_t *keep, int64_t *counts, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     Origin o{{origin[0], origin[1], origin[2]}};
     Pose12 P{};
@@ -203,7 +205,7 @@ cudaError_t launch_insert_points(uint8_t *env, const uint8_t *self, int X, int Y
     const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
     const int blocks = static_cast<int>(want < cap ? want : cap);
     return launch_pdl(k_insert_points, dim3(blocks), dim3(256), 0, s, env, self, X, Y, Z, vs, o, xyz, n, P,
-                      T != nullptr ? 1 : 0, filter_self, reinterpret_cast<unsigned long long *>(counts));
+                      T != nullptr ? 1 : 0, filter_self, keep, reinterpret_cast<unsigned long long *>(counts));
 }
 
 cudaError_t launch_insert_links(uint8_t *self, int X, int Y, int Z, float vs, const float *origin,

@@ -96,7 +96,7 @@ cudaError_t launch_occ_diff(const uint8_t *occ, uint8_t *snap, uint32_t *changed
                             cudaStream_t s);
 cudaError_t launch_insert_points(uint8_t *env, const uint8_t *self, int X, int Y, int Z, float vs,
                                  const float *origin, const float *xyz, int64_t n, const float *T,
-                                 int filter_self, int64_t *counts, cudaStream_t s);
+                                 int filter_self, const uint8_t *keep, int64_t *counts, cudaStream_t s);
 cudaError_t launch_insert_links(uint8_t *self, int X, int Y, int Z, float vs, const float *origin,
                                 const float *pts, const uint8_t *link_of, int64_t n,
                                 const LinkPose &poses, uint32_t mask, cudaStream_t s);

@@ -53,6 +53,12 @@ _sig = {
     "vedt_map_info": [_P, _P, _P, _P],
     "vedt_clear": [_P, _I32],
     "vedt_insert_pointcloud": [_P, _P, _I64, _P, _I32, _P],
+    "vedt_insert_pointcloud_masked": [_P, _P, _I64, _P, _I32, _P, _P],
+    "vedt_sor_create": [_I64, _P, _P],
+    "vedt_sor_destroy": [_P],
+    "vedt_sor_filter": [_P, _P, _I64, _I32, ctypes.c_double, _P],
+    "vedt_sor_stats": [_P, _P, _P],
+    "vedt_sor_mean_distances": [_P, _P],
     "vedt_register_links": [_P, _I32, _P, _P],
     "vedt_insert_links": [_P, _P, _U32],
     "vedt_fk": [_P, _P, _P],
@@ -250,6 +256,16 @@ class Map:
                                          1 if filter_self else 0, dev_ptr(counts_dev)),
              "vedt_insert_pointcloud")
 
+    def insert_pointcloud_masked(self, xyz_dev, keep_dev, n=None, T_world_sensor=None, filter_self=False,
+                                 counts_dev=None):
+        n = int(xyz_dev.shape[0]) if n is None else int(n)
+        T = None
+        if T_world_sensor is not None:
+            T = np.ascontiguousarray(T_world_sensor, dtype=np.float32).reshape(12)
+        _chk(_lib.vedt_insert_pointcloud_masked(self._h, dev_ptr(xyz_dev), n, None if T is None else _np_ptr(T),
+                                                1 if filter_self else 0, dev_ptr(keep_dev), dev_ptr(counts_dev)),
+             "vedt_insert_pointcloud_masked")
+
     def register_links(self, link_points):
         arrs = [np.ascontiguousarray(p, dtype=np.float32).reshape(-1, 3) for p in link_points]
         ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
@@ -384,6 +400,44 @@ class Map:
         src = torch.as_tensor(np.ascontiguousarray(occ, dtype=np.uint8)) if isinstance(occ, np.ndarray) else occ
         dst.copy_(src.reshape(dst.shape))
         torch.cuda.synchronize()
+
+
+class OutlierFilter:
+    """Statistical outlier filter of a raw cloud (vedt_sor_*): keep flags per point."""
+
+    def __init__(self, max_points, stream=None):
+        h = ctypes.c_void_p()
+        _chk(_lib.vedt_sor_create(int(max_points), stream_handle(stream), ctypes.byref(h)), "vedt_sor_create")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            _lib.vedt_sor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def filter(self, xyz_dev, keep_dev, k=50, std_mul=1.0, n=None):
+        n = int(xyz_dev.shape[0]) if n is None else int(n)
+        _chk(_lib.vedt_sor_filter(self._h, dev_ptr(xyz_dev), n, int(k), float(std_mul), dev_ptr(keep_dev)),
+             "vedt_sor_filter")
+
+    def stats(self):
+        """((mean, std, threshold), (valid points, kept points)) of the last call."""
+        st = np.zeros(3, np.float64)
+        ct = np.zeros(2, np.int64)
+        _chk(_lib.vedt_sor_stats(self._h, _np_ptr(st), _np_ptr(ct)), "vedt_sor_stats")
+        return tuple(float(v) for v in st), tuple(int(v) for v in ct)
+
+    def mean_distances(self, n):
+        """The last call's d_i as a borrowed float64 device view of n entries."""
+        p = ctypes.c_void_p()
+        _chk(_lib.vedt_sor_mean_distances(self._h, ctypes.byref(p)), "vedt_sor_mean_distances")
+        return device_view(p.value, (int(n),), "<f8")
 
 
 class Batch:
