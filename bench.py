@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--sur-steps", type=int, default=20000, help="surrogate AdamW steps (batch 8192)")
     p.add_argument("--serve-frames", type=int, default=80, help="frames per arrival rate in the serving leg (0: skip)")
     p.add_argument("--paper-reps", type=int, default=50, help="EDT launches per map size in the paper-sizes leg (0: skip)")
+    p.add_argument("--loop-frames", type=int, default=150,
+                   help="cycles of the closed-loop controller leg, with and without avoidance (0: skip)")
     p.add_argument("--sor-reps", type=int, default=20,
                    help="calls per setting of the outlier-filter leg (0: skip)")
     p.add_argument("--static-frames", type=int, default=200,
@@ -388,6 +390,7 @@ def run_vedt(args):
         e2e = run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream)
     m.close()
     sor_leg = run_outlier_filter(args, v, clouds[0], dev) if (args.sor_reps > 0 and rank == 0) else None
+    loop = run_closed_loop_leg(args, v) if (args.loop_frames > 0 and rank == 0) else None
     static = None
     if args.static_frames > 0 and rank == 0:
         static = run_static_scene(args, v, W, clouds[0], centres, radii, m_sph, cchain, dev)
@@ -414,13 +417,32 @@ def run_vedt(args):
                            "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
             "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
             "batched": batched, "surrogate": sur, "serving": srv, "paper_sizes": paper,
-            "static_scene": static, "outlier_filter": sor_leg,
+            "static_scene": static, "outlier_filter": sor_leg, "closed_loop": loop,
             "gpu_launches": int(round(sum(k["launches"] for k in kernels.values()) / kernel_frames * args.steps)),
             "kernels_from": f"{kernel_frames} frames right after the timed region, CUDA events around each launch "
                             "on the library's stream",
             "clocks": clk,
         }
         print(json.dumps(line))
+
+
+def run_closed_loop_leg(args, v):
+    """Algs. 2-3 closed: a 7-DoF arm reaching while a 12 cm sphere obstacle (2000 surface
+    points) sweeps through it, 96^3 maps at 2 cm, one library frame from host buffers plus
+    one task-priority controller step per cycle.  Wall time per cycle (host FK and
+    controller included) and the smallest geometric clearance, with and without the
+    avoidance tasks."""
+    from paper_2407_02363_b300 import control
+    out = {"what": "closed control loop: library frame (host buffers) + task-priority controller per cycle",
+           "frames": args.loop_frames}
+    for name, avoid in (("avoidance", True), ("no_avoidance", False)):
+        control.run_closed_loop(v, n_frames=10, avoid=avoid)          # warm-up
+        t0 = time.perf_counter()
+        r = control.run_closed_loop(v, n_frames=args.loop_frames, avoid=avoid)
+        dt = time.perf_counter() - t0
+        out[name] = {"min_clearance_m": r["min_clearance_m"], "tip_error_m": r["tip_error_m"],
+                     "ms_per_cycle_wall": dt / args.loop_frames * 1e3}
+    return out
 
 
 def run_outlier_filter(args, v, cloud, dev):

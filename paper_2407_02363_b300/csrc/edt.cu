@@ -1506,7 +1506,7 @@ static cudaError_t launch_persistent_impl(const GridTable &t, const PersistCount
     const size_t sy = smem_y(t), sz = smem_z(t);
     const size_t sm = sy > sz ? sy : sz;
     auto k = k_edt_persistent<S, SMALL>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+    cudaError_t e = ensure_dyn_smem<k_edt_persistent<S, SMALL>>(sm);
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kLanes, sm);
@@ -1529,11 +1529,11 @@ cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int 
     return launch_persistent_impl<32, false>(t, c, ctas_per_sm, rows_per_item, s);
 }
 
-template <int NB, class K>
-static cudaError_t launch_small(K kernel, int64_t tiles, int sm, const GridTable &t, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+template <int NB, auto K>
+static cudaError_t launch_small(int64_t tiles, int sm, const GridTable &t, cudaStream_t s) {
+    const cudaError_t e = ensure_dyn_smem<K>(static_cast<size_t>(sm));
     if (e != cudaSuccess) return e;
-    return launch_pdl(kernel, dim3(static_cast<unsigned>(tiles)), dim3(NB * kTile), static_cast<size_t>(sm), s, t.desc,
+    return launch_pdl(K, dim3(static_cast<unsigned>(tiles)), dim3(NB * kTile), static_cast<size_t>(sm), s, t.desc,
                       t.tmaps, t.n, t.err);
 }
 
@@ -1551,14 +1551,14 @@ cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) {
     const int nb = bands_for(t, t.maxY);
     if (!t.large) {
         switch (nb) {
-            case 1: return launch_small<1>(k_pass_y_small<1, false>, t.tiles_y, small_smem<1, PolY<false>>(t.maxY), t, s);
-            case 2: return launch_small<2>(k_pass_y_small<2, false>, t.tiles_y, small_smem<2, PolY<false>>(t.maxY), t, s);
-            case 8: return launch_small<8>(k_pass_y_small<8, false>, t.tiles_y, small_smem<8, PolY<false>>(t.maxY), t, s);
-            default: return launch_small<4>(k_pass_y_small<4, false>, t.tiles_y, small_smem<4, PolY<false>>(t.maxY), t, s);
+            case 1: return launch_small<1, k_pass_y_small<1, false>>(t.tiles_y, small_smem<1, PolY<false>>(t.maxY), t, s);
+            case 2: return launch_small<2, k_pass_y_small<2, false>>(t.tiles_y, small_smem<2, PolY<false>>(t.maxY), t, s);
+            case 8: return launch_small<8, k_pass_y_small<8, false>>(t.tiles_y, small_smem<8, PolY<false>>(t.maxY), t, s);
+            default: return launch_small<4, k_pass_y_small<4, false>>(t.tiles_y, small_smem<4, PolY<false>>(t.maxY), t, s);
         }
     }
-    if (nb == 4) return launch_small<4>(k_pass_y_small<4, true>, t.tiles_y, small_smem<4, PolY<true>>(t.maxY), t, s);
-    return launch_small<8>(k_pass_y_small<8, true>, t.tiles_y, small_smem<8, PolY<true>>(t.maxY), t, s);
+    if (nb == 4) return launch_small<4, k_pass_y_small<4, true>>(t.tiles_y, small_smem<4, PolY<true>>(t.maxY), t, s);
+    return launch_small<8, k_pass_y_small<8, true>>(t.tiles_y, small_smem<8, PolY<true>>(t.maxY), t, s);
 }
 
 cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s) {
@@ -1566,14 +1566,14 @@ cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s) {
     const int nb = bands_for(t, t.maxZ);
     if (!t.large) {
         switch (nb) {
-            case 1: return launch_small<1>(k_pass_z_small<1, false>, t.tiles_z, small_smem<1, PolZ<false>>(t.maxZ), t, s);
-            case 2: return launch_small<2>(k_pass_z_small<2, false>, t.tiles_z, small_smem<2, PolZ<false>>(t.maxZ), t, s);
-            case 8: return launch_small<8>(k_pass_z_small<8, false>, t.tiles_z, small_smem<8, PolZ<false>>(t.maxZ), t, s);
-            default: return launch_small<4>(k_pass_z_small<4, false>, t.tiles_z, small_smem<4, PolZ<false>>(t.maxZ), t, s);
+            case 1: return launch_small<1, k_pass_z_small<1, false>>(t.tiles_z, small_smem<1, PolZ<false>>(t.maxZ), t, s);
+            case 2: return launch_small<2, k_pass_z_small<2, false>>(t.tiles_z, small_smem<2, PolZ<false>>(t.maxZ), t, s);
+            case 8: return launch_small<8, k_pass_z_small<8, false>>(t.tiles_z, small_smem<8, PolZ<false>>(t.maxZ), t, s);
+            default: return launch_small<4, k_pass_z_small<4, false>>(t.tiles_z, small_smem<4, PolZ<false>>(t.maxZ), t, s);
         }
     }
-    if (nb == 4) return launch_small<4>(k_pass_z_small<4, true>, t.tiles_z, small_smem<4, PolZ<true>>(t.maxZ), t, s);
-    return launch_small<8>(k_pass_z_small<8, true>, t.tiles_z, small_smem<8, PolZ<true>>(t.maxZ), t, s);
+    if (nb == 4) return launch_small<4, k_pass_z_small<4, true>>(t.tiles_z, small_smem<4, PolZ<true>>(t.maxZ), t, s);
+    return launch_small<8, k_pass_z_small<8, true>>(t.tiles_z, small_smem<8, PolZ<true>>(t.maxZ), t, s);
 }
 
 }  // namespace vedt

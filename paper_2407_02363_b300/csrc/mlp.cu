@@ -736,8 +736,7 @@ template <int N, int EPI>
 cudaError_t gemm(const bf16 *A, int lda, int rows_a, int M, const bf16 *B, int ldb, int K, int k_split,
                  const EpiArgs &ep, int32_t *err, cudaStream_t s) {
     const size_t smem = 128 * 64 * 2 + static_cast<size_t>(N) * 64 * 2;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm<N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = ensure_dyn_smem<k_gemm<N, EPI>>(smem);
     if (e != cudaSuccess) return e;
     const int splits = (K + k_split - 1) / k_split;
     dim3 grid((M + 127) / 128, 1, splits);

@@ -674,9 +674,7 @@ vedt_status vedt_sor_filter(vedt_sor *f, const float *xyz_dev, int64_t n, int k,
     k_scan_add<<<sb, 1024, 0, s>>>(f->start, f->sums, ncs);
     k_sor_scatter<<<nb, 256, 0, s>>>(xyz_dev, n, f->cell_of, f->rank, f->start, f->sorted);
     const size_t knn_smem = sizeof(unsigned long long) * (k + kExtra) * kKnnThreads;
-    if (cudaFuncSetAttribute(k_sor_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(knn_smem)) !=
-        cudaSuccess)
-        return VEDT_ECUDA;
+    if (ensure_dyn_smem<k_sor_knn>(knn_smem) != cudaSuccess) return VEDT_ECUDA;
     k_sor_knn<<<static_cast<unsigned>((n + kKnnThreads - 1) / kKnnThreads), kKnnThreads, knn_smem, s>>>(
         f->sorted, f->start, f->plan, k, f->d);
     k_sor_sums<<<kStatBlocks, 256, 0, s>>>(f->d, f->cell_of, n, f->part);

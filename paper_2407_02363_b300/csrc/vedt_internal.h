@@ -1,5 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libvedt.
 #pragma once
+#include <atomic>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -75,6 +77,21 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`, calling the runtime
+// only when the limit grows (the attribute call costs far more host time than a launch).
+template <auto Kernel>
+cudaError_t ensure_dyn_smem(size_t bytes) {
+    static std::atomic<size_t> have{0};
+    if (bytes <= have.load(std::memory_order_acquire)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(bytes));
+    if (e != cudaSuccess) return e;
+    size_t h = have.load(std::memory_order_acquire);
+    while (h < bytes && !have.compare_exchange_weak(h, bytes, std::memory_order_acq_rel)) {
+    }
+    return cudaSuccess;
 }
 
 // host-side helpers (api.cu)

@@ -1,0 +1,19 @@
+"""The closed loop of Algs. 2-3 on the GPU: every cycle runs one library frame (clear,
+insert the arm and the obstacle cloud, EDT of both maps, sphere queries) and one step of
+the task-priority controller.  With the avoidance tasks the bounding spheres stay clear
+of a sphere obstacle sweeping through the arm; without them the obstacle hits the arm."""
+import pytest
+
+from paper_2407_02363_b300 import control
+from gpu_helpers import lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("seed", [3, 7])
+def test_closed_loop_avoids_the_sweeping_obstacle(seed):
+    v = lib()
+    with_tasks = control.run_closed_loop(v, seed=seed, avoid=True)
+    without = control.run_closed_loop(v, seed=seed, avoid=False)
+    assert with_tasks["min_clearance_m"] > 0.0
+    assert without["min_clearance_m"] < -0.05
