@@ -99,28 +99,30 @@ def avoidance_tasks(results, centres, radii, poses, spheres, params, self_mask=N
     reference rates.  Spheres with no obstacle, outside the grid, or masked for the self
     map contribute no row."""
     m = len(radii)
-    rows, acts, refs = [], [], []
-    for blk in (0, 1):
-        for i in range(m):
-            if blk == 1 and self_mask is not None and not self_mask[i]:
-                continue
-            r = results[blk * m + i]
-            if int(r["status"]) != 0:
-                continue
-            O = np.array(r["nearest"], np.float64)
-            C = np.asarray(centres[i], np.float64)
-            d = O - C
-            x = float(np.linalg.norm(d))
-            x_m = float(radii[i]) + params.margin
-            a = float(activation(x, x_m, params.buffer))
-            if a == 0.0 or x == 0.0:
-                continue
-            Jc = position_jacobian(poses, int(spheres.link[i]), C)
-            rows.append(-(d / x) @ Jc)
-            acts.append(a)
-            refs.append(params.kappa * (x_m + params.buffer - x))
-    n = np.asarray(poses).shape[0] - 1
-    return (np.array(rows).reshape(-1, n), np.array(acts), np.array(refs))
+    P = np.asarray(poses, np.float64)
+    n = P.shape[0] - 1
+    o, z = joint_axes(P)
+    C = np.asarray(centres, np.float64)
+    links = np.asarray(spheres.link, np.int64)
+    # position Jacobians of all sphere centres: (m, 3, n), column j zero past the link
+    Jc = np.cross(z[None, :, :], C[:, None, :] - o[None, :, :])          # (m, n, 3)
+    Jc = np.where((np.arange(n)[None, :] < links[:, None])[:, :, None], Jc, 0.0).transpose(0, 2, 1)
+    res = np.asarray(results)
+    keep = np.ones(2 * m, bool)
+    if self_mask is not None:
+        keep[m:] = np.asarray(self_mask, bool)
+    keep &= res["status"] == 0
+    O = res["nearest"].astype(np.float64)
+    sph = np.concatenate([np.arange(m), np.arange(m)])
+    d = O - C[sph]
+    x = np.linalg.norm(d, axis=1)
+    x_m = np.asarray(radii, np.float64)[sph] + params.margin
+    a = activation(x, x_m, params.buffer)
+    keep &= (a > 0.0) & (x > 0.0)
+    idx = np.nonzero(keep)[0]
+    u = d[idx] / x[idx, None]
+    rows = -np.einsum("ka,kaj->kj", u, Jc[sph[idx]])
+    return rows.reshape(-1, n), a[idx], params.kappa * (x_m[idx] + params.buffer - x[idx])
 
 
 def fibonacci_sphere(n, radius):
