@@ -63,6 +63,17 @@ def test_null_handle_calls_rejected(v):
     assert L.vedt_map_destroy(None) == v.OK
     assert L.vedt_check(None) == v.EINVAL
     assert L.vedt_fk(None, None, None) == v.EINVAL
+    assert L.vedt_map_set_bands(None, 4) == v.EINVAL
+    assert L.vedt_map_set_incremental(None, 1) == v.EINVAL
+    assert L.vedt_map_edt_recomputed(None, 3, None) == v.EINVAL
+    assert L.vedt_insert_pointcloud_masked(None, None, 10, None, 0, None, None) == v.EINVAL
+    assert L.vedt_sor_filter(None, None, 10, 8, 1.0, None) == v.EINVAL
+    assert L.vedt_sor_stats(None, None, None) == v.EINVAL
+    assert L.vedt_sor_mean_distances(None, None) == v.EINVAL
+    assert L.vedt_sor_destroy(None) == v.OK
+    out = ctypes.c_void_p()
+    for bad in (0, -5):
+        assert L.vedt_sor_create(bad, None, ctypes.byref(out)) == v.EINVAL
 
 
 def test_fk_matches_oracle(v, oracle_mod):
