@@ -2,31 +2,31 @@
 //
 //   pass X  (Step 1, BandSweep + PropagateAcrossBand): for every voxel the nearest
 //           occupied x in its row.  One warp per row, each lane owning a contiguous
-//           segment of S voxels: the segment's occupancy becomes an S-bit mask, a warp
-//           prefix-max / suffix-min of the segments' last / first occupied x carries the
-//           sites across segments, and two register sweeps finish each segment.
+//           segment of voxels: the segment's occupancy becomes a bit mask, a ballot of the
+//           non-empty segments and two shuffles give each lane the nearest sites left and
+//           right of its segment, and register sweeps finish each segment.
 //   pass Y  (Steps 2-3, ComputeProximateSite + QueryNearestSite in every slice): per
 //           column (x, z) the lower envelope of the parabolas (x - x_s(y'))^2 + (y - y')^2.
 //   pass Z  (Step 4, the same along the stacking axis): per column (x, y) the lower
 //           envelope of g2(z') + (z - z')^2, producing sqdist and a nearest voxel index.
 //
-// Passes Y and Z run one 64-thread CTA per 32 adjacent columns: thread t owns column
-// (t & 31), the lower warp the lower half of every line and the upper warp the upper half
-// (the banding of Alg. 1 with m2 = m3 = 2), so every global access is coalesced across x
-// and all lanes of a warp scan the same positions.  The tile (32 columns x the whole line)
-// is staged into shared memory with TMA box loads.  Each thread keeps the stack of
-// proximate sites of its half explicitly in shared memory; after a CTA barrier both
-// threads of a column merge the two stacks at the junction, and each walks the merged
-// envelope forward over its own half.  The domination test is exact integer arithmetic
-// with h_s = f(s) + s^2:
+// Passes Y and Z run one CTA of NB warps per 32 adjacent columns (NB = 4 by default, 8
+// for lines longer than 256; the m2 / m3 banding of Alg. 1): lane t owns column t, warp b
+// the b-th band of every line, so every global access is coalesced across x and all lanes
+// of a warp scan the same positions.  The tile (32 columns x the whole line) is staged
+// into shared memory with TMA box loads.  Each warp builds its band's stacks of proximate
+// sites in place in the staged tile; after a CTA barrier warp 0 joins the bands of each
+// column (the junction repair) and publishes the kept ranges, and every warp walks the
+// merged envelope over its band.  The persistent batch kernel runs two-band tiles of 64
+// threads.  The domination test is exact integer arithmetic with h_s = f(s) + s^2:
 //   b (above a) is dropped under c  iff  (h_c - h_b)(b - a) <= (h_b - h_a)(c - b),
 // i.e. c overtakes b no later than b overtakes a.  In the query the next proximate site
 // p+1 is strictly nearer to voxel j iff h_(p+1) - h_p < 2 j (c_(p+1) - c_p).
 //
 // Small mode (every dim <= 256): pass X writes 8-bit row sites plus a per-row flag,
-// pass Y 16-bit packed 2-D sites (x | y << 8), stack entries are 8-bit.  Large mode (dims
-// up to 1024): 16-bit row sites with an explicit "none", 32-bit packed sites
-// (x | y << 16), 16-bit stack entries and 64-bit products in the domination test.
+// pass Y 16-bit packed 2-D sites (x | y << 8), stack positions are 8-bit.  Large mode
+// (dims up to 1024): 16-bit row sites, 32-bit packed sites (x | y << 16), 64-bit products
+// in the domination test; pass Z keeps stack positions in the sites' free bits.
 #include <climits>
 #include <type_traits>
 
