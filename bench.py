@@ -15,6 +15,7 @@ collective on the data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -345,6 +346,7 @@ def run_vedt(args):
     time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize()
+    gc.disable()   # no collector pauses in the host loop that feeds the stream
     t_start.record(stream)
     for i in range(args.steps):
         evs[i][0].record(stream)
@@ -352,6 +354,7 @@ def run_vedt(args):
         evs[i][1].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
+    gc.enable()
     barrier(world)
     clk = clocks.stop()
     m.check()
