@@ -145,3 +145,27 @@ def test_edt_repeat_is_deterministic_and_independent_of_other_grid():
     (a, ai), = run_gpu_edt(occ, which=None)
     (b, bi), (_, _) = run_gpu_edt(occ, other)
     assert np.array_equal(a, b) and np.array_equal(ai, bi)
+
+
+def test_edt_random_sweep_of_shapes_densities_and_bands():
+    """Seeded sweep: ragged dims (not multiples of 32), densities from one site to dense,
+    every band count of the mode, small and large mode."""
+    rng = np.random.default_rng(2024)
+    for case in range(40):
+        large = case % 5 == 4
+        if large:
+            dims = (int(rng.integers(257, 400)), int(rng.integers(1, 40)), int(rng.integers(1, 40)))
+            dims = tuple(np.roll(dims, int(rng.integers(0, 3))))
+            bands = int(rng.choice([0, 4, 8]))
+        else:
+            dims = tuple(int(d) for d in rng.integers(1, 97, 3))
+            bands = int(rng.choice([0, 1, 2, 4, 8]))
+        dens = float(10 ** rng.uniform(-4, -0.3))
+        occ = synth.random_occupancy(5000 + case, dims, dens)
+        if occ.sum() == 0 and case % 2:
+            occ.flat[int(rng.integers(0, occ.size))] = 1
+        (sq, ix), = run_gpu_edt(occ, bands=bands)
+        if occ.any():
+            assert_parity(occ, sq, ix)
+        else:
+            assert (sq == INT32_MAX).all() and (ix == -1).all()
