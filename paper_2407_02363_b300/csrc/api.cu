@@ -162,6 +162,9 @@ void free_map(vedt_map *m) {
         if (m->consumed[b]) cudaEventDestroy(m->consumed[b]);
     }
     if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
+    if (m->side_stream) cudaStreamDestroy(m->side_stream);
+    if (m->links_done) cudaEventDestroy(m->links_done);
+    if (m->self_done) cudaEventDestroy(m->self_done);
     if (m->done) cudaEventDestroy(m->done);
     for (auto &p : m->pending) {
         cudaEventDestroy(p.a);
@@ -537,9 +540,26 @@ vedt_status vedt_frame(vedt_map *m, const float *xyz, int64_t n, const float *T,
     if (nq > 0 && (!centres || !radii || !out)) return VEDT_EINVAL;
     vedt_status st = vedt_clear(m, VEDT_MAP_BOTH);
     if (st == VEDT_OK && chain) st = vedt_insert_robot(m, chain, q, mask);
-    if (st == VEDT_OK) st = vedt_insert_pointcloud(m, xyz, n, T, 1, nullptr);
-    if (st == VEDT_OK) st = vedt_compute_edt(m, VEDT_MAP_BOTH);
-    if (st == VEDT_OK && nq > 0) st = vedt_query_spheres_dev(m, centres, radii, nq, VEDT_MAP_BOTH, out);
+    if (st != VEDT_OK) return st;
+    if (!m->side_stream) {
+        VCHECK(cudaStreamCreateWithFlags(&m->side_stream, cudaStreamNonBlocking));
+        VCHECK(cudaEventCreateWithFlags(&m->links_done, cudaEventDisableTiming));
+        VCHECK(cudaEventCreateWithFlags(&m->self_done, cudaEventDisableTiming));
+    }
+    // M_S is final once the links are in: its EDT overlaps the point insertion and M_I's EDT
+    VCHECK(cudaEventRecord(m->links_done, m->stream));
+    VCHECK(cudaStreamWaitEvent(m->side_stream, m->links_done, 0));
+    cudaStream_t main = m->stream;
+    m->stream = m->side_stream;
+    st = vedt_compute_edt(m, VEDT_MAP_SELF);
+    m->stream = main;
+    if (st != VEDT_OK) return st;
+    VCHECK(cudaEventRecord(m->self_done, m->side_stream));
+    st = vedt_insert_pointcloud(m, xyz, n, T, 1, nullptr);
+    if (st == VEDT_OK) st = vedt_compute_edt(m, VEDT_MAP_ENV);
+    if (st != VEDT_OK) return st;
+    VCHECK(cudaStreamWaitEvent(m->stream, m->self_done, 0));
+    if (nq > 0) st = vedt_query_spheres_dev(m, centres, radii, nq, VEDT_MAP_BOTH, out);
     return st;
 }
 

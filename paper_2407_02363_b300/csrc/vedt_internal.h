@@ -176,6 +176,10 @@ struct vedt_map {
     // so that the next frame's upload overlaps this frame's kernels
     float *stage[2] = {nullptr, nullptr};
     cudaStream_t copy_stream = nullptr;
+    // frames: the self map's EDT runs on a side stream, concurrently with the point
+    // insertion and the environment map's EDT
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t links_done = nullptr, self_done = nullptr;
     cudaEvent_t copied[2] = {nullptr, nullptr};    // upload into stage[b] finished
     cudaEvent_t consumed[2] = {nullptr, nullptr};  // frame reading stage[b] finished
     int parity = 0;                // staging buffer of the next host frame
