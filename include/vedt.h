@@ -200,9 +200,13 @@ vedt_status vedt_query_spheres_dev(vedt_map *map, const float *centres_dev, cons
 
 /* Alg. 2 lines 4-10 in one call on device buffers, asynchronous: vedt_clear(BOTH),
  * vedt_insert_robot(chain, q, link_mask) (skipped if chain == NULL), vedt_insert_pointcloud
- * (xyz_dev, n_points, T_world_sensor_host, filter_self = 1), vedt_compute_edt(BOTH) and
+ * (xyz_dev, n_points, T_world_sensor_host, filter_self = 1), the EDT of both maps and
  * vedt_query_spheres_dev(centres_dev, radii_dev, m, BOTH, out_dev) (skipped if m == 0).
- * Errors: as the individual calls. */
+ * M_S is final once the links are in, so its EDT runs on a side stream owned by the map,
+ * concurrently with the point insertion and M_I's EDT on the map's stream; the query
+ * waits for both, and the call's work is complete when the map's stream is (one frame
+ * never overlaps the next).  While per-kernel timing is on, the same launches run one
+ * after another on the map's stream.  Errors: as the individual calls. */
 vedt_status vedt_frame(vedt_map *map, const float *xyz_dev, int64_t n_points,
                        const float *T_world_sensor_host, const vedt_chain *chain, const double *q,
                        uint32_t link_mask, const float *centres_dev, const float *radii_dev, int m,

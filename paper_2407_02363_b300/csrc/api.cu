@@ -541,6 +541,15 @@ vedt_status vedt_frame(vedt_map *m, const float *xyz, int64_t n, const float *T,
     vedt_status st = vedt_clear(m, VEDT_MAP_BOTH);
     if (st == VEDT_OK && chain) st = vedt_insert_robot(m, chain, q, mask);
     if (st != VEDT_OK) return st;
+    if (m->timing) {
+        // per-kernel timing: the same launches, one after another on the map's stream, so
+        // that each launch's events time that kernel alone
+        st = vedt_compute_edt(m, VEDT_MAP_SELF);
+        if (st == VEDT_OK) st = vedt_insert_pointcloud(m, xyz, n, T, 1, nullptr);
+        if (st == VEDT_OK) st = vedt_compute_edt(m, VEDT_MAP_ENV);
+        if (st == VEDT_OK && nq > 0) st = vedt_query_spheres_dev(m, centres, radii, nq, VEDT_MAP_BOTH, out);
+        return st;
+    }
     if (!m->side_stream) {
         VCHECK(cudaStreamCreateWithFlags(&m->side_stream, cudaStreamNonBlocking));
         VCHECK(cudaEventCreateWithFlags(&m->links_done, cudaEventDisableTiming));
