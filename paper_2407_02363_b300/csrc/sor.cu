@@ -315,7 +315,7 @@ __device__ __forceinline__ double sq_dist(float4 a, float4 b) {
 // the squared distance to the searched cube's nearest open face, which keeps every
 // unexamined point out of the band.
 constexpr int kKnnThreads = 128;
-constexpr int kExtra = 8;
+constexpr int kExtra = 4;
 constexpr float kBand = 1.000004f;
 constexpr float kStop = 1.00001f;
 
