@@ -84,3 +84,17 @@ def test_fk_matches_oracle(v, oracle_mod):
         assert np.abs(P - R).max() < 1e-12
         # same operation order on both sides: identical fp32 poses
         assert np.array_equal(P.astype(np.float32), R.astype(np.float32))
+
+
+def test_binding_refuses_to_load_without_the_library(tmp_path):
+    """No CPU fallback: a copy of the package without libvedt.so fails at import."""
+    import shutil
+    pkg = tmp_path / "paper_2407_02363_b300"
+    pkg.mkdir()
+    src = os.path.join(ROOT, "paper_2407_02363_b300")
+    for f in ("__init__.py", "vedt.py"):
+        shutil.copy(os.path.join(src, f), pkg / f)
+    code = "import paper_2407_02363_b300.vedt"
+    r = subprocess.run([os.sys.executable, "-c", code], cwd=tmp_path, capture_output=True, text=True)
+    assert r.returncode != 0
+    assert "libvedt.so not built" in r.stderr
