@@ -550,10 +550,21 @@ vedt_status vedt_frame(vedt_map *m, const float *xyz, int64_t n, const float *T,
         if (st == VEDT_OK && nq > 0) st = vedt_query_spheres_dev(m, centres, radii, nq, VEDT_MAP_BOTH, out);
         return st;
     }
-    if (!m->side_stream) {
-        VCHECK(cudaStreamCreateWithFlags(&m->side_stream, cudaStreamNonBlocking));
-        VCHECK(cudaEventCreateWithFlags(&m->links_done, cudaEventDisableTiming));
-        VCHECK(cudaEventCreateWithFlags(&m->self_done, cudaEventDisableTiming));
+    if (!m->side_stream) {   // created together, or not at all
+        cudaStream_t side = nullptr;
+        cudaEvent_t a = nullptr, b = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (b) cudaEventDestroy(b);
+            if (a) cudaEventDestroy(a);
+            if (side) cudaStreamDestroy(side);
+            return from_cuda(e);
+        }
+        m->side_stream = side;
+        m->links_done = a;
+        m->self_done = b;
     }
     // M_S is final once the links are in: its EDT overlaps the point insertion and M_I's EDT
     VCHECK(cudaEventRecord(m->links_done, m->stream));
