@@ -592,11 +592,21 @@ namespace {
 vedt_status queue_host_frame(vedt_map *m, const float *xyz, int64_t n, const float *T, const vedt_chain *chain,
                              const double *q, uint32_t mask, const float *centres, const float *radii, int nq,
                              vedt_sphere_result *out) {
-    if (!m->copy_stream) {
-        VCHECK(cudaStreamCreateWithFlags(&m->copy_stream, cudaStreamNonBlocking));
+    if (!m->copy_stream) {   // created together, or not at all
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (int j = 0; j < 4 && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            if (cs) cudaStreamDestroy(cs);
+            return from_cuda(e);
+        }
+        m->copy_stream = cs;
         for (int b = 0; b < 2; ++b) {
-            VCHECK(cudaEventCreateWithFlags(&m->copied[b], cudaEventDisableTiming));
-            VCHECK(cudaEventCreateWithFlags(&m->consumed[b], cudaEventDisableTiming));
+            m->copied[b] = ev[2 * b];
+            m->consumed[b] = ev[2 * b + 1];
         }
     }
     if (n > m->stage_cap) {   // grow both buffers once nothing reads or writes them
