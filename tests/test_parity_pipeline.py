@@ -122,6 +122,57 @@ def test_config2_frame_full_size():
     check_frame(grid, r)
 
 
+@pytest.mark.parametrize("timing", [False, True])
+def test_frame_api_full_size_on_two_streams(timing):
+    """vedt_frame, the call the bench times: the self map's EDT on the side stream, the
+    cloud and the environment EDT on the map's stream, then the query; several frames
+    back to back.  Each frame's fields and sphere results against the oracle (with
+    per-kernel timing on, the same launches run serially)."""
+    v = lib()
+    grid = synth.GridSpec((256, 256, 256), 0.01)
+    scene = synth.CameraScene(1234 + 2000, grid)
+    chain = synth.make_chain(1234 + 2000, (1.28, 1.28, 1.28))
+    links = synth.link_models(chain, grid.voxel_size)
+    spheres = synth.sphere_model(chain)
+    traj = synth.joint_trajectory(1234 + 2000, 40)
+    m = v.Map(grid.dims, grid.voxel_size, grid.origin, stream=torch.cuda.Stream())
+    m.register_links(links)
+    m.set_timing(timing)
+    cchain = v.make_chain(chain)
+    nm = len(spheres.radius)
+    out = torch.empty(2 * nm * 32, dtype=torch.uint8, device="cuda")
+    radii = torch.from_numpy(spheres.radius).cuda()
+    for f in (30, 31, 32):
+        cloud = scene.frame(f)
+        cl = torch.from_numpy(cloud).cuda()
+        centres_np = oracle.sphere_centres(chain, spheres, traj[f])
+        centres = torch.from_numpy(centres_np).cuda()
+        torch.cuda.synchronize()
+        m.frame(cl, cl.shape[0], cchain, traj[f], SELF_MASK, centres, radii, nm, out)
+        m.check()
+        res = out.cpu().numpy().view(v.SPHERE_DTYPE)
+        poses = v.fk(chain, traj[f]).astype(np.float32)
+        X, Y, Z = grid.dims
+        o_self = np.zeros((Z, Y, X), np.uint8)
+        oracle.insert_links(o_self, grid.dims, grid.voxel_size, grid.origin, links, poses, SELF_MASK)
+        o_env = np.zeros((Z, Y, X), np.uint8)
+        oracle.insert_points(o_env, o_self, grid.dims, grid.voxel_size, grid.origin, cloud, filter_self=True)
+        for g, occ in ((v.MAP_ENV, o_env), (v.MAP_SELF, o_self)):
+            sq, ix = (t.cpu().numpy() for t in m.field(g))
+            osq, _ = oracle.edt(occ)
+            assert np.array_equal(sq, osq)
+            check_idx_valid(occ, sq, ix)
+            k = 0 if g == v.MAP_ENV else 1
+            expect = oracle.query_spheres(osq, ix, grid.dims, grid.voxel_size, grid.origin, centres_np,
+                                          spheres.radius)
+            got = res[k * nm:(k + 1) * nm].copy()
+            exp = np.zeros(nm, dtype=got.dtype)
+            for name in exp.dtype.names:
+                exp[name] = expect[name]
+            assert spheres_bitequal(got, exp)
+    m.close()
+
+
 def test_async_host_frames_back_to_back_match_sync_frames():
     """Frames queued back to back with vedt_frame_host_async alternate the two staging
     buffers, each upload running on the copy stream while the previous frame computes;
