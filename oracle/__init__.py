@@ -14,6 +14,7 @@ Contents (each function cites the passage it follows):
   mlp_*           learned surrogate reference (not in the paper)       (numpy, fp64)
   sor.sor_filter  statistical outlier filter of the raw cloud, Sec. III-A
                   (oracle/sor.py: numpy brute-force kNN, fp64, exact sums)
+  logodds.update  Bayesian (log-odds) occupancy update, Sec. III-A (oracle/logodds.py)
 """
 from __future__ import annotations
 
