@@ -42,7 +42,7 @@ WORKLOAD = ("frame256: 256^3 grid at 1 cm; 300k-point synthetic depth-camera clo
             "maps; 24-sphere query on both maps; consecutive frames")
 
 # ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one capture
-# of the frame256 workload, profiles/edt_passes_frame256.md; the mean of the two maps'
+# of the frame256 workload, kept under profiles/; the mean of the two maps'
 # launches, one map per launch) with a hash of the kernel
 # sources it was taken from (comments and blank space excluded) and the algorithmic bytes
 # of the captured launch; reported only while both still match.
@@ -101,6 +101,8 @@ def parse():
                    help="calls per setting of the outlier-filter leg (0: skip)")
     p.add_argument("--static-frames", type=int, default=200,
                    help="frames of the static-scene leg, incremental EDT off and on (0: skip)")
+    p.add_argument("--logodds-frames", type=int, default=200,
+                   help="frames of the log-odds occupancy leg, update off and on (0: skip)")
     return p.parse_args()
 
 
@@ -212,7 +214,7 @@ def _isnum(s):
 
 
 # ------------------------------------------------------------------------------------
-# algorithmic bytes per launch (design traffic of each kernel)
+# algorithmic bytes per launch (the design traffic of each kernel)
 # ------------------------------------------------------------------------------------
 def frame_bytes(kind, n_vox_per_grid, n_points, n_link_pts):
     """Algorithmic bytes one frame of both grids needs from each kernel kind (grids with
@@ -226,6 +228,7 @@ def frame_bytes(kind, n_vox_per_grid, n_points, n_link_pts):
         "edt_y": N * (1 + 2),                    # uint8 row site in, uint16 2-D site out
         "edt_z": N * (2 + 4 + 4),                # uint16 2-D site in, int32 sqdist + int32 idx out
         "query": 24 * 2 * (12 + 8 + 32),
+        "occupancy": n_vox_per_grid * 4,         # M_I occupancy and log-odds, each read and written
     }[kind]
 
 
@@ -445,6 +448,9 @@ def run_vedt(args):
     static = None
     if args.static_frames > 0 and rank == 0:
         static = run_static_scene(args, v, W, clouds[0], centres, radii, m_sph, cchain, dev)
+    lo_leg = None
+    if args.logodds_frames > 0 and rank == 0:
+        lo_leg = run_logodds(args, v, W, clouds, centres, radii, m_sph, cchain, dev)
 
     batched = run_batched(args, v, dev) if args.batch_steps > 0 else None
     sur = run_surrogate(args, v, dev) if (args.sur_train > 0 and rank == 0) else None
@@ -468,7 +474,7 @@ def run_vedt(args):
                            "max": frame_ms[-1], "what": "device time per frame (events around each frame)"},
             "roofline": roof, "edt": edt, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
             "batched": batched, "surrogate": sur, "serving": srv, "paper_sizes": paper,
-            "static_scene": static, "outlier_filter": sor_leg, "closed_loop": loop,
+            "static_scene": static, "outlier_filter": sor_leg, "closed_loop": loop, "logodds": lo_leg,
             "gpu_launches": int(round(sum(k["launches"] for k in kernels.values()) / kernel_frames * args.steps)),
             "kernels_from": f"{kernel_frames} frames right after the timed region, CUDA events around each launch "
                             "on the library's stream",
@@ -568,6 +574,58 @@ def run_static_scene(args, v, W, cloud, centres, radii, m_sph, cchain, dev):
                     "(vedt_map_set_incremental), device time per frame", "frames": args.static_frames,
             "off": res["off"], "on": res["on"], "speedup": res["off"]["ms_per_frame"] / res["on"]["ms_per_frame"],
             "fields_bit_equal": bool(equal)}
+
+
+def run_logodds(args, v, W, clouds, centres, radii, m_sph, cchain, dev):
+    """The frame256 workload (moving cloud, moving arm) through vedt_frame with the
+    log-odds occupancy update of the environment grid off and on: device time per frame,
+    and the update kernel's own time (per-launch events, serial frames) against its
+    4 B per voxel (occupancy and log-odds, each read and written once)."""
+    import torch
+    grid = W["grid"]
+    n_traj = len(W["traj"])
+    out = torch.empty(2 * m_sph * 32, dtype=torch.uint8, device=dev)
+    N = grid.dims[0] * grid.dims[1] * grid.dims[2]
+    res = {}
+    for mode in ("off", "on"):
+        stream = torch.cuda.Stream(device=dev)
+        m = v.Map(grid.dims, grid.voxel_size, grid.origin, stream=stream)
+        m.register_links(W["links"])
+        if mode == "on":
+            m.set_logodds(True, l_hit=9, l_miss=4, l_min=-20, l_max=40, threshold=15)
+
+        def step(i):
+            k = i % n_traj
+            c = clouds[i % len(clouds)]
+            m.frame(c, c.shape[0], cchain, W["traj"][k], SELF_MASK, centres[k], radii, m_sph, out)
+
+        for i in range(5):
+            step(i)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(args.logodds_frames):
+            step(5 + i)
+        b.record(stream)
+        torch.cuda.synchronize()
+        m.check()
+        res[mode] = {"ms_per_frame": a.elapsed_time(b) / args.logodds_frames}
+        if mode == "on":
+            m.set_timing(True)
+            for i in range(50):
+                step(i)
+            t = m.kernel_times()["occupancy"]
+            m.set_timing(False)
+            us = t[0] / t[1] * 1e3
+            res[mode]["update_us"] = us
+            res[mode]["update_gbs"] = 4 * N / (us * 1e-6) / 1e9
+            res[mode]["update_launches"] = t[1]
+        m.close()
+    return {"what": "frame256 through vedt_frame, log-odds occupancy of the environment grid off / on "
+                    "(l_hit 9, l_miss 4, clamp [-20, 40], threshold 15), device time per frame; the update "
+                    "kernel timed alone over 50 serial frames (4 B per voxel; its 33.6 MB fit in the 126 MB L2 "
+                    "between the insertion and the EDT)", "frames": args.logodds_frames,
+            "off": res["off"], "on": res["on"], "overhead_ms": res["on"]["ms_per_frame"] - res["off"]["ms_per_frame"]}
 
 
 # The paper's map sizes (X x Y x Z, 2 cm voxels) with its GTX 1080 Ti PBA EDT times, for

@@ -107,6 +107,23 @@ vedt_status vedt_map_set_stream(vedt_map *map, void *stream);
  * vedt_compute_edt on.  Errors: EINVAL (NULL map, other values). */
 vedt_status vedt_map_set_bands(vedt_map *map, int bands);
 
+/* Bayesian occupancy of M_I (Sec. III-A names a Bayesian per-voxel update and gives
+ * no model), in integer log-odds.  With on = 1 the map keeps an int8 log-odds value per
+ * voxel of M_I, 0 (unknown) at the start.  Each
+ * vedt_update_occupancy turns the current M_I (the voxels this frame's points landed in:
+ * hits; all others: misses, no ray casting) into L <- clamp(L + l_hit | L - l_miss,
+ * l_min, l_max) and sets M_I to L >= threshold.  vedt_frame / _host run it after the
+ * point insertion.  0 <= l_hit, l_miss <= 255; -128 <= l_min <= 0 <= l_max <= 127;
+ * l_min < threshold (a threshold above l_max leaves M_I empty).
+ * on = 0 frees the log-odds; enabling again restarts from 0.  Synchronises the map's
+ * streams.  Errors: EINVAL, ENOMEM, ECUDA. */
+vedt_status vedt_map_set_logodds(vedt_map *map, int on, int l_hit, int l_miss, int l_min, int l_max,
+                                 int threshold);
+
+/* The log-odds update of M_I from its current occupancy (see vedt_map_set_logodds),
+ * asynchronous on the map's stream.  Errors: EINVAL (NULL map, log-odds off). */
+vedt_status vedt_update_occupancy(vedt_map *map);
+
 /* Incremental EDT (on = 1): vedt_compute_edt first compares each selected grid's
  * occupancy with a device snapshot taken at that grid's last EDT (one extra read of the
  * grid and of the snapshot, a write of the snapshot where they differ) and skips all
@@ -318,7 +335,7 @@ vedt_status vedt_check(vedt_map *map);
  * the accumulated milliseconds and launch counts of each kernel kind into ms_out /
  * count_out (arrays of VEDT_NUM_KERNELS, nullable), then resets the accumulators. */
 enum { VEDT_K_CLEAR = 0, VEDT_K_INSERT_LINKS, VEDT_K_INSERT_POINTS, VEDT_K_EDT_X,
-       VEDT_K_EDT_Y, VEDT_K_EDT_Z, VEDT_K_QUERY, VEDT_NUM_KERNELS };
+       VEDT_K_EDT_Y, VEDT_K_EDT_Z, VEDT_K_QUERY, VEDT_K_OCCUPANCY, VEDT_NUM_KERNELS };
 vedt_status vedt_set_timing(vedt_map *map, int enable);
 vedt_status vedt_kernel_times(vedt_map *map, double *ms_out, int64_t *count_out);
 

@@ -141,6 +141,7 @@ void free_map(vedt_map *m) {
             cudaFree(m->occ[0]);   // both grids share one allocation
             cudaFree(m->snap);
             cudaFree(m->changed);
+            cudaFree(m->logodds);
         }
         cudaFree(m->sq[i]);
         cudaFree(m->ix[i]);
@@ -291,6 +292,38 @@ vedt_status vedt_map_destroy(vedt_map *m) {
 vedt_status vedt_map_set_stream(vedt_map *m, void *stream) {
     if (!m) return VEDT_EINVAL;
     m->stream = static_cast<cudaStream_t>(stream);
+    return VEDT_OK;
+}
+
+vedt_status vedt_map_set_logodds(vedt_map *m, int on, int l_hit, int l_miss, int l_min, int l_max,
+                                 int threshold) {
+    if (!m) return VEDT_EINVAL;
+    if (on && (l_hit < 0 || l_hit > 255 || l_miss < 0 || l_miss > 255 || l_min < -128 || l_min > 0 ||
+               l_max < 0 || l_max > 127 || threshold <= l_min))
+        return VEDT_EINVAL;
+    VCHECK(cudaStreamSynchronize(m->stream));
+    if (m->side_stream) VCHECK(cudaStreamSynchronize(m->side_stream));
+    cudaFree(m->logodds);
+    m->logodds = nullptr;
+    if (!on) return VEDT_OK;
+    const int64_t n_al = m->occ[1] - m->occ[0];
+    cudaError_t e = cudaMalloc(&m->logodds, n_al);
+    if (e == cudaSuccess) e = cudaMemset(m->logodds, 0, n_al);   // 0: unknown
+    if (e != cudaSuccess) {
+        cudaFree(m->logodds);
+        m->logodds = nullptr;
+        return from_cuda(e);
+    }
+    const int p[5] = {l_hit, l_miss, l_min, l_max, threshold};
+    for (int k = 0; k < 5; ++k) m->lo_param[k] = p[k];
+    return VEDT_OK;
+}
+
+vedt_status vedt_update_occupancy(vedt_map *m) {
+    if (!m || !m->logodds) return VEDT_EINVAL;
+    const int slot = timing_begin(m, VEDT_K_OCCUPANCY);
+    VCHECK(launch_logodds(m->occ[0], m->logodds, m->N, m->lo_param, m->stream));
+    timing_end(m, slot);
     return VEDT_OK;
 }
 
@@ -546,6 +579,7 @@ vedt_status vedt_frame(vedt_map *m, const float *xyz, int64_t n, const float *T,
         // that each launch's events time that kernel alone
         st = vedt_compute_edt(m, VEDT_MAP_SELF);
         if (st == VEDT_OK) st = vedt_insert_pointcloud(m, xyz, n, T, 1, nullptr);
+        if (st == VEDT_OK && m->logodds) st = vedt_update_occupancy(m);
         if (st == VEDT_OK) st = vedt_compute_edt(m, VEDT_MAP_ENV);
         if (st == VEDT_OK && nq > 0) st = vedt_query_spheres_dev(m, centres, radii, nq, VEDT_MAP_BOTH, out);
         return st;
@@ -576,6 +610,7 @@ vedt_status vedt_frame(vedt_map *m, const float *xyz, int64_t n, const float *T,
     if (st != VEDT_OK) return st;
     VCHECK(cudaEventRecord(m->self_done, m->side_stream));
     st = vedt_insert_pointcloud(m, xyz, n, T, 1, nullptr);
+    if (st == VEDT_OK && m->logodds) st = vedt_update_occupancy(m);
     if (st == VEDT_OK) st = vedt_compute_edt(m, VEDT_MAP_ENV);
     if (st != VEDT_OK) return st;
     VCHECK(cudaStreamWaitEvent(m->stream, m->self_done, 0));

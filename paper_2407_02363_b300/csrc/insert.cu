@@ -56,6 +56,40 @@ __global__ void __launch_bounds__(256) k_occ_diff(const uint8_t *__restrict__ oc
     if (__syncthreads_or(diff) && threadIdx.x == 0) changed[g] = 1u;
 }
 
+// Bayesian occupancy update of M_I (Sec. III-A, log-odds form): per voxel, a hit (some
+// point of the frame landed in it) adds l_hit, a miss subtracts l_miss, the sum is
+// clamped to [l_min, l_max], and the voxel is occupied for the EDT iff it reaches the
+// threshold.  16 voxels per thread and iteration; the alignment tail past the n voxels
+// keeps its zeros.
+struct LogOdds { int hit, miss, lo, hi, thr; };
+
+__global__ void __launch_bounds__(256) k_logodds(uint8_t *__restrict__ occ, int8_t *__restrict__ L, int64_t n,
+                                                 LogOdds p) {
+    const int64_t nvec = (n + 15) / 16;
+    pdl_trigger();
+    pdl_wait();
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    uint4 *o4 = reinterpret_cast<uint4 *>(occ);
+    uint4 *l4 = reinterpret_cast<uint4 *>(L);
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nvec; i += stride) {
+        uint4 ov = o4[i], lv = l4[i];
+        uint8_t *ob = reinterpret_cast<uint8_t *>(&ov);
+        int8_t *lb = reinterpret_cast<int8_t *>(&lv);
+        const int64_t left = n - i * 16;
+        const int valid = left < 16 ? static_cast<int>(left) : 16;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            if (b < valid) {
+                const int v = min(max(static_cast<int>(lb[b]) + (ob[b] ? p.hit : -p.miss), p.lo), p.hi);
+                lb[b] = static_cast<int8_t>(v);
+                ob[b] = v >= p.thr ? 1 : 0;
+            }
+        }
+        o4[i] = ov;
+        l4[i] = lv;
+    }
+}
+
 struct Pose12 { float T[12]; };
 
 // Insert(Point_Cloud) with robot-point removal (Alg. 2 line 7; Sec. III-A).
@@ -182,6 +216,14 @@ cudaError_t launch_clear(uint8_t *p, int64_t n, cudaStream_t s) {
     const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
     const int blocks = static_cast<int>(want < 1 ? 1 : (want < cap ? want : cap));
     return launch_pdl(k_clear, dim3(blocks), dim3(256), 0, s, p, n);
+}
+
+cudaError_t launch_logodds(uint8_t *occ, int8_t *L, int64_t n, const int (&p)[5], cudaStream_t s) {
+    const int64_t nvec = (n + 15) / 16;
+    const int64_t want = (nvec + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+    const int blocks = static_cast<int>(want < 1 ? 1 : (want < cap ? want : cap));
+    return launch_pdl(k_logodds, dim3(blocks), dim3(256), 0, s, occ, L, n, LogOdds{p[0], p[1], p[2], p[3], p[4]});
 }
 
 cudaError_t launch_occ_diff(const uint8_t *occ, uint8_t *snap, uint32_t *changed, int64_t n_al, int grids,

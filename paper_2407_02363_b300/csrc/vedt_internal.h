@@ -109,6 +109,7 @@ cudaError_t launch_wait_selftest(const unsigned *counter, uint32_t limit, int32_
 // launchers (insert.cu)
 struct LinkPose { float T[VEDT_MAX_LINKS][12]; };
 cudaError_t launch_clear(uint8_t *p, int64_t n, cudaStream_t s);
+cudaError_t launch_logodds(uint8_t *occ, int8_t *L, int64_t n, const int (&p)[5], cudaStream_t s);
 cudaError_t launch_occ_diff(const uint8_t *occ, uint8_t *snap, uint32_t *changed, int64_t n_al, int grids,
                             cudaStream_t s);
 cudaError_t launch_insert_points(uint8_t *env, const uint8_t *self, int X, int Y, int Z, float vs,
@@ -160,6 +161,10 @@ struct vedt_map {
     // in one allocation, same layout as occ)
     uint32_t *changed = nullptr;
     uint8_t *snap = nullptr;
+    // Bayesian occupancy of M_I: int8 log-odds per voxel (layout of the occupancy) and
+    // the update's parameters {l_hit, l_miss, l_min, l_max, threshold}
+    int8_t *logodds = nullptr;
+    int lo_param[5] = {0, 0, 0, 0, 0};
     int incremental = 0;
     bool snap_valid[2] = {false, false};   // fields match the snapshot (host view)
     // EDT launch tables for which = ENV (0), SELF (1), BOTH (2)

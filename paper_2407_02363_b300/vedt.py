@@ -24,7 +24,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 MAP_ENV, MAP_SELF, MAP_BOTH = 1, 2, 3
 SPHERE_OK, SPHERE_OUTSIDE, SPHERE_EMPTY = 0, 1, 2
 MAX_DIM, MAX_LINKS, MAX_JOINTS = 1024, 16, 15
-KERNELS = ("clear", "insert_links", "insert_points", "edt_x", "edt_y", "edt_z", "query")
+KERNELS = ("clear", "insert_links", "insert_points", "edt_x", "edt_y", "edt_z", "query", "occupancy")
 
 SPHERE_DTYPE = np.dtype([("sqdist", "<i4"), ("idx", "<i4"), ("dist", "<f4"),
                          ("clearance", "<f4"), ("nearest", "<f4", (3,)), ("status", "<i4")])
@@ -49,6 +49,8 @@ _sig = {
     "vedt_map_set_stream": [_P, _P],
     "vedt_map_set_bands": [_P, _I32],
     "vedt_map_set_incremental": [_P, _I32],
+    "vedt_map_set_logodds": [_P, _I32, _I32, _I32, _I32, _I32, _I32],
+    "vedt_update_occupancy": [_P],
     "vedt_map_edt_recomputed": [_P, _I32, _P],
     "vedt_map_info": [_P, _P, _P, _P],
     "vedt_clear": [_P, _I32],
@@ -233,6 +235,14 @@ class Map:
         """Bands per line of EDT passes Y and Z (0: default; 1/2/4/8 for dims <= 256, 4/8
         above)."""
         _chk(_lib.vedt_map_set_bands(self._h, int(bands)), "vedt_map_set_bands")
+
+    def set_logodds(self, on=True, l_hit=9, l_miss=4, l_min=-20, l_max=40, threshold=15):
+        """Bayesian (log-odds) occupancy of the environment grid; see vedt_map_set_logodds."""
+        _chk(_lib.vedt_map_set_logodds(self._h, 1 if on else 0, int(l_hit), int(l_miss), int(l_min), int(l_max),
+                                       int(threshold)), "vedt_map_set_logodds")
+
+    def update_occupancy(self):
+        _chk(_lib.vedt_update_occupancy(self._h), "vedt_update_occupancy")
 
     def set_incremental(self, on=True):
         """Skip the EDT of a grid whose occupancy is unchanged since its last EDT."""
