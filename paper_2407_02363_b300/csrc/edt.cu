@@ -517,10 +517,12 @@ struct PolY {
     static constexpr int kMax = L ? 1024 : 256;
     static constexpr bool kPacked = false;   // stack positions in a separate array
     int x;
-    __device__ __forceinline__ int h(uint32_t r, int p) const {
+    // squared distance within the line's plane, and with the position p along the line
+    __device__ __forceinline__ int f(uint32_t r) const {
         const int d = x - static_cast<int>(r);
-        return d * d + p * p;
+        return d * d;
     }
+    __device__ __forceinline__ int h(uint32_t r, int p) const { return f(r) + p * p; }
     static __device__ __forceinline__ uint32_t pack(uint32_t r, int) { return r; }
     static __device__ __forceinline__ int pos_of(uint32_t) { return 0; }
 };
@@ -538,10 +540,11 @@ struct PolZ {
     // array; small mode's 16-bit site has no free bits.
     static constexpr bool kPacked = L;
     int x, y;
-    __device__ __forceinline__ int h(uint32_t r, int p) const {
+    __device__ __forceinline__ int f(uint32_t r) const {
         const int dx = x - static_cast<int>(r & kMask), dy = y - static_cast<int>((r >> kShift) & kMask);
-        return dx * dx + dy * dy + p * p;
+        return dx * dx + dy * dy;
     }
+    __device__ __forceinline__ int h(uint32_t r, int p) const { return f(r) + p * p; }
     static __device__ __forceinline__ uint32_t pack(uint32_t r, int c) {
         return r | (static_cast<uint32_t>(c & 63) << 10) | (static_cast<uint32_t>(c >> 6) << 26);
     }
@@ -567,13 +570,12 @@ __device__ __forceinline__ bool dominated(int ca, int ha, int cb, int hb, int cc
 
 // Stack of proximate sites of one band (Steps 2 and 4) over its valid positions
 // lo + 32 w + (bit of vm[w]), ascending.  `col` = this column's input (stride kCols), the
-// stack's input words are written back in place from slot lo; `mypos` = this thread's
-// position stack (stride NB * 32).
+// stack's input words are written back in place from slot lo; `cpos` = this column's
+// positions (stride kTile), entry k's position kept in slot lo + k like its word.
 template <int NB, class P>
-__device__ __forceinline__ int small_build(const P &pol, typename P::In *col, typename P::Pos *mypos, int lo,
+__device__ __forceinline__ int small_build(const P &pol, typename P::In *col, typename P::Pos *cpos, int lo,
                                            const uint32_t (&vm)[Bands<NB, P::kMax>::kWords]) {
     using Prod = typename P::Prod;
-    constexpr int kS = NB * kTile;
     int k = 0, a = 0, b = 0, ha = 0, hb = 0, dab = 0, wab = 0;
     auto step = [&](int c) {
         const uint32_t r = col[c * kCols];
@@ -585,7 +587,7 @@ __device__ __forceinline__ int small_build(const P &pol, typename P::In *col, ty
             if (k >= 2) {
                 const uint32_t ra = col[(lo + k - 2) * kCols];
                 if constexpr (P::kPacked) a = P::pos_of(ra);
-                else a = mypos[(k - 2) * kS];
+                else a = cpos[(lo + k - 2) * kTile];
                 ha = pol.h(ra, a);
                 dab = hb - ha;
                 wab = b - a;
@@ -595,7 +597,7 @@ __device__ __forceinline__ int small_build(const P &pol, typename P::In *col, ty
             col[(lo + k) * kCols] = static_cast<typename P::In>(P::pack(r, c));
         } else {
             col[(lo + k) * kCols] = static_cast<typename P::In>(r);
-            mypos[k * kS] = static_cast<typename P::Pos>(c);
+            cpos[(lo + k) * kTile] = static_cast<typename P::Pos>(c);
         }
         dab = hc - hb;
         wab = c - b;
@@ -638,15 +640,17 @@ __device__ __forceinline__ int pick(const int (&a)[NB], int b) {
 template <int NB, class P>
 struct SmallMerged {
     typename P::In *in;         // this column's slots (stride kCols)
-    const typename P::Pos *pos; // this column's band-0 positions (stride NB * 32)
+    const typename P::Pos *pos; // this column's positions, slot by slot (stride kTile)
     int bl;                     // band length
     int j[NB], i[NB];
     int last;                   // last non-empty band
-    __device__ __forceinline__ void at(int b, int t, int &c, uint32_t &r) const {
-        r = in[(b * bl + t) * kCols];
+    // entry of slot s = b * bl + t (band b's stack entry t)
+    __device__ __forceinline__ void at_slot(int s, int &c, uint32_t &r) const {
+        r = in[s * kCols];
         if constexpr (P::kPacked) c = P::pos_of(r);
-        else c = pos[t * (NB * kTile) + b * kTile];
+        else c = pos[s * kTile];
     }
+    __device__ __forceinline__ void at(int b, int t, int &c, uint32_t &r) const { at_slot(b * bl + t, c, r); }
     // largest non-empty band below b, or -1
     __device__ __forceinline__ int prev_band(int b) const {
         int s = -1;
@@ -740,24 +744,52 @@ struct SmallMerged {
     }
 };
 
-// Cursor over the merged envelope: entry (b, t) with its band's last kept index.
+// Position of the walk's first entry: band b, stack entry t.
 template <int NB, class P>
 struct Cursor {
-    int b, t, tend;
-    __device__ __forceinline__ void set(const SmallMerged<NB, P> &M, int bb, int tt) {
+    int b, t;
+    __device__ __forceinline__ void set(const SmallMerged<NB, P> &, int bb, int tt) {
         b = bb;
         t = tt;
-        tend = pick<NB>(M.i, bb);
+    }
+};
+
+// Forward cursor of the walk over slots: the current band's kept range, then the later
+// non-empty bands' ranges queued in order (first slot | last slot << 16), so a step
+// needs no band search.
+template <int NB, class P>
+struct Walk {
+    static constexpr int kQ = NB > 1 ? NB - 1 : 1;
+    int s, se;
+    uint32_t q[kQ];
+    __device__ __forceinline__ void init(const SmallMerged<NB, P> &M, int b, int t) {
+        s = b * M.bl + t;
+        se = b * M.bl + pick<NB>(M.i, b);
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) q[k] = ~0u;
+        int n = 0;
+#pragma unroll
+        for (int u = 1; u < NB; ++u) {
+            const bool take = u > b && M.j[u] <= M.i[u];
+            const uint32_t v = static_cast<uint32_t>(u * M.bl + M.j[u]) | (static_cast<uint32_t>(u * M.bl + M.i[u]) << 16);
+#pragma unroll
+            for (int k = 0; k < kQ; ++k)
+                if (take && k == n) q[k] = v;
+            n += take ? 1 : 0;
+        }
     }
     // next entry; false at the end of the envelope
-    __device__ __forceinline__ bool next(const SmallMerged<NB, P> &M) {
-        if (t < tend) {
-            ++t;
+    __device__ __forceinline__ bool next() {
+        if (s < se) {
+            ++s;
             return true;
         }
-        const int nb = M.next_band(b);
-        if (nb < 0) return false;
-        set(M, nb, pick<NB>(M.j, nb));
+        if (q[0] == ~0u) return false;
+        s = static_cast<int>(q[0] & 0xFFFFu);
+        se = static_cast<int>(q[0] >> 16);
+#pragma unroll
+        for (int k = 0; k + 1 < kQ; ++k) q[k] = q[k + 1];
+        q[kQ - 1] = ~0u;
         return true;
     }
 };
@@ -798,7 +830,8 @@ __device__ __forceinline__ void small_query(const P &pol, const SmallMerged<NB, 
         r0 = r;
         h0 = hb;
     }
-    Cursor<NB, P> nxt = cur;
+    Walk<NB, P> nxt;
+    nxt.init(M, cur.b, cur.t);
     if constexpr (E::kValues) {
         // Values at the current voxel j of the current entry (v0 = h0 - 2 j c0 + j^2, step
         // i0) and of the next one (v1, i1; 2^30 when there is none, above any value reached
@@ -808,10 +841,11 @@ __device__ __forceinline__ void small_query(const P &pol, const SmallMerged<NB, 
         uint32_t r1 = 0;
         int v0 = h0 - 2 * lo * c0 + lo * lo, i0 = 2 * (lo - c0) + 1;
         auto fetch = [&](int j) {
-            if (nxt.next(M)) {
-                M.at(nxt.b, nxt.t, c1, r1);
-                v1 = pol.h(r1, c1) + j * (j - 2 * c1);
-                i1 = 2 * (j - c1) + 1;
+            if (nxt.next()) {
+                M.at_slot(nxt.s, c1, r1);
+                const int d = j - c1;
+                v1 = pol.f(r1) + d * d;
+                i1 = 2 * d + 1;
             } else {
                 v1 = kNone;
                 i1 = 0;
@@ -842,8 +876,8 @@ __device__ __forceinline__ void small_query(const P &pol, const SmallMerged<NB, 
         int c1 = 0, h1 = 0, dc2 = 0, dh = INT_MAX;
         uint32_t r1 = 0;
         auto fetch = [&]() {
-            if (nxt.next(M)) {
-                M.at(nxt.b, nxt.t, c1, r1);
+            if (nxt.next()) {
+                M.at_slot(nxt.s, c1, r1);
                 h1 = pol.h(r1, c1);
                 dc2 = 2 * (c1 - c0);
                 dh = h1 - h0;
@@ -936,10 +970,20 @@ __host__ __device__ constexpr int tile_pos_bytes(int n) {
     if (P::kPacked) return 0;
     return Bands<NB, P::kMax>::len(n) * NB * kTile * static_cast<int>(sizeof(typename P::Pos));
 }
+// Stack sizes and kept ranges per (band, column): 8 bits while a band holds at most 255
+// positions.
+template <int NB, class P>
+using RangeIdx = typename std::conditional<(P::kMax / NB <= 255), uint8_t, uint16_t>::type;
+template <int NB, class P>
+__host__ __device__ constexpr int small_region_off(int n) {
+    return ((tile_in_bytes<NB, P>(n) + 15) & ~15) + ((tile_pos_bytes<NB, P>(n) + 15) & ~15);
+}
+// The range area (2 x NB x 32 indices, at least 64 bytes) also holds the standalone
+// kernels' TMA barrier in its first 8 bytes until the tile is staged.  A 256-long pass-Z
+// line tile then takes 24,832 bytes: nine CTAs per SM.
 template <int NB, class P>
 __host__ __device__ constexpr int small_smem(int n) {
-    return ((tile_in_bytes<NB, P>(n) + 15) & ~15) + ((tile_pos_bytes<NB, P>(n) + 15) & ~15) + NB * kTile * 4 +
-           2 * NB * kTile * 2;
+    return small_region_off<NB, P>(n) + 2 * NB * kTile * static_cast<int>(sizeof(RangeIdx<NB, P>));
 }
 
 constexpr int kNBY = 4;   // default bands per line in the standalone passes, dims <= 256
@@ -948,12 +992,15 @@ constexpr int kNBLs = 4;  // bands per line once some dim exceeds 256, lines up 
 
 // One envelope tile over the staged line tile `in` (n positions x 32 columns), after
 // its TMA loads were issued: builds the bands, merges, walks.  `flags` = validity of each
-// position; `emit` starts at the thread's first voxel.  Returns the total stack size of
-// the column (0 iff no valid position), identical for every column.
-template <int NB, class P, class E>
-__device__ __forceinline__ int small_envelope(typename P::In *in, typename P::Pos *pos, int *ks,
+// position; `emit` starts at the thread's first voxel; `region` = the range area.  With
+// kOwnBar the TMA barrier `bar` lies in the range area's first bytes and is invalidated
+// before the ranges overwrite it.  Returns 1 iff the line has a valid position (the same
+// for every column), else 0.
+template <int NB, class P, bool kOwnBar, class E>
+__device__ __forceinline__ int small_envelope(typename P::In *in, typename P::Pos *pos, uint8_t *region,
                                               const uint8_t *flags, int n, const P &pol, E &emit, uint64_t *bar,
                                               uint32_t phase, int32_t *err, bool &ok) {
+    using RIdx = RangeIdx<NB, P>;
     const int tid = threadIdx.x, lane = tid & (kTile - 1), band = tid >> 5;
     const int bl = Bands<NB, P::kMax>::len(n);
     const int lo = band * bl, hi = min(n, lo + bl);
@@ -961,40 +1008,43 @@ __device__ __forceinline__ int small_envelope(typename P::In *in, typename P::Po
     band_mask(flags, lo, hi, lane, vm);
     ok = mbar_wait_bounded(bar, phase, err);
     if (!ok) return 0;
-    const int k = small_build<NB>(pol, in + lane, pos + tid, lo, vm);
-    ks[tid] = k;
-    __syncthreads();
-    int total = 0;
-#pragma unroll
-    for (int b = 0; b < NB; ++b) total += ks[b * kTile + lane];
-    if (total == 0) return 0;   // the same for every column
+    const int k = small_build<NB>(pol, in + lane, pos + lane, lo, vm);
+    // [NB][32] first kept entry per band, then [NB][32] stack sizes, overwritten by the
+    // last kept entry + 1; the second half starts at byte 64 or later, past the barrier
+    RIdx *rj = reinterpret_cast<RIdx *>(region);
+    RIdx *ri = rj + NB * kTile;
+    ri[tid] = static_cast<RIdx>(k);
+    if (!__syncthreads_or(k)) return 0;   // no valid position: the same for every column
     SmallMerged<NB, P> M;
     M.in = in + lane;
     M.pos = pos + lane;
     M.bl = bl;
-    int16_t *rng = reinterpret_cast<int16_t *>(ks + NB * kTile);   // [2][NB][32]
     if (band == 0) {   // one merge per column, published to the other bands
+        if constexpr (kOwnBar) {
+            if (tid == 0) mbar_inval(bar);   // every thread has passed its wait
+            __syncwarp();
+        }
         int kk[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) kk[b] = ks[b * kTile + lane];
+        for (int b = 0; b < NB; ++b) kk[b] = ri[b * kTile + lane];
         M.merge(pol, kk);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            rng[b * kTile + lane] = static_cast<int16_t>(M.j[b]);
-            rng[(NB + b) * kTile + lane] = static_cast<int16_t>(M.i[b]);
+            rj[b * kTile + lane] = static_cast<RIdx>(M.j[b]);
+            ri[b * kTile + lane] = static_cast<RIdx>(M.i[b] + 1);
         }
     }
     __syncthreads();
     if (band != 0) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            M.j[b] = rng[b * kTile + lane];
-            M.i[b] = rng[(NB + b) * kTile + lane];
+            M.j[b] = rj[b * kTile + lane];
+            M.i[b] = static_cast<int>(ri[b * kTile + lane]) - 1;
         }
         M.find_last();
     }
     small_query<NB>(pol, M, lo, hi, band, emit);
-    return total;
+    return 1;
 }
 
 // Issues the TMA loads of a line tile: boxes of up to kBox positions along the line.
@@ -1012,8 +1062,8 @@ __device__ __forceinline__ void load_line_tile(In *in, const CUtensorMap *map, i
 
 // One pass-Y tile (grid g, slice z, columns x0..x0+31) with NB * 32 threads.  Same
 // contract as tile_y: `phase` is the barrier's current parity; ends with a CTA barrier
-// so the caller may reuse shared memory.
-template <int NB, bool L>
+// so the caller may reuse shared memory.  kOwnBar: `bar` lies in the tile's range area.
+template <int NB, bool L, bool kOwnBar>
 __device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
                                              int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
                                              int32_t *err) {
@@ -1026,7 +1076,7 @@ __device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, co
     const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
     In *in = reinterpret_cast<In *>(smem);                                        // [Y][32]
     auto *pos = reinterpret_cast<typename P::Pos *>(smem + align16(tile_in_bytes<NB, P>(Y)));
-    int *ks = reinterpret_cast<int *>(reinterpret_cast<uint8_t *>(pos) + align16(tile_pos_bytes<NB, P>(Y)));
+    uint8_t *region = smem + small_region_off<NB, P>(Y);
     if (tid == 0) load_line_tile(in, &tm[2 * g], Y, x0, z, true, bar);
     const int lo = (tid >> 5) * Bands<NB, P::kMax>::len(Y);
     const P pol{x0 + lane};
@@ -1034,11 +1084,11 @@ __device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, co
                 static_cast<uint32_t>((static_cast<int64_t>(z) * Y + lo) * Xp + x0 + lane), static_cast<uint32_t>(Xp),
                 0};
     bool ok;
-    const int total = small_envelope<NB>(in, pos, ks, gd[g].row_has + static_cast<int64_t>(z) * Y, Y, pol, e, bar,
-                                         phase, err, ok);
+    const int total = small_envelope<NB, P, kOwnBar>(in, pos, region, gd[g].row_has + static_cast<int64_t>(z) * Y, Y,
+                                                     pol, e, bar, phase, err, ok);
     if (!ok) {
         drain_after_timeout(bar, phase);
-        __syncthreads();
+        (void)__syncthreads_or(0);   // pairs with the first barrier of the others
         return false;
     }
     // an empty slice (the same for every column) writes no sites: pass Z skips it
@@ -1048,7 +1098,7 @@ __device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, co
 }
 
 // One pass-Z tile (grid g, row y, columns x0..x0+31) with NB * 32 threads.
-template <int NB, bool L>
+template <int NB, bool L, bool kOwnBar>
 __device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
                                              int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
                                              int32_t *err) {
@@ -1061,7 +1111,7 @@ __device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, co
     const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
     In *in = reinterpret_cast<In *>(smem);                                        // [Z][32]
     auto *pos = reinterpret_cast<typename P::Pos *>(smem + align16(tile_in_bytes<NB, P>(Z)));
-    int *ks = reinterpret_cast<int *>(reinterpret_cast<uint8_t *>(pos) + align16(tile_pos_bytes<NB, P>(Z)));
+    uint8_t *region = smem + small_region_off<NB, P>(Z);
     if (tid == 0) load_line_tile(in, &tm[2 * g + 1], Z, x0, y, false, bar);
     const int bl = Bands<NB, P::kMax>::len(Z);
     const int lo = (tid >> 5) * bl, hi = min(Z, lo + bl);
@@ -1073,10 +1123,11 @@ __device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, co
                 static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(y * X + (live ? x : 0)), plane, X, X * Y,
                 live, 0};
     bool ok;
-    const int total = small_envelope<NB>(in, pos, ks, gd[g].slice_has, Z, pol, e, bar, phase, err, ok);
+    const int total = small_envelope<NB, P, kOwnBar>(in, pos, region, gd[g].slice_has, Z, pol, e, bar, phase, err,
+                                                     ok);
     if (!ok) {
         drain_after_timeout(bar, phase);
-        __syncthreads();
+        (void)__syncthreads_or(0);   // pairs with the first barrier of the others
         return false;
     }
     if (total == 0) {   // empty grid
@@ -1097,15 +1148,15 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_y_small(const GridDesc *__r
                                                              const CUtensorMap *__restrict__ tm, int ng,
                                                              int32_t *err) {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint64_t bar;
     pdl_trigger();
     const int64_t t = blockIdx.x;
     const int g = find_grid(gd, ng, t, 0);
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + small_region_off<NB, PolY<L>>(gd[g].Y));
+    if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     pdl_wait();   // the staged tile and the validity flags come from the previous pass
     if (gd[g].changed && *gd[g].changed == 0) return;   // unchanged since its last EDT
-    tile_y_small<NB, L>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, 0, err);
+    tile_y_small<NB, L, true>(gd, tm, g, t - gd[g].ty_begin, smem, bar, 0, err);
 }
 
 template <int NB, bool L>
@@ -1113,15 +1164,15 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_z_small(const GridDesc *__r
                                                              const CUtensorMap *__restrict__ tm, int ng,
                                                              int32_t *err) {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint64_t bar;
     pdl_trigger();
     const int64_t t = blockIdx.x;
     const int g = find_grid(gd, ng, t, 1);
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + small_region_off<NB, PolZ<L>>(gd[g].Z));
+    if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     pdl_wait();   // the staged tile and the validity flags come from the previous pass
     if (gd[g].changed && *gd[g].changed == 0) return;   // unchanged since its last EDT
-    tile_z_small<NB, L>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, 0, err);
+    tile_z_small<NB, L, true>(gd, tm, g, t - gd[g].tz_begin, smem, bar, 0, err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1209,7 +1260,7 @@ __device__ __forceinline__ bool tile_y_generic(const GridDesc *__restrict__ gd, 
 template <bool SMALL>
 __device__ __forceinline__ bool tile_y(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
                                        int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
-    if constexpr (SMALL) return tile_y_small<2, false>(gd, tm, g, lt, smem, bar, phase, err);
+    if constexpr (SMALL) return tile_y_small<2, false, false>(gd, tm, g, lt, smem, bar, phase, err);
     else return tile_y_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
 }
 
@@ -1312,7 +1363,7 @@ __device__ __forceinline__ bool tile_z_generic(const GridDesc *__restrict__ gd, 
 template <bool SMALL>
 __device__ __forceinline__ bool tile_z(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
                                        int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
-    if constexpr (SMALL) return tile_z_small<2, false>(gd, tm, g, lt, smem, bar, phase, err);
+    if constexpr (SMALL) return tile_z_small<2, false, false>(gd, tm, g, lt, smem, bar, phase, err);
     else return tile_z_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
 }
 
