@@ -492,13 +492,14 @@ def run_closed_loop_leg(args, v):
     from paper_2407_02363_b300 import control
     out = {"what": "closed control loop: library frame (host buffers) + task-priority controller per cycle",
            "frames": args.loop_frames}
-    for name, avoid in (("avoidance", True), ("no_avoidance", False)):
-        control.run_closed_loop(v, n_frames=10, avoid=avoid)          # warm-up
+    for name, avoid, rule in (("avoidance", True, "fixed"), ("no_avoidance", False, "fixed"),
+                              ("avoidance_obb_spheres", True, "obb")):
+        control.run_closed_loop(v, n_frames=10, avoid=avoid, sphere_rule=rule)          # warm-up
         t0 = time.perf_counter()
-        r = control.run_closed_loop(v, n_frames=args.loop_frames, avoid=avoid)
+        r = control.run_closed_loop(v, n_frames=args.loop_frames, avoid=avoid, sphere_rule=rule)
         dt = time.perf_counter() - t0
         out[name] = {"min_clearance_m": r["min_clearance_m"], "tip_error_m": r["tip_error_m"],
-                     "ms_per_cycle_wall": dt / args.loop_frames * 1e3}
+                     "spheres": r["spheres"], "ms_per_cycle_wall": dt / args.loop_frames * 1e3}
     return out
 
 

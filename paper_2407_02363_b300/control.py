@@ -135,22 +135,30 @@ def fibonacci_sphere(n, radius):
 
 
 def run_closed_loop(v, n_frames=150, avoid=True, seed=3, dims=(96, 96, 96), vs=0.02, dt=1.0 / 60.0,
-                    obstacle_radius=0.12, params=None):
+                    obstacle_radius=0.12, params=None, sphere_rule="fixed"):
     """A synthetic closed loop (Alg. 2 with Alg. 3 as the consumer): a 7-DoF arm reaches
     for a target while a spherical obstacle (its surface as a point cloud) sweeps through
     the arm.  Every cycle runs one library frame (clear, insert links and cloud, EDT of
     both maps, sphere queries) and one controller step.  Returns the smallest geometric
     clearance between any bounding sphere and the obstacle over the run, and the final
-    distance of the reaching point to its target."""
+    distance of the reaching point to its target.  sphere_rule: "fixed" (24 spheres of
+    5 cm spread by link length) or "obb" (the OBB sphere rows of Sec. III-B)."""
     from . import synth
     params = params or AvoidanceParams()
     grid = synth.GridSpec(tuple(dims), vs)
     ext = np.array(grid.extent)
     chain = synth.make_chain(seed, (ext[0] / 2, ext[1] / 2, 0.25))
-    spheres = synth.sphere_model(chain)
+    models = synth.link_models(chain, vs)
+    if sphere_rule == "obb":
+        from .spheres import sphere_model_obb
+        spheres = sphere_model_obb(models)
+    elif sphere_rule == "fixed":
+        spheres = synth.sphere_model(chain)
+    else:
+        raise ValueError(f"unknown sphere rule {sphere_rule!r}")
     n = chain.n_joints
     m = v.Map(grid.dims, grid.voxel_size, grid.origin)
-    m.register_links(synth.link_models(chain, vs))
+    m.register_links(models)
     cchain = v.make_chain(chain)
     self_mask = ~np.asarray(spheres.acm, bool)
     q = np.array([0.4 * (-1) ** k for k in range(n)], np.float64)
@@ -181,4 +189,5 @@ def run_closed_loop(v, n_frames=150, avoid=True, seed=3, dims=(96, 96, 96), vs=0
         qdot = np.clip(qdot, -2.0, 2.0)
         q = q + dt * qdot
     m.close()
-    return {"min_clearance_m": min_clear, "tip_error_m": float(np.linalg.norm(target - tip)), "frames": n_frames}
+    return {"min_clearance_m": min_clear, "tip_error_m": float(np.linalg.norm(target - tip)), "frames": n_frames,
+            "spheres": int(len(spheres.radius))}

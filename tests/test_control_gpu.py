@@ -17,3 +17,13 @@ def test_closed_loop_avoids_the_sweeping_obstacle(seed):
     without = control.run_closed_loop(v, seed=seed, avoid=False)
     assert with_tasks["min_clearance_m"] > 0.0
     assert without["min_clearance_m"] < -0.05
+
+
+def test_closed_loop_with_obb_sphere_rows():
+    """The same loop with the bounding spheres of Sec. III-B (one row per link OBB)."""
+    v = lib()
+    with_tasks = control.run_closed_loop(v, seed=3, avoid=True, sphere_rule="obb")
+    without = control.run_closed_loop(v, seed=3, avoid=False, sphere_rule="obb")
+    assert with_tasks["spheres"] > 7
+    assert with_tasks["min_clearance_m"] > 0.0
+    assert without["min_clearance_m"] < -0.05
