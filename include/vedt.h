@@ -436,7 +436,9 @@ vedt_status vedt_selftest_wait(void *stream, uint32_t limit);
 /* Human-readable text for a status code (static storage). */
 const char *vedt_status_string(vedt_status s);
 
-/* Library version string. */
+/* Library version string; the bounds-checked debug build (libvedt_debug.so, built with
+ * -DVEDT_DEBUG_BOUNDS: the EDT passes check each index they compute and report a bad one
+ * as VEDT_ECUDA from vedt_check) says "index checks". */
 const char *vedt_version(void);
 
 #ifdef __cplusplus

@@ -196,7 +196,13 @@ GridDesc grid_of(const vedt_map *m, int i) {
 
 extern "C" {
 
-const char *vedt_version(void) { return "vedt 0.1 (sm_103a)"; }
+const char *vedt_version(void) {
+#ifdef VEDT_DEBUG_BOUNDS
+    return "vedt 0.1 (sm_103a, index checks)";
+#else
+    return "vedt 0.1 (sm_103a)";
+#endif
+}
 
 const char *vedt_status_string(vedt_status s) {
     switch (s) {

@@ -574,10 +574,12 @@ __device__ __forceinline__ bool dominated(int ca, int ha, int cb, int hb, int cc
 // positions (stride kTile), entry k's position kept in slot lo + k like its word.
 template <int NB, class P>
 __device__ __forceinline__ int small_build(const P &pol, typename P::In *col, typename P::Pos *cpos, int lo,
-                                           const uint32_t (&vm)[Bands<NB, P::kMax>::kWords]) {
+                                           const uint32_t (&vm)[Bands<NB, P::kMax>::kWords], int cap,
+                                           int32_t *err) {
     using Prod = typename P::Prod;
     int k = 0, a = 0, b = 0, ha = 0, hb = 0, dab = 0, wab = 0;
     auto step = [&](int c) {
+        if (!in_range(k, cap, err)) return;   // debug builds: the stack never outgrows its band
         const uint32_t r = col[c * kCols];
         const int hc = pol.h(r, c);
         while (k >= 2 && static_cast<Prod>(hc - hb) * wab <= static_cast<Prod>(dab) * (c - b)) {
@@ -644,8 +646,14 @@ struct SmallMerged {
     int bl;                     // band length
     int j[NB], i[NB];
     int last;                   // last non-empty band
+    int32_t *err;               // error word (debug bounds checks)
     // entry of slot s = b * bl + t (band b's stack entry t)
     __device__ __forceinline__ void at_slot(int s, int &c, uint32_t &r) const {
+        if (!in_range(s, NB * bl, err)) {
+            c = 0;
+            r = 0;
+            return;
+        }
         r = in[s * kCols];
         if constexpr (P::kPacked) c = P::pos_of(r);
         else c = pos[s * kTile];
@@ -928,11 +936,13 @@ struct EmitYs {
     Site *s2;
     uint32_t off, Xp;
     Site v;
+    uint32_t lim;   // elements of s2 (debug bounds checks)
+    int32_t *err;
     __device__ __forceinline__ void start(int c, uint32_t r) {
         v = static_cast<Site>(r | (static_cast<uint32_t>(c) << (L ? 16 : 8)));
     }
     __device__ __forceinline__ void put(int) {
-        s2[off] = v;
+        if (in_range(off, lim, err)) s2[off] = v;
         off += Xp;
     }
 };
@@ -945,12 +955,14 @@ struct EmitZs {
     int X, XY;
     bool live;
     int id;
+    uint32_t lim;   // voxels of the grid (debug bounds checks)
+    int32_t *err;
     __device__ __forceinline__ void start(int c, uint32_t r) {
         id = static_cast<int>(r & PolZ<L>::kMask) + X * static_cast<int>((r >> PolZ<L>::kShift) & PolZ<L>::kMask) +
              XY * c;
     }
     __device__ __forceinline__ void put(int val) {
-        if (live) {
+        if (live && in_range(off, lim, err)) {
             sq[off] = val;
             ix[off] = id;
         }
@@ -1008,7 +1020,7 @@ __device__ __forceinline__ int small_envelope(typename P::In *in, typename P::Po
     band_mask(flags, lo, hi, lane, vm);
     ok = mbar_wait_bounded(bar, phase, err);
     if (!ok) return 0;
-    const int k = small_build<NB>(pol, in + lane, pos + lane, lo, vm);
+    const int k = small_build<NB>(pol, in + lane, pos + lane, lo, vm, bl, err);
     // [NB][32] first kept entry per band, then [NB][32] stack sizes, overwritten by the
     // last kept entry + 1; the second half starts at byte 64 or later, past the barrier
     RIdx *rj = reinterpret_cast<RIdx *>(region);
@@ -1019,6 +1031,7 @@ __device__ __forceinline__ int small_envelope(typename P::In *in, typename P::Po
     M.in = in + lane;
     M.pos = pos + lane;
     M.bl = bl;
+    M.err = err;
     if (band == 0) {   // one merge per column, published to the other bands
         if constexpr (kOwnBar) {
             if (tid == 0) mbar_inval(bar);   // every thread has passed its wait
@@ -1082,7 +1095,7 @@ __device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, co
     const P pol{x0 + lane};
     EmitYs<L> e{static_cast<typename EmitYs<L>::Site *>(gd[g].s2),
                 static_cast<uint32_t>((static_cast<int64_t>(z) * Y + lo) * Xp + x0 + lane), static_cast<uint32_t>(Xp),
-                0};
+                0, static_cast<uint32_t>(Xp * Y * gd[g].Z), err};
     bool ok;
     const int total = small_envelope<NB, P, kOwnBar>(in, pos, region, gd[g].row_has + static_cast<int64_t>(z) * Y, Y,
                                                      pol, e, bar, phase, err, ok);
@@ -1121,7 +1134,7 @@ __device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, co
     const P pol{x, y};
     EmitZs<L> e{gd[g].sqdist, gd[g].idx,
                 static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(y * X + (live ? x : 0)), plane, X, X * Y,
-                live, 0};
+                live, 0, plane * static_cast<uint32_t>(Z), err};
     bool ok;
     const int total = small_envelope<NB, P, kOwnBar>(in, pos, region, gd[g].slice_has, Z, pol, e, bar, phase, err,
                                                      ok);
@@ -1197,12 +1210,15 @@ struct EmitY {
     typename Env<SMALL>::Site *po;
     int Xp;
     typename Env<SMALL>::Site v;
+    int64_t left;   // elements from po to the end of the buffer (debug bounds checks)
+    int32_t *err;
     __device__ __forceinline__ void site(int c, uint32_t r) {
         v = static_cast<typename Env<SMALL>::Site>(r | (static_cast<uint32_t>(c) << Env<SMALL>::kShift));
     }
     __device__ __forceinline__ void put(int val) {
-        *po = val == INT_MAX ? static_cast<typename Env<SMALL>::Site>(~0u) : v;
+        if (in_range(0, left, err)) *po = val == INT_MAX ? static_cast<typename Env<SMALL>::Site>(~0u) : v;
         po += Xp;
+        if constexpr (kCheckBounds) left -= Xp;
     }
 };
 
@@ -1249,7 +1265,8 @@ __device__ __forceinline__ bool tile_y_generic(const GridDesc *__restrict__ gd, 
     const int ci = tid & (kCols - 1);
     const int lo = tid >= kTile ? half : 0;
     const LineY<SMALL> L{in + ci, rh, x0 + ci};
-    EmitY<SMALL> emit{reinterpret_cast<Site *>(gd[g].s2) + (static_cast<int64_t>(z) * Y + lo) * Xp + x0 + ci, Xp, 0};
+    const int64_t oy = (static_cast<int64_t>(z) * Y + lo) * Xp + x0 + ci;
+    EmitY<SMALL> emit{reinterpret_cast<Site *>(gd[g].s2) + oy, Xp, 0, static_cast<int64_t>(Xp) * Y * gd[g].Z - oy, err};
     int k_total;
     envelope_two_warps<SMALL>(Y, tid, stack, ks, L, emit, k_total);
     if (x0 == 0 && tid == 0) gd[g].slice_has[z] = k_total > 0 ? 1 : 0;
@@ -1300,16 +1317,19 @@ struct EmitZ {
     int X, XY;
     int32_t id;
     bool live;
+    int64_t left;   // voxels from osq to the end of the field (debug bounds checks)
+    int32_t *err;
     __device__ __forceinline__ void site(int c, uint32_t r) {
         id = static_cast<int32_t>(r & Env<SMALL>::kMask) + X * static_cast<int32_t>(r >> Env<SMALL>::kShift) + XY * c;
     }
     __device__ __forceinline__ void put(int val) {
-        if (live) {
+        if (live && in_range(0, left, err)) {
             *osq = val;
             *oix = val == INT_MAX ? -1 : id;
         }
         osq += plane;
         oix += plane;
+        if constexpr (kCheckBounds) left -= plane;
     }
 };
 
@@ -1353,7 +1373,7 @@ __device__ __forceinline__ bool tile_z_generic(const GridDesc *__restrict__ gd, 
     const int64_t plane = static_cast<int64_t>(X) * Y;
     const int xc = x < X ? x : X - 1;   // padding columns build but never store
     const int64_t off = static_cast<int64_t>(lo) * plane + static_cast<int64_t>(y) * X + xc;
-    EmitZ<SMALL> emit{gd[g].sqdist + off, gd[g].idx + off, plane, X, X * Y, -1, x < X};
+    EmitZ<SMALL> emit{gd[g].sqdist + off, gd[g].idx + off, plane, X, X * Y, -1, x < X, plane * Z - off, err};
     int k_total;
     envelope_two_warps<SMALL>(Z, tid, stack, ks, L, emit, k_total);
     __syncthreads();

@@ -261,6 +261,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Debug builds (-DVEDT_DEBUG_BOUNDS, libvedt_debug.so) check the indices the EDT passes
+// compute against their buffers: a bad one sets kErrBounds in the error word (reported by
+// vedt_check as VEDT_ECUDA) and its access is skipped.  Release builds drop the checks.
+#ifdef VEDT_DEBUG_BOUNDS
+constexpr bool kCheckBounds = true;
+#else
+constexpr bool kCheckBounds = false;
+#endif
+
+__device__ __forceinline__ bool in_range(int64_t i, int64_t n, int32_t *err) {
+    if constexpr (!kCheckBounds) return true;
+    if (i >= 0 && i < n) return true;
+    if (err) atomicOr(err, kErrBounds);
+    return false;
+}
+
 // Bounded wait: gives up after `limit` polls (each try_wait already suspends for a
 // hardware-chosen interval), flags kErrTimeout and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int32_t *err,

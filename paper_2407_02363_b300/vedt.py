@@ -13,10 +13,13 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libvedt.so")
+# VEDT_DEBUG_BOUNDS=1 selects the bounds-checked build (python -m paper_2407_02363_b300.build --debug)
+DEBUG_BOUNDS = os.environ.get("VEDT_DEBUG_BOUNDS") == "1"
+LIB_PATH = os.path.join(_HERE, "libvedt_debug.so" if DEBUG_BOUNDS else "libvedt.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libvedt.so not built at {LIB_PATH}; run `python -m paper_2407_02363_b300.build`")
+    raise ImportError(f"{os.path.basename(LIB_PATH)} not built at {LIB_PATH}; run "
+                      f"`python -m paper_2407_02363_b300.build{' --debug' if DEBUG_BOUNDS else ''}`")
 
 _lib = ctypes.CDLL(LIB_PATH)
 
