@@ -356,6 +356,15 @@ vedt_status vedt_mlp_destroy(vedt_mlp *net);
 /* Loads fp32 parameters (host), resets the AdamW moments and step count; synchronises. */
 vedt_status vedt_mlp_set_params(vedt_mlp *net, const float *params_host, int64_t count);
 vedt_status vedt_mlp_get_params(vedt_mlp *net, float *params_host, int64_t count);
+/* Training state for checkpoint / resume: the parameters, the AdamW first and second
+ * moments (each `count` = vedt_mlp_num_params() fp32 values in the flat layout, host
+ * buffers) and the step count.  get synchronises; set loads all of it (the next
+ * vedt_mlp_train_step continues from there) and synchronises.  Errors: EINVAL (NULL
+ * pointers, wrong count, negative step), ECUDA. */
+vedt_status vedt_mlp_get_state(vedt_mlp *net, float *params_host, float *m1_host, float *m2_host, int64_t count,
+                               int64_t *step);
+vedt_status vedt_mlp_set_state(vedt_mlp *net, const float *params_host, const float *m1_host,
+                               const float *m2_host, int64_t count, int64_t step);
 /* q_dev: B x 7 fp32 joint angles; out_dev: B x 24 fp32 predicted distances.  Async.
  * One persistent fused kernel, one CTA per SM: each CTA keeps two 128-row activation
  * tiles in shared memory through all five layers, with one fp32 accumulator per tile in

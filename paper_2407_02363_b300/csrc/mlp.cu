@@ -941,16 +941,22 @@ int64_t vedt_mlp_num_params(void) {
     return c;
 }
 
-vedt_status vedt_mlp_set_params(vedt_mlp *n, const float *params, int64_t count) {
-    if (!n || !params || count != vedt_mlp_num_params()) return VEDT_EINVAL;
+// flat host layout -> the padded device layout (zeros in the padding)
+static std::vector<float> padded(const vedt_mlp *n, const float *flat) {
     std::vector<float> pad(static_cast<size_t>(n->np), 0.f);
     int64_t r = 0;
     for (int l = 0; l < kLayers; ++l) {
         const int Nv = layer_n_valid(l), Kv = layer_k_valid(l), K = layer_k(l);
         for (int i = 0; i < Nv; ++i)
-            for (int k = 0; k < Kv; ++k) pad[n->offW[l] + static_cast<int64_t>(i) * K + k] = params[r++];
-        for (int i = 0; i < Nv; ++i) pad[n->offB[l] + i] = params[r++];
+            for (int k = 0; k < Kv; ++k) pad[n->offW[l] + static_cast<int64_t>(i) * K + k] = flat[r++];
+        for (int i = 0; i < Nv; ++i) pad[n->offB[l] + i] = flat[r++];
     }
+    return pad;
+}
+
+vedt_status vedt_mlp_set_params(vedt_mlp *n, const float *params, int64_t count) {
+    if (!n || !params || count != vedt_mlp_num_params()) return VEDT_EINVAL;
+    const std::vector<float> pad = padded(n, params);
     MCHECK(cudaMemcpyAsync(n->p, pad.data(), sizeof(float) * n->np, cudaMemcpyHostToDevice, n->stream));
     MCHECK(cudaMemsetAsync(n->m, 0, sizeof(float) * n->np, n->stream));
     MCHECK(cudaMemsetAsync(n->v, 0, sizeof(float) * n->np, n->stream));
@@ -980,6 +986,28 @@ static vedt_status unpad(vedt_mlp *n, const float *dev, float *host, int64_t cou
 vedt_status vedt_mlp_get_params(vedt_mlp *n, float *params, int64_t count) {
     if (!n || !params) return VEDT_EINVAL;
     return unpad(n, n->p, params, count);
+}
+
+vedt_status vedt_mlp_get_state(vedt_mlp *n, float *params, float *m1, float *m2, int64_t count, int64_t *step) {
+    if (!n || !params || !m1 || !m2 || !step) return VEDT_EINVAL;
+    vedt_status st = unpad(n, n->p, params, count);
+    if (st == VEDT_OK) st = unpad(n, n->m, m1, count);
+    if (st == VEDT_OK) st = unpad(n, n->v, m2, count);
+    if (st == VEDT_OK) *step = n->step;
+    return st;
+}
+
+vedt_status vedt_mlp_set_state(vedt_mlp *n, const float *params, const float *m1, const float *m2, int64_t count,
+                               int64_t step) {
+    if (!n || !params || !m1 || !m2 || step < 0 || count != vedt_mlp_num_params()) return VEDT_EINVAL;
+    vedt_status st = vedt_mlp_set_params(n, params, count);   // also refreshes the bf16 copies
+    if (st != VEDT_OK) return st;
+    const std::vector<float> a = padded(n, m1), b = padded(n, m2);
+    MCHECK(cudaMemcpyAsync(n->m, a.data(), sizeof(float) * n->np, cudaMemcpyHostToDevice, n->stream));
+    MCHECK(cudaMemcpyAsync(n->v, b.data(), sizeof(float) * n->np, cudaMemcpyHostToDevice, n->stream));
+    MCHECK(cudaStreamSynchronize(n->stream));
+    n->step = step;
+    return VEDT_OK;
 }
 
 vedt_status vedt_mlp_forward(vedt_mlp *n, const float *q_dev, int B, float *out_dev) {

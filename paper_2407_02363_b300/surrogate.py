@@ -12,6 +12,7 @@ All compute runs in libvedt (CUDA); this module only schedules it.
 from __future__ import annotations
 
 import math
+import os
 import time
 from dataclasses import dataclass
 
@@ -159,6 +160,21 @@ def predict(net, q_dev, chunk=None):
         net.forward(q_dev[s:s + chunk].contiguous(), out[s:s + chunk])
     net.check()
     return out
+
+
+def cached_labels(lab, q, path):
+    """lab(q), kept in an .npz file: read back when the file holds labels of exactly these
+    joint states (a SHA-1 of q is stored with them), else computed and written."""
+    import hashlib
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    key = hashlib.sha1(q.tobytes()).hexdigest()
+    if os.path.exists(path):
+        with np.load(path) as z:
+            if str(z["key"]) == key:
+                return z["dist"], z["status"]
+    d, s = lab(q)
+    np.savez(path, key=np.array(key), dist=d, status=s)
+    return d, s
 
 
 def fit(lab, net, n_train, n_val, seed, steps, batch=8192, lr=3e-3, log_every=0):

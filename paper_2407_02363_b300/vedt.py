@@ -93,6 +93,8 @@ _sig = {
     "vedt_mlp_destroy": [_P],
     "vedt_mlp_set_params": [_P, _P, _I64],
     "vedt_mlp_get_params": [_P, _P, _I64],
+    "vedt_mlp_get_state": [_P, _P, _P, _P, _I64, _P],
+    "vedt_mlp_set_state": [_P, _P, _P, _P, _I64, _I64],
     "vedt_mlp_forward": [_P, _P, _I32, _P],
     "vedt_mlp_forward_layers": [_P, _P, _I32, _P],
     "vedt_mlp_grads": [_P, _P, _P, _P, _I32, _P, _I64, _P],
@@ -542,6 +544,29 @@ class MLP:
         p = np.zeros(self.n_params, dtype=np.float32)
         _chk(_lib.vedt_mlp_get_params(self._h, _np_ptr(p), p.size), "vedt_mlp_get_params")
         return p
+
+    def get_state(self):
+        """(params, AdamW first moments, second moments, step) for a checkpoint."""
+        p, m1, m2 = (np.zeros(self.n_params, dtype=np.float32) for _ in range(3))
+        step = ctypes.c_int64()
+        _chk(_lib.vedt_mlp_get_state(self._h, _np_ptr(p), _np_ptr(m1), _np_ptr(m2), p.size, ctypes.byref(step)),
+             "vedt_mlp_get_state")
+        return p, m1, m2, int(step.value)
+
+    def set_state(self, params, m1, m2, step):
+        p, a, b = (np.ascontiguousarray(x, dtype=np.float32) for x in (params, m1, m2))
+        _chk(_lib.vedt_mlp_set_state(self._h, _np_ptr(p), _np_ptr(a), _np_ptr(b), p.size, int(step)),
+             "vedt_mlp_set_state")
+
+    def save(self, path):
+        """Writes the training state to an .npz file (parameters, moments, step)."""
+        p, m1, m2, step = self.get_state()
+        np.savez(path, params=p, m1=m1, m2=m2, step=np.int64(step))
+
+    def load(self, path):
+        """Restores a state written by save(); training continues from its step."""
+        with np.load(path) as z:
+            self.set_state(z["params"], z["m1"], z["m2"], int(z["step"]))
 
     def forward(self, q_dev, out_dev, B=None):
         B = int(q_dev.shape[0]) if B is None else int(B)

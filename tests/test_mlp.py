@@ -175,3 +175,50 @@ def test_fused_forward_follows_training_updates():
     assert not torch.equal(got, before)
     assert rel(got.cpu().numpy().astype(np.float64), lay.cpu().numpy().astype(np.float64)) < 2e-3
     net.close()
+
+
+def test_checkpoint_round_trip_and_resume(tmp_path):
+    """save() / load() carry the parameters, both AdamW moments and the step exactly; a
+    network resumed from the file continues like the one that wrote it (the dW
+    reductions use fp32 atomics, so the match is close, not bitwise)."""
+    v = lib()
+    B = 1024
+    rng = np.random.default_rng(8)
+    q = torch.from_numpy(rng.uniform(-np.pi, np.pi, size=(B, 7)).astype(np.float32)).cuda()
+    W = torch.from_numpy(rng.normal(size=(7, 24)).astype(np.float32)).cuda()
+    y = 0.3 + 0.1 * torch.sin(q @ W)
+    a = _net(v, B, omlp.init_params(3))
+    for _ in range(20):
+        a.train_step(q, y, None, lr=2e-3, wd=1e-4)
+    a.check()
+    path = str(tmp_path / "mlp_state.npz")
+    a.save(path)
+    b = v.MLP(B)
+    b.load(path)
+    pa, m1a, m2a, sa = a.get_state()
+    pb, m1b, m2b, sb = b.get_state()
+    assert sa == sb == 20
+    assert np.array_equal(pa, pb) and np.array_equal(m1a, m1b) and np.array_equal(m2a, m2b)
+    assert np.abs(m1a).max() > 0 and np.abs(m2a).max() > 0
+    for net in (a, b):
+        for _ in range(10):
+            net.train_step(q, y, None, lr=2e-3, wd=1e-4)
+        net.check()
+    pa, _, _, sa = a.get_state()
+    pb, _, _, sb = b.get_state()
+    assert sa == sb == 30
+    # parameters whose gradient sums nearly cancel may take differently rounded AdamW
+    # steps; the bulk agrees to fp32 rounding and the loss is the same
+    assert float(np.quantile(np.abs(pa - pb), 0.999)) <= 1e-5
+    la, _ = a.grads(q, y)
+    lb, _ = b.grads(q, y)
+    assert abs(la - lb) <= 1e-3 * la
+    # a fresh network that only got the parameters restarts AdamW (step 0, zero moments)
+    c = v.MLP(B)
+    c.set_params(pa)
+    _, m1c, m2c, sc = c.get_state()
+    assert sc == 0 and not m1c.any() and not m2c.any()
+    with pytest.raises(v.VedtError):
+        c.set_state(pa, m1a, m2a, -1)
+    for net in (a, b, c):
+        net.close()

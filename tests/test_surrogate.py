@@ -2,6 +2,8 @@
 evaluation / fallback bookkeeping on the CPU, and on the GPU a short training run whose
 network, with the exact fallback below the margin, answers faster than the exact path
 alone without missing a near-collision configuration of the held-out set."""
+import os
+
 import numpy as np
 import pytest
 
@@ -44,6 +46,27 @@ def test_exact_labels_match_oracle():
                                  spheres.radius)
         assert np.array_equal(stat[i], r["status"])
         assert np.array_equal(dist[i].view(np.uint32), r["dist"].view(np.uint32))
+    lab.close()
+
+
+@pytest.mark.gpu
+def test_label_cache_reads_back_the_same_labels(tmp_path):
+    from paper_2407_02363_b300.surrogate import ExactSelfDistance, cached_labels
+    chain, spheres = _setup()
+    lab = ExactSelfDistance(chain, spheres, n_maps=8)
+    q = synth.joint_states(77, 12)
+    path = str(tmp_path / "labels.npz")
+    d1, s1 = cached_labels(lab, q, path)
+    stamp = os.path.getmtime(path)
+    d2, s2 = cached_labels(lab, q, path)
+    assert os.path.getmtime(path) == stamp          # read back, not rewritten
+    assert np.array_equal(d1, d2) and np.array_equal(s1, s2)
+    d0, s0 = lab(q)
+    assert np.array_equal(d0, d1) and np.array_equal(s0, s1)
+    q2 = q.copy()
+    q2[0, 0] += 0.1                                                 # other joint states: recomputed
+    d3, _ = cached_labels(lab, q2, path)
+    assert np.array_equal(d3, lab(q2)[0])
     lab.close()
 
 
