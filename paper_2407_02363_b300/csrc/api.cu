@@ -256,7 +256,8 @@ vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float
     const size_t desc_bytes = sizeof(GridDesc) * 4, tm_bytes = sizeof(CUtensorMap) * 8;
     if (e == cudaSuccess) e = cudaMalloc(&m->tab_mem, desc_bytes + tm_bytes + 256);
     if (e == cudaSuccess) e = cudaMalloc(&m->qgrids, sizeof(QueryGrid) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&m->q_in, sizeof(float) * 4 * kMaxQuery);
+    // three query input areas: vedt_query_spheres, then one per host-frame staging parity
+    if (e == cudaSuccess) e = cudaMalloc(&m->q_in, sizeof(float) * 3 * 4 * kMaxQuery);
     if (e == cudaSuccess) e = cudaMalloc(&m->q_out, sizeof(vedt_sphere_result) * 2 * kMaxQuery);
     if (e != cudaSuccess) {
         free_map(m);
@@ -663,19 +664,23 @@ vedt_status queue_host_frame(vedt_map *m, const float *xyz, int64_t n, const flo
     }
     const int b = m->parity;
     m->parity ^= 1;
-    if (n > 0) {
+    // the cloud and the sphere inputs go up on the copy stream (the map's stream then has
+    // one event wait between frames instead of copies, which would end the programmatic
+    // overlap of one frame's last kernel with the next frame's first)
+    float *qin = m->q_in + (1 + b) * 4 * kMaxQuery;
+    if (n > 0 || nq > 0) {
         VCHECK(cudaStreamWaitEvent(m->copy_stream, m->consumed[b], 0));
-        VCHECK(cudaMemcpyAsync(m->stage[b], xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->copy_stream));
+        if (n > 0)
+            VCHECK(cudaMemcpyAsync(m->stage[b], xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->copy_stream));
+        if (nq > 0) {
+            VCHECK(cudaMemcpyAsync(qin, centres, sizeof(float) * 3 * nq, cudaMemcpyHostToDevice, m->copy_stream));
+            VCHECK(cudaMemcpyAsync(qin + 3 * kMaxQuery, radii, sizeof(float) * nq, cudaMemcpyHostToDevice,
+                                   m->copy_stream));
+        }
         VCHECK(cudaEventRecord(m->copied[b], m->copy_stream));
         VCHECK(cudaStreamWaitEvent(m->stream, m->copied[b], 0));
     }
-    if (nq > 0) {
-        VCHECK(cudaMemcpyAsync(m->q_in, centres, sizeof(float) * 3 * nq, cudaMemcpyHostToDevice, m->stream));
-        VCHECK(cudaMemcpyAsync(m->q_in + 3 * kMaxQuery, radii, sizeof(float) * nq, cudaMemcpyHostToDevice,
-                               m->stream));
-    }
-    vedt_status st = vedt_frame(m, m->stage[b], n, T, chain, q, mask, m->q_in, m->q_in + 3 * kMaxQuery, nq,
-                                m->q_out);
+    vedt_status st = vedt_frame(m, m->stage[b], n, T, chain, q, mask, qin, qin + 3 * kMaxQuery, nq, m->q_out);
     if (st != VEDT_OK) return st;
     VCHECK(cudaEventRecord(m->consumed[b], m->stream));
     if (nq > 0)

@@ -172,7 +172,7 @@ struct vedt_map {
     void *tab_mem = nullptr;
     // query scratch
     QueryGrid *qgrids = nullptr;   // device [3]: env, self, env+self ... see below
-    float *q_in = nullptr;         // device centres (3*kMaxQuery) + radii (kMaxQuery)
+    float *q_in = nullptr;         // 3 areas of device centres (3*kMaxQuery) + radii (kMaxQuery)
     vedt_sphere_result *q_out = nullptr;
     // links
     float *link_pts = nullptr;
