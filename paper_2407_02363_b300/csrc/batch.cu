@@ -24,12 +24,6 @@ struct MapRef {
     int64_t N;
 };
 
-int sm_count() {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
-}
 
 // ClearMap of both grids of every map: blockIdx.y = map * 2 + grid.
 __global__ void __launch_bounds__(256) k_clear_many(const MapRef *__restrict__ maps) {

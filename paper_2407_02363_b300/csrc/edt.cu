@@ -1519,12 +1519,6 @@ __global__ void __launch_bounds__(kLanes) k_edt_persistent(const GridDesc *__res
 // ------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------
-static int sm_count() {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
-}
 
 static size_t smem_y(const GridTable &t) {
     if (!t.large) return static_cast<size_t>(small_smem<2, PolY<false>>(t.maxY));

@@ -203,10 +203,21 @@ __global__ void __launch_bounds__(128) k_query(const QueryGrid *__restrict__ gri
     out[t] = r;
 }
 
-static int sm_count() {
-    int dev = 0, sms = 148;
+
+int sm_count() {
+    // the launchers ask on every launch: remember the answer per device
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> cache[kMaxDevices] = {};
+    int dev = 0;
     cudaGetDevice(&dev);
+    const bool keep = dev >= 0 && dev < kMaxDevices;
+    if (keep) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (keep) cache[dev].store(sms, std::memory_order_relaxed);
     return sms;
 }
 

@@ -98,6 +98,9 @@ cudaError_t ensure_dyn_smem(size_t bytes) {
 CUresult encode_tmap(CUtensorMap *m, CUtensorMapDataType t, int elem, void *base,
                      uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1, uint32_t b2);
 
+// SM count of the current device, cached per device (insert.cu)
+int sm_count();
+
 // launchers (edt.cu)
 cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s);
 cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s);
