@@ -46,7 +46,7 @@ WORKLOAD = ("frame256: 256^3 grid at 1 cm; 300k-point synthetic depth-camera clo
 # launches, one map per launch) with a hash of the kernel
 # sources it was taken from (comments and blank space excluded) and the algorithmic bytes
 # of the captured launch; reported only while both still match.
-NCU_TRAFFIC = {"edt_z": {"bytes": 107460224, "alg_bytes_per_launch": 167772160, "src": "14b82876ac465812"}}
+NCU_TRAFFIC = {"edt_z": {"bytes": 107607168, "alg_bytes_per_launch": 167772160, "src": "8bf47ecec26302c4"}}
 KERNEL_SOURCES = ("paper_2407_02363_b300/csrc/edt.cu", "paper_2407_02363_b300/csrc/vedt_internal.h")
 
 
@@ -632,7 +632,8 @@ def run_logodds(args, v, W, clouds, centres, radii, m_sph, cchain, dev):
             res[mode]["update_launches"] = t[1]
         m.close()
     return {"what": "frame256 through vedt_frame, log-odds occupancy of the environment grid off / on "
-                    "(l_hit 9, l_miss 4, clamp [-20, 40], threshold 15), device time per frame; the update "
+                    "(l_hit 9, l_miss 4, clamp [-20, 40], threshold 15; the frame applies it inside the environment "
+                    "map's pass X), device time per frame; the separate update "
                     "kernel timed alone over 50 serial frames (4 B per voxel; its 33.6 MB fit in the 126 MB L2 "
                     "between the insertion and the EDT)", "frames": args.logodds_frames,
             "off": res["off"], "on": res["on"], "overhead_ms": res["on"]["ms_per_frame"] - res["off"]["ms_per_frame"]}

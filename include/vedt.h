@@ -113,7 +113,8 @@ vedt_status vedt_map_set_bands(vedt_map *map, int bands);
  * vedt_update_occupancy turns the current M_I (the voxels this frame's points landed in:
  * hits; all others: misses, no ray casting) into L <- clamp(L + l_hit | L - l_miss,
  * l_min, l_max) and sets M_I to L >= threshold.  vedt_frame / _host run it after the
- * point insertion.  0 <= l_hit, l_miss <= 255; -128 <= l_min <= 0 <= l_max <= 127;
+ * point insertion (inside M_I's pass X when every dim is <= 256 and the map is not
+ * incremental).  0 <= l_hit, l_miss <= 255; -128 <= l_min <= 0 <= l_max <= 127;
  * l_min < threshold (a threshold above l_max leaves M_I empty).
  * on = 0 frees the log-odds; enabling again restarts from 0.  Synchronises the map's
  * streams.  Errors: EINVAL, ENOMEM, ECUDA. */

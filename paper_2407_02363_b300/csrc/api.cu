@@ -527,7 +527,7 @@ vedt_status vedt_compute_edt(vedt_map *m, int which) {
         VCHECK(launch_occ_diff(m->occ[g0], m->snap + g0 * n_al, m->changed + g0, n_al, ng, m->stream));
         for (int g = g0; g < g0 + ng; ++g) m->snap_valid[g] = true;
     }
-    VCHECK(launch_pass_x(t, m->stream));
+    VCHECK(launch_pass_x(t, m->stream, (m->fuse_lo && which == VEDT_MAP_ENV) ? m->logodds : nullptr, m->lo_param));
     timing_end(m, slot);
     slot = timing_begin(m, VEDT_K_EDT_Y);
     VCHECK(launch_pass_y(t, m->stream));
@@ -617,8 +617,15 @@ vedt_status vedt_frame(vedt_map *m, const float *xyz, int64_t n, const float *T,
     if (st != VEDT_OK) return st;
     VCHECK(cudaEventRecord(m->self_done, m->side_stream));
     st = vedt_insert_pointcloud(m, xyz, n, T, 1, nullptr);
-    if (st == VEDT_OK && m->logodds) st = vedt_update_occupancy(m);
-    if (st == VEDT_OK) st = vedt_compute_edt(m, VEDT_MAP_ENV);
+    // the log-odds update rides in M_I's pass X (small grids, no incremental snapshot,
+    // which must see the updated occupancy before pass X); else its own kernel
+    const bool fuse = m->logodds && !m->incremental && !m->tab[VEDT_MAP_ENV - 1].large;
+    if (st == VEDT_OK && m->logodds && !fuse) st = vedt_update_occupancy(m);
+    if (st == VEDT_OK) {
+        m->fuse_lo = fuse;
+        st = vedt_compute_edt(m, VEDT_MAP_ENV);
+        m->fuse_lo = false;
+    }
     if (st != VEDT_OK) return st;
     VCHECK(cudaStreamWaitEvent(m->stream, m->self_done, 0));
     if (nq > 0) st = vedt_query_spheres_dev(m, centres, radii, nq, VEDT_MAP_BOTH, out);

@@ -372,6 +372,42 @@ __device__ __forceinline__ uint2 row_bytes8(const uint8_t *row, int X, int x0, b
     return make_uint2(lo, hi);
 }
 
+// The same bytes after this frame's log-odds step (LogOdds): a voxel is a hit iff its
+// occupancy byte is nonzero; the new log-odds and the 0/1 occupancy are stored back.
+__device__ __forceinline__ uint2 row_logodds8(uint8_t *row, int8_t *lrow, int X, int x0, bool vec,
+                                              const LogOdds &p) {
+    if (vec) {
+        if (x0 >= X) return make_uint2(0u, 0u);
+        uint2 o = *reinterpret_cast<const uint2 *>(row + x0);
+        uint2 l = *reinterpret_cast<const uint2 *>(lrow + x0);
+        uint8_t *ob = reinterpret_cast<uint8_t *>(&o);
+        int8_t *lb = reinterpret_cast<int8_t *>(&l);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int v = logodds_step(lb[b], ob[b] != 0, p);
+            lb[b] = static_cast<int8_t>(v);
+            ob[b] = v >= p.thr ? 1 : 0;
+        }
+        *reinterpret_cast<uint2 *>(row + x0) = o;
+        *reinterpret_cast<uint2 *>(lrow + x0) = l;
+        return o;
+    }
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int x = x0 + i;
+        if (x < X) {
+            const int v = logodds_step(lrow[x], row[x] != 0, p);
+            lrow[x] = static_cast<int8_t>(v);
+            const uint32_t b = v >= p.thr ? 1u : 0u;
+            row[x] = static_cast<uint8_t>(b);
+            if (i < 4) lo |= b << (8 * i);
+            else hi |= b << (8 * (i - 4));
+        }
+    }
+    return make_uint2(lo, hi);
+}
+
 __device__ __forceinline__ void pass_x_small_row(uint8_t *xs, uint8_t *row_has, int Xp, int64_t lr, int lane,
                                                  uint2 w) {
     constexpr int kNoLeft = -1024, kNoRight = 2048;
@@ -456,8 +492,11 @@ struct RowGrid {
 
 // INCR: the table's grids may be incremental maps; rows of a grid whose occupancy is
 // unchanged since its last EDT are skipped (the flag is read after the dependency wait).
-template <bool INCR>
-__global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict__ gd, int ng, int64_t rows_total) {
+// LO: the table is one grid with a log-odds occupancy `L`: each row's occupancy is
+// updated (hits and misses of this frame, LogOdds p) as it is loaded.
+template <bool INCR, bool LO>
+__global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict__ gd, int ng, int64_t rows_total,
+                                                      int8_t *__restrict__ L, LogOdds p) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     const int64_t stride = nwarps * kXRows;
@@ -480,6 +519,9 @@ __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict
         if (rr >= rows_total) return make_uint2(0u, 0u);
         if (!Gl.has(rr)) Gl.load(gd, ng, rr);
         if (INCR && Gl.skip) return make_uint2(0u, 0u);
+        if constexpr (LO)
+            return row_logodds8(const_cast<uint8_t *>(Gl.occ) + (rr - Gl.begin) * Gl.X, L + (rr - Gl.begin) * Gl.X,
+                                Gl.X, 8 * lane, Gl.vec, p);
         return row_bytes8(Gl.occ + (rr - Gl.begin) * Gl.X, Gl.X, 8 * lane, Gl.vec);
     };
     uint2 w[kXRows];
@@ -1536,7 +1578,7 @@ static size_t smem_z(const GridTable &t) {
     return rows * kCols * site + static_cast<size_t>((t.maxZ + 1) / 2) * kLanes * link + 16 + kLanes * 4 + t.maxZ;
 }
 
-cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s) {
+cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s, int8_t *logodds, const int *lo_param) {
     if (t.rows == 0) return cudaSuccess;
     const int64_t want = (t.rows + 7) / 8;
     const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
@@ -1546,7 +1588,8 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s) {
         static int per_sm = 0;
         if (per_sm == 0) {
             int occ = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass_x_small<false>, 256, 0) != cudaSuccess ||
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass_x_small<false, false>, 256, 0) !=
+                    cudaSuccess ||
                 occ < 1)
                 occ = 1;
             per_sm = occ;
@@ -1554,8 +1597,17 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s) {
         const int64_t cap_small = static_cast<int64_t>(sm_count()) * per_sm;
         const int64_t want_small = (t.rows + 8 * kXRows - 1) / (8 * kXRows);
         const int nb = static_cast<int>(want_small < cap_small ? want_small : cap_small);
-        if (t.incr) return launch_pdl(k_pass_x_small<true>, dim3(nb), dim3(256), 0, s, t.desc, t.n, t.rows);
-        return launch_pdl(k_pass_x_small<false>, dim3(nb), dim3(256), 0, s, t.desc, t.n, t.rows);
+        const LogOdds p = lo_param ? LogOdds{lo_param[0], lo_param[1], lo_param[2], lo_param[3], lo_param[4]}
+                                   : LogOdds{0, 0, 0, 0, 0};
+        if (logodds) {
+            if (t.n != 1 || t.incr) return cudaErrorInvalidValue;
+            return launch_pdl(k_pass_x_small<false, true>, dim3(nb), dim3(256), 0, s, t.desc, t.n, t.rows, logodds, p);
+        }
+        if (t.incr)
+            return launch_pdl(k_pass_x_small<true, false>, dim3(nb), dim3(256), 0, s, t.desc, t.n, t.rows,
+                              static_cast<int8_t *>(nullptr), p);
+        return launch_pdl(k_pass_x_small<false, false>, dim3(nb), dim3(256), 0, s, t.desc, t.n, t.rows,
+                          static_cast<int8_t *>(nullptr), p);
     } else if (t.maxXp <= 256) {
         return launch_pdl(k_pass_x<8, false>, dim3(blocks), dim3(256), 0, s, t.desc, t.n, t.rows);
     } else if (t.maxXp <= 512) {

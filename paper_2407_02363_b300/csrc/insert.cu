@@ -61,7 +61,6 @@ __global__ void __launch_bounds__(256) k_occ_diff(const uint8_t *__restrict__ oc
 // clamped to [l_min, l_max], and the voxel is occupied for the EDT iff it reaches the
 // threshold.  16 voxels per thread and iteration; the alignment tail past the n voxels
 // keeps its zeros.
-struct LogOdds { int hit, miss, lo, hi, thr; };
 
 __global__ void __launch_bounds__(256) k_logodds(uint8_t *__restrict__ occ, int8_t *__restrict__ L, int64_t n,
                                                  LogOdds p) {
@@ -80,7 +79,7 @@ __global__ void __launch_bounds__(256) k_logodds(uint8_t *__restrict__ occ, int8
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
             if (b < valid) {
-                const int v = min(max(static_cast<int>(lb[b]) + (ob[b] ? p.hit : -p.miss), p.lo), p.hi);
+                const int v = logodds_step(lb[b], ob[b] != 0, p);
                 lb[b] = static_cast<int8_t>(v);
                 ob[b] = v >= p.thr ? 1 : 0;
             }

@@ -102,7 +102,11 @@ CUresult encode_tmap(CUtensorMap *m, CUtensorMapDataType t, int elem, void *base
 int sm_count();
 
 // launchers (edt.cu)
-cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s);
+// logodds (non-null: small-mode tables of one grid only) = that grid's log-odds, updated
+// by pass X from the occupancy before the rows are swept; lo_param = {l_hit, l_miss,
+// l_min, l_max, threshold}
+cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s, int8_t *logodds = nullptr,
+                          const int *lo_param = nullptr);
 cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s);
 cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s);
 cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm, int rows_per_item,
@@ -168,6 +172,7 @@ struct vedt_map {
     // the update's parameters {l_hit, l_miss, l_min, l_max, threshold}
     int8_t *logodds = nullptr;
     int lo_param[5] = {0, 0, 0, 0, 0};
+    bool fuse_lo = false;   // set by vedt_frame: the M_I EDT's pass X applies the update
     int incremental = 0;
     bool snap_valid[2] = {false, false};   // fields match the snapshot (host view)
     // EDT launch tables for which = ENV (0), SELF (1), BOTH (2)
@@ -278,6 +283,14 @@ __device__ __forceinline__ bool in_range(int64_t i, int64_t n, int32_t *err) {
     if (i >= 0 && i < n) return true;
     if (err) atomicOr(err, kErrBounds);
     return false;
+}
+
+// Log-odds occupancy of M_I (Sec. III-A, integer log-odds reading): a hit adds l_hit, a
+// miss subtracts l_miss, the sum is clamped to [l_min, l_max]; occupied iff >= threshold.
+struct LogOdds { int hit, miss, lo, hi, thr; };
+
+__device__ __forceinline__ int logodds_step(int L, bool hit, const LogOdds &p) {
+    return min(max(L + (hit ? p.hit : -p.miss), p.lo), p.hi);
 }
 
 // Bounded wait: gives up after `limit` polls (each try_wait already suspends for a
