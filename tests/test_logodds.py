@@ -169,3 +169,32 @@ def test_turning_off_and_bad_arguments():
     m.update_occupancy()
     assert occ_np(m, v.MAP_ENV).sum() == 0           # one hit (9) is below the threshold
     m.close()
+
+
+@pytest.mark.parametrize("dims,incremental", [((300, 48, 40), False), ((96, 80, 72), True)])
+def test_frames_on_the_standalone_update_path(dims, incremental):
+    """Frames whose log-odds update cannot ride in pass X: a grid wider than 256 voxels,
+    and an incremental map (its snapshot diff must see the updated occupancy).  No arm:
+    the cloud alone, M_I against the oracle chain and its field exact."""
+    v = lib()
+    grid = synth.GridSpec(dims, 0.02)
+    m = v.Map(grid.dims, grid.voxel_size, grid.origin, stream=torch.cuda.Stream())
+    m.set_logodds(True, **PARAMS)
+    m.set_incremental(incremental)
+    X, Y, Z = dims
+    L = np.zeros((Z, Y, X), np.int8)
+    empty = np.zeros((Z, Y, X), np.uint8)
+    for f in range(5):
+        cloud = synth.surface_cloud(70 + (f % 3), grid, 30_000)      # frames 3 and 4 repeat 0 and 1
+        cl = torch.from_numpy(cloud).cuda()
+        torch.cuda.synchronize()
+        m.frame(cl, cl.shape[0], None, None, 0, None, None, 0, None)
+        m.check()
+        hit = np.zeros((Z, Y, X), np.uint8)
+        oracle.insert_points(hit, empty, grid.dims, grid.voxel_size, grid.origin, cloud, filter_self=True)
+        L, occ = logodds.update(L, hit, **PARAMS)
+        assert np.array_equal(occ_np(m, v.MAP_ENV), occ), f"frame {f}"
+        sq, ix = (t.cpu().numpy() for t in m.field(v.MAP_ENV))
+        assert np.array_equal(sq, oracle.edt(occ)[0])
+        check_idx_valid(occ, sq, ix)
+    m.close()
