@@ -71,6 +71,10 @@ def test_null_handle_calls_rejected(v):
     assert L.vedt_sor_stats(None, None, None) == v.EINVAL
     assert L.vedt_sor_mean_distances(None, None) == v.EINVAL
     assert L.vedt_sor_destroy(None) == v.OK
+    assert L.vedt_map_set_logodds(None, 1, 9, 4, -20, 40, 15) == v.EINVAL
+    assert L.vedt_update_occupancy(None) == v.EINVAL
+    assert L.vedt_mlp_get_state(None, None, None, None, 10, None) == v.EINVAL
+    assert L.vedt_mlp_set_state(None, None, None, None, 10, 0) == v.EINVAL
     out = ctypes.c_void_p()
     for bad in (0, -5):
         assert L.vedt_sor_create(bad, None, ctypes.byref(out)) == v.EINVAL
