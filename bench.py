@@ -152,11 +152,8 @@ def build_workload(n_frames, rank=0):
 
 
 def sphere_centres_lib(v, chain, spheres, q):
-    """Sphere centres C_i in the world from the library's host FK (Alg. 2 line 8)."""
-    P = v.fk(chain, q)
-    R = P[spheres.link]
-    c = np.einsum("nij,nj->ni", R[:, :, :3], spheres.local) + R[:, :, 3]
-    return c.astype(np.float32)
+    """Sphere centres C_i in the world from the library (vedt_sphere_centres, Alg. 2 line 8)."""
+    return v.sphere_centres(chain, spheres, q)
 
 
 # ------------------------------------------------------------------------------------
@@ -720,8 +717,7 @@ def run_batched(args, v, dev):
         ch.base[:, 3] = np.array(grid.extent) / 2
         P = v.fk(ch, qs[i])
         poses.append(P.astype(np.float32))
-        R = P[spheres.link]
-        centres.append((np.einsum("nij,nj->ni", R[:, :, :3], spheres.local) + R[:, :, 3]).astype(np.float32))
+        centres.append(v.sphere_centres(ch, spheres, qs[i]))
     offs = np.zeros(len(dims_list) + 1, dtype=np.int64)
     offs[1:] = np.cumsum([len(c) for c in clouds])
     xyz = torch.from_numpy(np.concatenate(clouds)).to(dev)
@@ -875,7 +871,7 @@ def run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream):
     N = W["grid"].n_voxels
     m_sph = len(spheres.radius)
     pinned = [torch.from_numpy(c).pin_memory() for c in W["clouds"]]
-    cen_host = [sphere_centres_lib(v, chain, spheres, q) for q in W["traj"]]
+    lib_chain = v.make_chain(chain)
     depth = 2
     item = v.SPHERE_DTYPE.itemsize
     outs = [torch.zeros(2 * m_sph * item, dtype=torch.uint8).pin_memory() for _ in range(depth)]
@@ -892,7 +888,9 @@ def run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream):
             if i >= depth:
                 evs[slot].synchronize()
                 read(slot)
-            m.frame_host_async(pinned[k], cchain, W["traj"][k], SELF_MASK, cen_host[k], spheres.radius, outs[slot])
+            # C_i <- FK(q) on the host for every step (Alg. 2 line 8), inside the timed loop
+            cen = v.sphere_centres(lib_chain, spheres, W["traj"][k])
+            m.frame_host_async(pinned[k], cchain, W["traj"][k], SELF_MASK, cen, spheres.radius, outs[slot])
             evs[slot].record(stream)
         for i in range(max(0, steps - depth), steps):
             evs[i % depth].synchronize()
@@ -912,8 +910,8 @@ def run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream):
     e2e = {"value": 2 * N * args.e2e_steps * world / e2e_s / 1e9, "unit": "Gvoxel/s",
            "h2d_bytes_per_step": N_POINTS * 12 + m_sph * 16, "d2h_bytes_per_step": 2 * m_sph * item,
            "steps": args.e2e_steps, "ms_per_step": e2e_s / args.e2e_steps * 1e3,
-           "api": "vedt_frame_host_async, two frames in flight (pinned host cloud in, sphere results read "
-                  "on the host every step)"}
+           "api": "vedt_sphere_centres + vedt_frame_host_async per step, two frames in flight (pinned host "
+                  "cloud in, sphere results read on the host every step)"}
     return e2e
 
 

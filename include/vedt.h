@@ -7,7 +7,7 @@
  *   line 4   ClearMap                                               -> vedt_clear
  *   line 5-6 UpdateLinks(q) + Insert(O_Lk) into M_S                 -> vedt_insert_links / vedt_insert_robot
  *   line 7   Insert(Point_Cloud) into M_I (robot points removed)    -> vedt_insert_pointcloud
- *   line 8   ForwardKinematics of the sphere centres                -> vedt_fk (host helper)
+ *   line 8   ForwardKinematics of the sphere centres                -> vedt_fk, vedt_sphere_centres (host)
  *   line 9   PBA_EDT(M_S, M_I): exact EDT, Sec. III-C, Alg. 1        -> vedt_compute_edt
  *   line 10  ExtractClosestObstaclePose, Eq. (dist), Alg. 3 l.3-4   -> vedt_query_spheres
  *
@@ -191,6 +191,20 @@ vedt_status vedt_fk(const vedt_chain *chain, const double *q, double *poses_out)
 
 /* vedt_fk for n joint vectors q[n][n_joints]: poses_out[n][n_joints + 1][12]. */
 vedt_status vedt_fk_batch(const vedt_chain *chain, const double *q, int64_t n, double *poses_out);
+
+/* C_i <- FK(q) (Alg. 2 line 8): world centres of m bounding spheres.  Sphere i sits on
+ * link link_of[i] (0 .. chain->n_joints; 0 = the static body) at local[3i .. 3i+3) in
+ * that link's frame (metres).  With T = vedt_fk(chain, q)[link_of[i]] (fp64) each
+ * coordinate is c_a = ((T_a0 l_0 + T_a1 l_1) + T_a2 l_2) + T_a3, summed left to right
+ * without FMA, then rounded to fp32 into centres_out[3i + a] (host memory, caller-owned,
+ * m x 3 floats).  m = 0 writes nothing.  Errors: EINVAL (null pointer with m > 0, m < 0,
+ * a link index outside 0 .. n_joints, an invalid chain). */
+vedt_status vedt_sphere_centres(const vedt_chain *chain, const double *q, int m, const int32_t *link_of,
+                                const double *local, float *centres_out);
+
+/* vedt_sphere_centres for n joint vectors q[n][n_joints]: centres_out[n][m][3]. */
+vedt_status vedt_sphere_centres_batch(const vedt_chain *chain, const double *q, int64_t n, int m,
+                                      const int32_t *link_of, const double *local, float *centres_out);
 
 /* vedt_fk followed by rounding the poses to fp32 and vedt_insert_links(link_mask).
  * The chain must have n_joints + 1 <= registered links.  Errors: as both calls. */
@@ -424,15 +438,20 @@ vedt_status vedt_sor_mean_distances(vedt_sor *f, const double **d_dev);
  * the device and has no latency bound) or a process whose device memory is already
  * reserved by another allocator.  It computes the same exact EDT as vedt_compute_edt for
  * one grid: occ_dev (X*Y*Z uint8, layout as above) in, sqdist_dev and idx_dev (X*Y*Z
- * int32 each) out, all caller-owned device memory, asynchronously on `stream`
- * (cudaStream_t, NULL = legacy default stream).  Scratch comes from one fixed array of
+ * int32 each) out, all caller-owned device memory, on `stream` (cudaStream_t, NULL =
+ * legacy default stream).  The call returns when its work on `stream` has finished (it
+ * synchronises the stream and reads back the device error word), so it also refuses a
+ * stream that is being captured (VEDT_ENOTSUP).  Scratch comes from one fixed array of
  * about 6.4 MB that the library keeps in every GPU's memory until the process exits: each
  * dimension must be <= 256 and ceil(X/32)*32*Y*Z <= 2^21 (a 128^3 grid fits), otherwise
  * the call returns VEDT_ENOTSUP without doing anything.  The first call on a device looks
- * the array up (cudaGetSymbolAddress); make that first call before any stream capture.
- * Calls share the array and leave their scratch in it; calls that may overlap on the GPU
- * (other streams, other host threads) race and must be serialised by the caller.
- * Errors: EINVAL (null pointer, dims < 1), ENOTSUP (grid larger than the scratch), ECUDA. */
+ * the array up (cudaGetSymbolAddress); like every handle of this library, that address
+ * does not survive cudaDeviceReset.  Calls share the array and leave their scratch in it;
+ * calls that may overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.
+ * Errors: EINVAL (null pointer, dims < 1), ENOTSUP (grid larger than the scratch, stream
+ * under capture), ECUDA (a CUDA error, or an index the bounds-checked build flagged),
+ * ETIMEOUT (an in-kernel wait expired). */
 vedt_status vedt_edt_noalloc(const uint8_t *occ_dev, int32_t X, int32_t Y, int32_t Z,
                              int32_t *sqdist_dev, int32_t *idx_dev, void *stream);
 

@@ -175,8 +175,7 @@ def run_closed_loop(v, n_frames=150, avoid=True, seed=3, dims=(96, 96, 96), vs=0
         ctr = mid + (f / max(n_frames - 1, 1) - 0.5) * 1.0 * direction
         cloud = (surf + ctr).astype(np.float32)
         poses = v.fk(chain, q)
-        R = poses[spheres.link]
-        centres = (np.einsum("nij,nj->ni", R[:, :, :3], spheres.local) + R[:, :, 3]).astype(np.float32)
+        centres = v.sphere_centres(cchain, spheres, q)
         res = m.frame_host(cloud, cchain, q, 0b111, centres, spheres.radius)
         gap = np.linalg.norm(centres.astype(np.float64) - ctr, axis=1) - obstacle_radius - spheres.radius
         min_clear = min(min_clear, float(gap.min()))

@@ -532,6 +532,41 @@ vedt_status vedt_fk_batch(const vedt_chain *c, const double *q, int64_t n, doubl
     return VEDT_OK;
 }
 
+vedt_status vedt_sphere_centres(const vedt_chain *c, const double *q, int n, const int32_t *link_of,
+                                const double *local, float *out) {
+    if (!c || n < 0 || c->n_joints < 1 || c->n_joints > VEDT_MAX_JOINTS) return VEDT_EINVAL;
+    if (n == 0) return VEDT_OK;
+    if (!q || !link_of || !local || !out) return VEDT_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (link_of[i] < 0 || link_of[i] > c->n_joints) return VEDT_EINVAL;
+    double P[(VEDT_MAX_JOINTS + 1) * 12];
+    const vedt_status st = vedt_fk(c, q, P);
+    if (st != VEDT_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        const double *T = P + 12 * link_of[i];
+        const double *l = local + 3 * i;
+        for (int a = 0; a < 3; ++a) {
+            double s = T[4 * a] * l[0];
+            s = s + T[4 * a + 1] * l[1];
+            s = s + T[4 * a + 2] * l[2];
+            out[3 * i + a] = static_cast<float>(s + T[4 * a + 3]);
+        }
+    }
+    return VEDT_OK;
+}
+
+vedt_status vedt_sphere_centres_batch(const vedt_chain *c, const double *q, int64_t n, int m, const int32_t *link_of,
+                                      const double *local, float *out) {
+    if (!c || n < 0 || m < 0 || c->n_joints < 1 || c->n_joints > VEDT_MAX_JOINTS) return VEDT_EINVAL;
+    if (n == 0 || m == 0) return VEDT_OK;
+    if (!q) return VEDT_EINVAL;
+    for (int64_t k = 0; k < n; ++k) {
+        const vedt_status st = vedt_sphere_centres(c, q + k * c->n_joints, m, link_of, local, out + k * m * 3);
+        if (st != VEDT_OK) return st;
+    }
+    return VEDT_OK;
+}
+
 vedt_status vedt_insert_robot(vedt_map *m, const vedt_chain *c, const double *q, uint32_t mask) {
     if (!m || !c || !q || c->n_joints < 1 || c->n_joints > VEDT_MAX_JOINTS) return VEDT_EINVAL;
     if (c->n_joints + 1 > m->n_links) return VEDT_EINVAL;

@@ -11,7 +11,11 @@
 // The caller still provides the occupancy input and the two output fields.  All calls
 // share the one array, which keeps whatever the last call left there; calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on it and must
-// be serialised by the caller.
+// be serialised by the caller.  The grid descriptor and the two tensor maps reach the
+// array as kernel parameters of a one-block header kernel (copied by the launch itself,
+// so nothing refers to this call's stack once it returns).  The call waits for its
+// passes and reads the device error word back, so a bounds error flagged by the
+// index-checked build or an expired in-kernel wait is returned to the caller.
 #include <mutex>
 #include <vector>
 
@@ -34,7 +38,8 @@ void *g_base[kMaxDevices] = {};
 
 // Device address of the scratch array for the current device, looked up once per device.
 // In host code g_noalloc_scratch only names a host-side stand-in, so its device address
-// must come from cudaGetSymbolAddress with that device current.
+// must come from cudaGetSymbolAddress with that device current.  (Like every handle of
+// this library, the address does not survive cudaDeviceReset of its device.)
 cudaError_t scratch_base(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -51,6 +56,23 @@ cudaError_t scratch_base(void **out) {
     return cudaSuccess;
 }
 
+// The scratch header of one call: grid descriptor, the two tensor maps (64-byte aligned
+// for TMA) and the cleared error word, written by thread 0 from the launch parameters.
+struct NoallocHeader {
+    GridDesc desc;
+    alignas(64) CUtensorMap tm[2];
+};
+
+__global__ void k_noalloc_header(const __grid_constant__ NoallocHeader h, NoallocHeader *dst, int32_t *err) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *dst = h;
+        *err = 0;
+        // the tensor maps were written through the generic proxy; release them to the
+        // tensor-map proxy the passes' TMA loads read them through
+        asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+    }
+}
+
 }  // namespace
 
 extern "C" vedt_status vedt_edt_noalloc(const uint8_t *occ_dev, int32_t X, int32_t Y, int32_t Z,
@@ -61,22 +83,27 @@ extern "C" vedt_status vedt_edt_noalloc(const uint8_t *occ_dev, int32_t X, int32
     const int32_t Xp = (X + kEnvCols - 1) / kEnvCols * kEnvCols;
     const int64_t Np = static_cast<int64_t>(Xp) * Y * Z;
     if (Np > kNoallocMaxVoxels) return VEDT_ENOTSUP;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the call ends by waiting for its own work, which a stream under capture cannot do
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return VEDT_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return VEDT_ENOTSUP;
 
     void *basev = nullptr;
     if (scratch_base(&basev) != cudaSuccess) return VEDT_ECUDA;
     uint8_t *base = static_cast<uint8_t *>(basev);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    // header: GridDesc at 0, tensor maps at 128 and 256, error word at 512
-    GridDesc *d_desc = reinterpret_cast<GridDesc *>(base);
-    CUtensorMap *d_tm = reinterpret_cast<CUtensorMap *>(base + 128);
+    // header: descriptor and tensor maps at 0, error word at 512
+    static_assert(sizeof(NoallocHeader) <= 512, "header must fit its slot");
+    NoallocHeader *d_hdr = reinterpret_cast<NoallocHeader *>(base);
     int32_t *d_err = reinterpret_cast<int32_t *>(base + 512);
     uint8_t *xs = base + kHeader;
     uint8_t *s2 = xs + ((Np + 255) / 256) * 256;
     uint8_t *row_has = s2 + ((2 * Np + 255) / 256) * 256;
     uint8_t *slice_has = row_has + static_cast<int64_t>(Y) * Z;
 
-    GridDesc g{};
+    NoallocHeader h{};
+    GridDesc &g = h.desc;
     g.occ = occ_dev;
     g.xs = xs;
     g.row_has = row_has;
@@ -89,23 +116,16 @@ extern "C" vedt_status vedt_edt_noalloc(const uint8_t *occ_dev, int32_t X, int32
     g.Z = Z;
     g.Xp = Xp;
     g.row_begin = g.ty_begin = g.tz_begin = 0;
-    CUtensorMap tm[2];
     const uint32_t by = static_cast<uint32_t>(Y), bz = static_cast<uint32_t>(Z);
-    if (encode_tmap(&tm[0], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, xs, Xp, Y, Z, kEnvCols, by, 1) != CUDA_SUCCESS ||
-        encode_tmap(&tm[1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s2, Xp, Y, Z, kEnvCols, 1, bz) != CUDA_SUCCESS)
+    if (encode_tmap(&h.tm[0], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, xs, Xp, Y, Z, kEnvCols, by, 1) != CUDA_SUCCESS ||
+        encode_tmap(&h.tm[1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s2, Xp, Y, Z, kEnvCols, 1, bz) != CUDA_SUCCESS)
         return VEDT_ECUDA;
-
-    // g and tm live on this stack frame: cudaMemcpyAsync from pageable memory stages them
-    // before returning, and no call below allocates device memory
-    static_assert(sizeof(GridDesc) <= 128, "descriptor must fit its header slot");
-    if (cudaMemcpyAsync(d_desc, &g, sizeof(GridDesc), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d_tm, tm, sizeof(tm), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(d_err, 0, sizeof(int32_t), s) != cudaSuccess)
-        return VEDT_ECUDA;
+    k_noalloc_header<<<1, 32, 0, s>>>(h, d_hdr, d_err);
+    if (cudaGetLastError() != cudaSuccess) return VEDT_ECUDA;
 
     GridTable t{};
-    t.desc = d_desc;
-    t.tmaps = d_tm;
+    t.desc = &d_hdr->desc;
+    t.tmaps = d_hdr->tm;
     t.n = 1;
     t.large = 0;
     t.maxY = Y;
@@ -118,5 +138,11 @@ extern "C" vedt_status vedt_edt_noalloc(const uint8_t *occ_dev, int32_t X, int32
     if (launch_pass_x(t, s) != cudaSuccess || launch_pass_y(t, s) != cudaSuccess ||
         launch_pass_z(t, s) != cudaSuccess)
         return VEDT_ECUDA;
+    // device-side errors of this call: index checks of the debug build, expired waits
+    int32_t e = 0;
+    if (cudaMemcpyAsync(&e, d_err, sizeof(e), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return VEDT_ECUDA;
+    if (e) return (e & kErrTimeout) ? VEDT_ETIMEOUT : VEDT_ECUDA;
     return VEDT_OK;
 }

@@ -208,10 +208,7 @@ def make_requests(seed, n, sizes=(128, 256, 512), rate_hz=120.0, voxel=0.01, poi
     reqs = []
     for i in range(n):
         S = int(sizes[rng.integers(0, len(sizes))])
-        ch = chain[S]
-        P = v.fk(ch, traj[i])
-        R = P[spheres.link]
-        cen = (np.einsum("nij,nj->ni", R[:, :, :3], spheres.local) + R[:, :, 3]).astype(np.float32)
+        cen = v.sphere_centres(cchain[S], spheres, traj[i])
         cl = clouds[S][int(rng.integers(0, len(clouds[S])))]
         reqs.append(Request(rid=i, dims=(S, S, S), cloud=cl, q=traj[i], centres=cen, radii=spheres.radius,
                             arrival=float(arr[i]), chain=cchain[S]))

@@ -56,10 +56,6 @@ class ExactSelfDistance:
         self.batch.set_frame(None, self.offs, self.poses, self_mask, self.cen, self.radii, m, self.out)
         self.batch.capture()
 
-    def _centres(self, P):
-        R = P[:, self.spheres.link]                                   # (n, m, 3, 4)
-        return (np.einsum("nmij,mj->nmi", R[..., :3], self.spheres.local) + R[..., 3]).astype(np.float32)
-
     def __call__(self, q):
         """(N, 7) joint angles -> (dist (N, m) float32 metres, status (N, m) int32)."""
         q = np.asarray(q, dtype=np.float64)
@@ -73,7 +69,7 @@ class ExactSelfDistance:
                 qc = np.concatenate([qc, np.repeat(qc[-1:], self.n_maps - n, axis=0)])
             P = v.fk_batch(self.cchain, qc)
             self.poses[:] = P[:, : self.n_links].astype(np.float32)
-            self.cen.copy_(self.torch.from_numpy(self._centres(P)))
+            self.cen.copy_(self.torch.from_numpy(v.sphere_centres_batch(self.cchain, self.spheres, qc)))
             self.batch.set_frame(None, self.offs, self.poses, self.mask, self.cen, self.radii, self.m, self.out)
             self.batch.replay()
             self.batch.check()

@@ -101,6 +101,8 @@ _sig = {
     "vedt_mlp_train_step": [_P, _P, _P, _P, _I32, _F32, _F32, _P],
     "vedt_mlp_check": [_P],
     "vedt_fk_batch": [_P, _P, _I64, _P],
+    "vedt_sphere_centres": [_P, _P, _I32, _P, _P, _P],
+    "vedt_sphere_centres_batch": [_P, _P, _I64, _I32, _P, _P, _P],
     "vedt_batch_set_grids": [_P, _I32],
     "vedt_frame_host_async": [_P, _P, _I64, _P, _P, _P, _U32, _P, _P, _I32, _P],
     "vedt_frame_done": [_P],
@@ -156,8 +158,21 @@ def stream_handle(s):
 
 def edt_noalloc(occ_dev, dims, sqdist_dev, idx_dev, stream=None):
     """Exact EDT of one grid into caller-provided device buffers using the library's
-    fixed static scratch (no device allocation; see vedt_edt_noalloc in include/vedt.h)."""
+    fixed static scratch (no device allocation; see vedt_edt_noalloc in include/vedt.h).
+    occ_dev: contiguous CUDA uint8 tensor of X*Y*Z voxels; sqdist_dev, idx_dev: contiguous
+    CUDA int32 tensors of at least X*Y*Z elements.  Returns once the fields are written."""
+    import torch
     X, Y, Z = (int(v) for v in dims)
+    n = X * Y * Z
+    bufs = ((occ_dev, torch.uint8, "occupancy"), (sqdist_dev, torch.int32, "sqdist"), (idx_dev, torch.int32, "idx"))
+    for t, dt, name in bufs:
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_contiguous():
+            raise ValueError(f"edt_noalloc: {name} must be a contiguous {dt} tensor")
+        if t.numel() < n or (name == "occupancy" and t.numel() != n):
+            raise ValueError(f"edt_noalloc: {name} holds {t.numel()} elements, the grid has {n}")
+    for t, _, name in bufs:
+        if not t.is_cuda:
+            raise ValueError(f"edt_noalloc: {name} must be in device memory")
     _chk(_lib.vedt_edt_noalloc(dev_ptr(occ_dev), X, Y, Z, dev_ptr(sqdist_dev), dev_ptr(idx_dev),
                                stream_handle(stream)), "vedt_edt_noalloc")
 
@@ -201,6 +216,31 @@ def fk_batch(chain, q) -> np.ndarray:
     qa = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, c.n_joints)
     out = np.zeros((qa.shape[0], c.n_joints + 1, 3, 4), dtype=np.float64)
     _chk(_lib.vedt_fk_batch(ctypes.byref(c), _np_ptr(qa), qa.shape[0], _np_ptr(out)), "vedt_fk_batch")
+    return out
+
+
+def sphere_centres(chain, spheres, q) -> np.ndarray:
+    """C_i <- FK(q) (Alg. 2 line 8) through vedt_sphere_centres: (m, 3) float32 world
+    centres of the spheres (`spheres.link`, `spheres.local` in link frames)."""
+    c = chain if isinstance(chain, Chain) else make_chain(chain)
+    qa = np.ascontiguousarray(q, dtype=np.float64)
+    lk = np.ascontiguousarray(spheres.link, dtype=np.int32)
+    lc = np.ascontiguousarray(spheres.local, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((lk.shape[0], 3), dtype=np.float32)
+    _chk(_lib.vedt_sphere_centres(ctypes.byref(c), _np_ptr(qa), lk.shape[0], _np_ptr(lk), _np_ptr(lc),
+                                  _np_ptr(out)), "vedt_sphere_centres")
+    return out
+
+
+def sphere_centres_batch(chain, spheres, q) -> np.ndarray:
+    """sphere_centres for many joint vectors: (n, m, 3) float32."""
+    c = chain if isinstance(chain, Chain) else make_chain(chain)
+    qa = np.ascontiguousarray(q, dtype=np.float64).reshape(-1, c.n_joints)
+    lk = np.ascontiguousarray(spheres.link, dtype=np.int32)
+    lc = np.ascontiguousarray(spheres.local, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((qa.shape[0], lk.shape[0], 3), dtype=np.float32)
+    _chk(_lib.vedt_sphere_centres_batch(ctypes.byref(c), _np_ptr(qa), qa.shape[0], lk.shape[0], _np_ptr(lk),
+                                        _np_ptr(lc), _np_ptr(out)), "vedt_sphere_centres_batch")
     return out
 
 

@@ -90,6 +90,46 @@ def test_fk_matches_oracle(v, oracle_mod):
         assert np.array_equal(P.astype(np.float32), R.astype(np.float32))
 
 
+def test_sphere_centres_bitequal_to_oracle(v, oracle_mod):
+    """vedt_sphere_centres (Alg. 2 line 8 behind the ABI) rounds the same fp64 sums as the
+    oracle's sphere_centres, in the same order: identical fp32 centres, one by one and
+    batched."""
+    chain = synth.make_chain(3, (1.28, 1.28, 1.28))
+    spheres = synth.sphere_model(chain)
+    rng = np.random.default_rng(5)
+    off_axis = synth.SphereModel(link=np.array([0, 1, 4, 7, 7], np.int32), local=rng.uniform(-0.2, 0.2, (5, 3)),
+                                 radius=np.full(5, 0.05, np.float32))
+    qs = synth.joint_states(6, 12)
+    for sph in (spheres, off_axis):
+        batch = v.sphere_centres_batch(chain, sph, qs)
+        for i, q in enumerate(qs):
+            want = oracle_mod.sphere_centres(chain, sph, q)
+            got = v.sphere_centres(chain, sph, q)
+            assert got.dtype == np.float32 and np.array_equal(got, want)
+            assert np.array_equal(batch[i], want)
+
+
+def test_sphere_centres_rejects_bad_arguments(v):
+    import ctypes
+    chain = synth.make_chain(3, (1.28, 1.28, 1.28))
+    c = v.make_chain(chain)
+    q = np.zeros(7)
+    loc = np.zeros((2, 3))
+    out = np.zeros((2, 3), np.float32)
+    L = v._lib
+    for links in (np.array([0, 8], np.int32), np.array([-1, 1], np.int32)):
+        assert L.vedt_sphere_centres(ctypes.byref(c), v._np_ptr(q), 2, v._np_ptr(links), v._np_ptr(loc),
+                                     v._np_ptr(out)) == v.EINVAL
+    ok = np.array([0, 7], np.int32)
+    assert L.vedt_sphere_centres(None, v._np_ptr(q), 2, v._np_ptr(ok), v._np_ptr(loc), v._np_ptr(out)) == v.EINVAL
+    assert L.vedt_sphere_centres(ctypes.byref(c), None, 2, v._np_ptr(ok), v._np_ptr(loc), v._np_ptr(out)) == v.EINVAL
+    assert L.vedt_sphere_centres(ctypes.byref(c), v._np_ptr(q), -1, v._np_ptr(ok), v._np_ptr(loc),
+                                 v._np_ptr(out)) == v.EINVAL
+    assert L.vedt_sphere_centres(ctypes.byref(c), None, 0, None, None, None) == v.OK
+    assert L.vedt_sphere_centres_batch(ctypes.byref(c), v._np_ptr(q), -1, 2, v._np_ptr(ok), v._np_ptr(loc),
+                                       v._np_ptr(out)) == v.EINVAL
+
+
 def test_binding_refuses_to_load_without_the_library(tmp_path):
     """No CPU fallback: a copy of the package without libvedt.so fails at import."""
     import shutil

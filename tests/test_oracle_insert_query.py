@@ -107,6 +107,52 @@ def test_fk_planar_closed_form(oracle_mod):
                                [math.sin(th[k - 1]), math.cos(th[k - 1]), 0], [0, 0, 1]], atol=1e-12)
 
 
+def _planar_chain(L, base_xyz, base_R=None):
+    """All joint axes parallel to the base's z axis, link k+1 offset along link k's x."""
+    n = len(L)
+    base = np.zeros((3, 4))
+    base[:, :3] = np.eye(3) if base_R is None else base_R
+    base[:, 3] = base_xyz
+    offs = np.zeros((n, 3, 4))
+    for k in range(n):
+        offs[k, :, :3] = np.eye(3)
+        offs[k, :, 3] = (L[k - 1] if k > 0 else 0.0, 0.0, 0.0)
+    return synth.Chain(base=base, offsets=offs, lengths=np.array(L))
+
+
+@pytest.mark.parametrize("tilt", [False, True])
+def test_sphere_centres_planar_closed_form(oracle_mod, tilt):
+    """Alg. 2 line 8 on a planar chain, by hand: link k's frame has heading
+    th_k = q_1 + ... + q_k and origin p_k = b + sum_{i<k} L_i (cos th_i, sin th_i, 0); a
+    sphere at local (lx, ly, lz) on link k sits at
+    p_k + (lx cos th_k - ly sin th_k, lx sin th_k + ly cos th_k, lz).
+    Off-axis local offsets, every link, the static body (link 0, th_0 = 0) and a base
+    tilted 90 degrees about x (the plane becomes x-z) catch a wrong link index, a
+    transposed rotation and a dropped translation."""
+    L = [0.3, 0.25, 0.2, 0.15, 0.1]
+    b = np.array([0.1, -0.2, 0.7])
+    Rb = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]]) if tilt else np.eye(3)
+    chain = _planar_chain(L, b, Rb)
+    rng = np.random.default_rng(17)
+    links = np.array([0, 1, 1, 2, 3, 3, 4, 5, 5, 2], dtype=np.int32)
+    local = rng.uniform(-0.1, 0.1, size=(len(links), 3))
+    sph = synth.SphereModel(link=links, local=local, radius=np.full(len(links), 0.05, np.float32))
+    for q in (np.array([0.3, -1.1, 2.0, 0.7, -0.4]), rng.uniform(-np.pi, np.pi, 5)):
+        got = oracle_mod.sphere_centres(chain, sph, q)
+        th = np.concatenate([[0.0], np.cumsum(q)])          # th[k] = heading of link k
+        org = [np.zeros(3)]
+        for k in range(1, len(L) + 1):
+            o = np.zeros(3)
+            for i in range(1, k):
+                o += L[i - 1] * np.array([math.cos(th[i]), math.sin(th[i]), 0.0])
+            org.append(o)
+        for i, (k, (lx, ly, lz)) in enumerate(zip(links, local)):
+            c, s_ = math.cos(th[k]), math.sin(th[k])
+            planar = org[k] + np.array([lx * c - ly * s_, lx * s_ + ly * c, lz])
+            want = b + Rb @ planar
+            assert np.abs(got[i].astype(np.float64) - want).max() <= 1e-6, (i, k, got[i], want)
+
+
 def test_fk_rotations_orthonormal(oracle_mod):
     chain = synth.make_chain(5, (1.0, 1.0, 1.0))
     for q in synth.joint_states(6, 10):
