@@ -1666,14 +1666,7 @@ static int bands_for(const GridTable &t, int line) {
 cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) {
     if (t.tiles_y == 0) return cudaSuccess;
     const int nb = bands_for(t, t.maxY);
-    if (!t.large) {
-        switch (nb) {
-            case 1: return launch_small<1, k_pass_y_small<1, false>>(t.tiles_y, small_smem<1, PolY<false>>(t.maxY), t, s);
-            case 2: return launch_small<2, k_pass_y_small<2, false>>(t.tiles_y, small_smem<2, PolY<false>>(t.maxY), t, s);
-            case 8: return launch_small<8, k_pass_y_small<8, false>>(t.tiles_y, small_smem<8, PolY<false>>(t.maxY), t, s);
-            default: return launch_small<4, k_pass_y_small<4, false>>(t.tiles_y, small_smem<4, PolY<false>>(t.maxY), t, s);
-        }
-    }
+    if (!t.large) return launch_env_y(t, nb, s);
     if (nb == 4) return launch_small<4, k_pass_y_small<4, true>>(t.tiles_y, small_smem<4, PolY<true>>(t.maxY), t, s);
     return launch_small<8, k_pass_y_small<8, true>>(t.tiles_y, small_smem<8, PolY<true>>(t.maxY), t, s);
 }
@@ -1681,14 +1674,7 @@ cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) {
 cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s) {
     if (t.tiles_z == 0) return cudaSuccess;
     const int nb = bands_for(t, t.maxZ);
-    if (!t.large) {
-        switch (nb) {
-            case 1: return launch_small<1, k_pass_z_small<1, false>>(t.tiles_z, small_smem<1, PolZ<false>>(t.maxZ), t, s);
-            case 2: return launch_small<2, k_pass_z_small<2, false>>(t.tiles_z, small_smem<2, PolZ<false>>(t.maxZ), t, s);
-            case 8: return launch_small<8, k_pass_z_small<8, false>>(t.tiles_z, small_smem<8, PolZ<false>>(t.maxZ), t, s);
-            default: return launch_small<4, k_pass_z_small<4, false>>(t.tiles_z, small_smem<4, PolZ<false>>(t.maxZ), t, s);
-        }
-    }
+    if (!t.large) return launch_env_z(t, nb, s);
     if (nb == 4) return launch_small<4, k_pass_z_small<4, true>>(t.tiles_z, small_smem<4, PolZ<true>>(t.maxZ), t, s);
     return launch_small<8, k_pass_z_small<8, true>>(t.tiles_z, small_smem<8, PolZ<true>>(t.maxZ), t, s);
 }

@@ -109,6 +109,9 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s, int8_t *logodds = 
                           const int *lo_param = nullptr);
 cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s);
 cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s);
+// small-mode envelope passes (envelope.cu), `bands` per line = 1, 2, 4 or 8
+cudaError_t launch_env_y(const GridTable &t, int bands, cudaStream_t s);
+cudaError_t launch_env_z(const GridTable &t, int bands, cudaStream_t s);
 cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm, int rows_per_item,
                               cudaStream_t s);
 cudaError_t launch_wait_selftest(const unsigned *counter, uint32_t limit, int32_t *err, cudaStream_t s);
