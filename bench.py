@@ -46,8 +46,9 @@ WORKLOAD = ("frame256: 256^3 grid at 1 cm; 300k-point synthetic depth-camera clo
 # launches, one map per launch) with a hash of the kernel
 # sources it was taken from (comments and blank space excluded) and the algorithmic bytes
 # of the captured launch; reported only while both still match.
-NCU_TRAFFIC = {"edt_z": {"bytes": 107607168, "alg_bytes_per_launch": 167772160, "src": "8bf47ecec26302c4"}}
-KERNEL_SOURCES = ("paper_2407_02363_b300/csrc/edt.cu", "paper_2407_02363_b300/csrc/vedt_internal.h")
+NCU_TRAFFIC = {"edt_z": {"bytes": 105844352, "alg_bytes_per_launch": 167772160, "src": "ddebe56f7edd5139"}}
+KERNEL_SOURCES = ("paper_2407_02363_b300/csrc/envelope.cuh", "paper_2407_02363_b300/csrc/envelope.cu",
+                  "paper_2407_02363_b300/csrc/edt.cu", "paper_2407_02363_b300/csrc/vedt_internal.h")
 
 
 def code_hash(texts):
@@ -66,10 +67,11 @@ DEVICE_PART = "device helpers: mbarrier + TMA"
 
 
 def kernel_texts(read):
-    """The EDT kernels' source: edt.cu, and the device-code part of vedt_internal.h (the
-    host-side structs above it do not reach the kernels)."""
-    edt, internal = (read(f) for f in KERNEL_SOURCES)
-    return [edt, internal[internal.index(DEVICE_PART):]]
+    """The EDT kernels' source: envelope.cuh / envelope.cu (passes Y and Z), edt.cu, and
+    the device-code part of vedt_internal.h (the host-side structs above it do not reach
+    the kernels)."""
+    *srcs, internal = (read(f) for f in KERNEL_SOURCES)
+    return srcs + [internal[internal.index(DEVICE_PART):]]
 
 
 def kernel_src_hash():
@@ -370,6 +372,11 @@ def run_vedt(args):
     for i in range(args.warmup):
         step(i)
     m.check()
+    # bands per line for this frame workload: the autotuner's pick (a short sweep of
+    # frames at every band count; cached per GPU and dims), kept for the timed region
+    import paper_2407_02363_b300.autotune as at
+    tuned_bands, tuned_ms = at.tune_map(m, stream, grid.dims, op=lambda: [step(j) for j in range(10)], reps=3,
+                                        force=True, kind="frame")
     # ---- timed region: K frames back to back, device time with CUDA events on the
     # library's stream at its two ends only (an event between two frames would end the
     # programmatic overlap of one frame's last kernel with the next frame's first) ----
@@ -473,7 +480,9 @@ def run_vedt(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dims": list(DIMS), "voxel_size_m": VOXEL, "points": N_POINTS,
                        "maps_per_step": 2, "distinct_frames": n_frames, "parallelism": f"replicas x{world}",
-                       "l2": "no flush: each step writes 268 MB of fields plus ~134 MB of scratch, > 126 MB L2"},
+                       "l2": "no flush: each step writes 268 MB of fields plus ~134 MB of scratch, > 126 MB L2",
+                       "bands": tuned_bands,
+                       "bands_sweep_ms_per_10_frames": {str(k): t for k, t in tuned_ms.items()}},
             "latency_ms": {"p50": frame_ms[len(frame_ms) // 2], "p99": frame_ms[min(len(frame_ms) - 1,
                                                                                      int(0.99 * len(frame_ms)))],
                            "max": frame_ms[-1], "what": "device time per frame (events around each frame, "
@@ -652,6 +661,8 @@ def run_paper_sizes(args, v):
     ablation of Tab. 2 (PBA with m3 = 8 against PBA-naive, m = 1) is the same timing at each
     admitted number of bands per line (vedt_map_set_bands)."""
     import torch
+
+    import paper_2407_02363_b300.autotune as at
     from paper_2407_02363_b300 import synth
     out = []
     for dims, paper_occ, paper_ms, paper_cmp_ms in PAPER_SIZES:
@@ -682,14 +693,20 @@ def run_paper_sizes(args, v):
         for nb in ((1, 2, 4, 8) if max(dims) <= 256 else (4, 8)):
             m.set_bands(nb)
             by_bands[str(nb)] = time_edt()
+        # the autotuner's pick for this map size (its own short sweep), then the full timing
+        nb, _ = at.tune_map(m, stream, dims, op=lambda: m.compute_edt(v.MAP_ENV), reps=5, force=True,
+                            kind="edt_env")
+        tuned_ms = time_edt()
         m.set_bands(0)
         out.append({"dims": list(dims), "occupied_voxels": occupied, "edt_ms": ms,
                     "gvoxel_s": n / (ms * 1e-3) / 1e9, "edt_ms_by_bands": by_bands,
+                    "tuned": {"bands": nb, "edt_ms": tuned_ms},
                     "paper": {"occupied_voxels": paper_occ, "pba_ms_stage_table": paper_ms,
                               "pba_ms_edt_table": paper_cmp_ms, "gpu": "GTX 1080 Ti"}})
         m.close()
     return {"what": "exact EDT of one map (environment grid) at the paper's 2 cm map sizes, default "
-                    "bands and each band count; the paper's times are context only", "sizes": out}
+                    "bands, each band count and the autotuner's pick; the paper's times are context only",
+            "sizes": out}
 
 
 def run_batched(args, v, dev):
@@ -729,8 +746,7 @@ def run_batched(args, v, dev):
     b.set_frame(xyz, offs, np.stack(poses), SELF_MASK, cen, radii, m_sph, out)
     b.run()
     b.check()
-    cands = [(0, 0, 32), (1, 0, 8), (1, 0, 32), (1, 0, 128), (1, 4, 32), (1, 8, 32)]
-    best, times = at.tune(b, stream, dims_list, candidates=cands, reps=3, force=True)
+    best, times = at.tune(b, stream, dims_list, reps=3, force=True)   # launch shapes x band counts
     b.capture()
     for _ in range(3):
         b.replay()
@@ -753,8 +769,9 @@ def run_batched(args, v, dev):
             "maps": len(dims_list), "voxels_per_frame": vox, "ms_per_frame": ms,
             "gvoxel_s": vox / (ms * 1e-3) / 1e9, "replays": args.batch_steps,
             "tuning": {"persistent": best.persistent, "ctas_per_sm": best.ctas_per_sm,
-                       "rows_per_item": best.rows_per_item},
-            "edt_ms_by_tuning": {f"{t.persistent}/{t.ctas_per_sm}/{t.rows_per_item}": ms_ for t, ms_ in times.items()}}
+                       "rows_per_item": best.rows_per_item, "bands": best.bands, "edt_ms": times[best]},
+            "edt_ms_by_tuning": {t.label(): ms_ for t, ms_ in times.items()},
+            "tuning_key": "persistent/ctas_per_sm/rows_per_item/bands (0 = three plain launches)"}
 
 
 def run_surrogate(args, v, dev):

@@ -275,6 +275,12 @@ vedt_status vedt_batch_destroy(vedt_batch *batch);
  * Drops a recorded graph. */
 vedt_status vedt_batch_set_tuning(vedt_batch *batch, int ctas_per_sm, int rows_per_item, int persistent);
 
+/* Bands per line of passes Y and Z for the batch's EDT, as vedt_map_set_bands (Alg. 1's
+ * m2 / m3): 0 = the default, 1, 2, 4 or 8 for the grids with every dim <= 256 (the maps
+ * with a larger dim keep 4 / 8 by line length, or take 4 or 8).  Applies to the plain
+ * and the persistent launches.  Drops a recorded graph.  Errors: EINVAL. */
+vedt_status vedt_batch_set_bands(vedt_batch *batch, int bands);
+
 /* PBA_EDT (Alg. 2 line 9) of the selected grids (default both) of every map in the batch. */
 vedt_status vedt_batch_compute_edt(vedt_batch *batch);
 

@@ -1,12 +1,18 @@
-"""Autotuner for the batched EDT launch shapes.
+"""Autotuner for the EDT's band counts and launch shapes.
 
-The exact result never depends on the launch shape, only the time does.  The knobs are
-those of vedt_batch_set_tuning: plain three-sweep launches versus one persistent launch,
-and for the persistent launch the CTAs per SM and the pass-X rows per work item (the
-role the band counts m1, m2, m3 of Alg. 1 play for PBA).  Each candidate is timed with
-CUDA events on the batch's stream over a few repetitions of the EDT (after warm-up), the
-fastest wins, and the winner is cached per (GPU name, grid-dimension signature) in a JSON
-file so later runs skip the sweep.
+The exact result never depends on these knobs, only the time does (the m1 / m2 / m3 bands
+of Alg. 1 are PBA's tunables, Sec. III-C; Tab. 2 compares band settings).
+
+* Single maps and frames (`tune_map`): the bands per line of passes Y and Z
+  (vedt_map_set_bands: 1, 2, 4 or 8 for grids with every dim <= 256; 4 or 8 above).
+* Batches (`tune`): three plain launches (one per sweep) versus one persistent launch
+  over a work queue, the bands per line of either, and for the persistent launch the
+  CTAs per SM and the pass-X rows per work item (vedt_batch_set_tuning / _set_bands).
+
+Each candidate is timed with CUDA events on the workload's stream over a few repetitions
+(after warm-up); the fastest wins.  Winners are cached per (GPU name, grid-dimension
+signature, workload kind) in a JSON file, so later runs, and maps or batches created
+with `apply_cached_map` / `apply_cached`, take them without a sweep.
 """
 from __future__ import annotations
 
@@ -15,10 +21,8 @@ import json
 import os
 from dataclasses import asdict, dataclass
 
-DEFAULT_CANDIDATES = (
-    [(0, 0, 32)] +
-    [(1, c, r) for c in (0, 2, 4, 8) for r in (8, 32, 128)]
-)
+BANDS_SMALL = (1, 2, 4, 8)    # grids with every dim <= 256
+BANDS_LARGE = (4, 8)
 
 
 @dataclass(frozen=True)
@@ -26,9 +30,27 @@ class Tuning:
     persistent: int
     ctas_per_sm: int
     rows_per_item: int
+    bands: int = 0
 
     def apply(self, batch):
         batch.set_tuning(self.ctas_per_sm, self.rows_per_item, self.persistent)
+        batch.set_bands(self.bands)
+
+    def label(self) -> str:
+        return f"{self.persistent}/{self.ctas_per_sm}/{self.rows_per_item}/{self.bands}"
+
+
+def batch_candidates(large=False, bands=None):
+    """Plain launches and persistent shapes, each at every admitted band count."""
+    bs = bands or (BANDS_LARGE if large else BANDS_SMALL)
+    out = []
+    for b in bs:
+        out.append((0, 0, 32, b))
+        out += [(1, c, r, b) for c in (0, 4) for r in (16, 64)]
+    return out
+
+
+DEFAULT_CANDIDATES = batch_candidates()
 
 
 def cache_path() -> str:
@@ -39,11 +61,11 @@ def cache_path() -> str:
     return os.path.join(root, "vedt", "autotune.json")
 
 
-def signature(gpu_name: str, dims_list) -> str:
-    """Cache key: the GPU and the multiset of grid extents in the batch."""
+def signature(gpu_name: str, dims_list, kind: str = "batch") -> str:
+    """Cache key: the GPU, the workload kind and the multiset of grid extents."""
     dims = sorted(tuple(int(v) for v in d) for d in dims_list)
     h = hashlib.sha1(json.dumps(dims).encode()).hexdigest()[:16]
-    return f"{gpu_name}|{len(dims)}|{h}"
+    return f"{gpu_name}|{kind}|{len(dims)}|{h}"
 
 
 def load_cache(path=None) -> dict:
@@ -64,50 +86,107 @@ def store_cache(entries: dict, path=None):
     os.replace(tmp, path)
 
 
-def pick(times: dict) -> Tuning:
+def pick(times: dict):
     """The candidate with the smallest time (ties: earliest in the sweep order)."""
     best = min(times.items(), key=lambda kv: kv[1])
     return best[0]
 
 
-def time_candidate(batch, stream, tuning: Tuning, reps=5, warmup=2, op=None):
-    """Median milliseconds of `op` (default: the batch EDT) under `tuning`."""
+def _time(op, stream, reps, warmup):
     import torch
-    tuning.apply(batch)
-    run = op or batch.compute_edt
     for _ in range(warmup):
-        run()
+        op()
     ts = []
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        run()
+        op()
         b.record(stream)
         b.synchronize()
         ts.append(a.elapsed_time(b))
-    batch.check()
     ts.sort()
     return ts[len(ts) // 2]
 
 
-def tune(batch, stream, dims_list, candidates=DEFAULT_CANDIDATES, reps=5, path=None, force=False, op=None):
-    """Returns (best Tuning, {Tuning: ms}) and applies the best to `batch`.  A cached
-    winner for the same GPU and dims is applied without timing unless force=True."""
+def time_candidate(batch, stream, tuning: Tuning, reps=5, warmup=2, op=None):
+    """Median milliseconds of `op` (default: the batch EDT) under `tuning`."""
+    tuning.apply(batch)
+    ms = _time(op or batch.compute_edt, stream, reps, warmup)
+    batch.check()
+    return ms
+
+
+def _gpu():
     import torch
-    gpu = torch.cuda.get_device_name()
-    key = signature(gpu, dims_list)
+    return torch.cuda.get_device_name()
+
+
+def _as_tuning(c):
+    return c if isinstance(c, Tuning) else Tuning(*c)
+
+
+def tune(batch, stream, dims_list, candidates=None, reps=5, path=None, force=False, op=None, kind="batch"):
+    """Returns (best Tuning, {Tuning: ms}) and applies the best to `batch`.  A cached
+    winner for the same GPU, dims and kind is applied without timing unless force=True."""
+    large = any(max(int(v) for v in d) > 256 for d in dims_list)
+    cands = [_as_tuning(c) for c in (candidates or batch_candidates(large))]
+    key = signature(_gpu(), dims_list, kind)
     cache = load_cache(path)
     if not force and key in cache:
         t = Tuning(**cache[key]["tuning"])
         t.apply(batch)
         return t, {}
-    times = {}
-    for c in candidates:
-        t = Tuning(*c)
-        times[t] = time_candidate(batch, stream, t, reps=reps, op=op)
+    times = {t: time_candidate(batch, stream, t, reps=reps, op=op) for t in cands}
     best = pick(times)
     best.apply(batch)
-    cache[key] = {"tuning": asdict(best), "ms": times[best],
-                  "swept": {f"{t.persistent}/{t.ctas_per_sm}/{t.rows_per_item}": ms for t, ms in times.items()}}
+    cache[key] = {"tuning": asdict(best), "ms": times[best], "swept": {t.label(): ms for t, ms in times.items()}}
     store_cache(cache, path)
     return best, times
+
+
+def apply_cached(batch, dims_list, path=None, kind="batch"):
+    """Applies a cached batch winner if there is one; returns it (or None)."""
+    cache = load_cache(path)
+    e = cache.get(signature(_gpu(), dims_list, kind))
+    if not e:
+        return None
+    t = Tuning(**e["tuning"])
+    t.apply(batch)
+    return t
+
+
+def map_candidates(dims):
+    return BANDS_LARGE if max(int(v) for v in dims) > 256 else BANDS_SMALL
+
+
+def tune_map(m, stream, dims, op=None, candidates=None, reps=5, warmup=2, path=None, force=False, kind="edt"):
+    """Bands per line for one map: times `op` (default: the EDT of both grids) at every
+    candidate band count, applies and caches the fastest.  Returns (bands, {bands: ms})."""
+    import paper_2407_02363_b300.vedt as v
+    run = op or (lambda: m.compute_edt(v.MAP_BOTH))
+    key = signature(_gpu(), [dims], kind)
+    cache = load_cache(path)
+    if not force and key in cache:
+        nb = int(cache[key]["bands"])
+        m.set_bands(nb)
+        return nb, {}
+    times = {}
+    for nb in (candidates or map_candidates(dims)):
+        m.set_bands(nb)
+        times[nb] = _time(run, stream, reps, warmup)
+    m.check()
+    best = pick(times)
+    m.set_bands(best)
+    cache[key] = {"bands": best, "ms": times[best], "swept": {str(k): t for k, t in times.items()}}
+    store_cache(cache, path)
+    return best, times
+
+
+def apply_cached_map(m, dims, path=None, kind="edt"):
+    """Sets a map's bands from the cache (a winner of tune_map for these dims and kind on
+    this GPU); returns the band count or None."""
+    e = load_cache(path).get(signature(_gpu(), [dims], kind))
+    if not e:
+        return None
+    m.set_bands(int(e["bands"]))
+    return int(e["bands"])

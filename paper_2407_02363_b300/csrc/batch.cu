@@ -156,6 +156,7 @@ struct vedt_batch {
     size_t counter_bytes = 0;
     int32_t *err = nullptr;
     int ctas_per_sm = 0, rows_per_item = 32, persistent = 1;
+    int bands = 0;                       // bands per line of passes Y and Z (0: default)
     int which = VEDT_MAP_BOTH;           // grids the EDT covers
     // pipeline
     MapRef *refs = nullptr;
@@ -231,6 +232,7 @@ vedt_status build_tables(vedt_batch *b) {
         off += sizeof(CUtensorMap) * 2 * nd;
         vedt_status st = build_table(b->tab[md], mode[md], desc, tm, b->err);
         if (st != VEDT_OK) return st;
+        b->tab[md].bands = md == 0 ? b->bands : ((b->bands == 4 || b->bands == 8) ? b->bands : 0);
     }
     return VEDT_OK;
 }
@@ -307,6 +309,21 @@ vedt_status vedt_batch_set_tuning(vedt_batch *b, int ctas_per_sm, int rows_per_i
         if (st != VEDT_OK) return st;
     }
     if (b->exec) {   // a recorded graph holds the old launch shapes
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+    }
+    return VEDT_OK;
+}
+
+vedt_status vedt_batch_set_bands(vedt_batch *b, int bands) {
+    if (!b || !(bands == 0 || bands == 1 || bands == 2 || bands == 4 || bands == 8)) return VEDT_EINVAL;
+    BCHECK(cudaStreamSynchronize(b->stream));
+    b->bands = bands;
+    b->tab[0].bands = bands;
+    b->tab[1].bands = (bands == 4 || bands == 8) ? bands : 0;
+    if (b->exec) {   // a recorded graph holds the old launches
         cudaGraphExecDestroy(b->exec);
         cudaGraphDestroy(b->graph);
         b->exec = nullptr;

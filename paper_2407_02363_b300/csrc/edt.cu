@@ -30,6 +30,7 @@
 #include <climits>
 #include <type_traits>
 
+#include "envelope.cuh"
 #include "vedt_internal.h"
 
 namespace vedt {
@@ -1558,6 +1559,101 @@ __global__ void __launch_bounds__(kLanes) k_edt_persistent(const GridDesc *__res
     }
 }
 
+// Persistent EDT for tables whose grids all have dims <= 256, on the stand-alone passes'
+// NB-band tiles (envelope.cuh).  Same in-order queue and bounded waits as above.  The
+// tile area of shared memory is reused from tile to tile: every thread fences its generic
+// accesses of a tile against the async proxy before the CTA barrier that precedes the
+// next tile's TMA load, which writes the same bytes.
+template <int NB>
+__global__ void __launch_bounds__(NB * 32) k_env_persistent(const GridDesc *__restrict__ gd,
+                                                            const CUtensorMap *__restrict__ tm, int ng,
+                                                            PersistCounters cnt, int rows_per_item, int32_t *err) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ uint64_t bar;
+    __shared__ unsigned item_s;
+    __shared__ int ok_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned nX = cnt.n_x, nY = cnt.n_y, total = cnt.n_x + cnt.n_y + cnt.n_z;
+    if (tid == 0) mbar_init(&bar, 1);
+    uint32_t phase = 0;
+    for (;;) {
+        if (tid == 0) item_s = atomicAdd(cnt.next, 1u);
+        __syncthreads();
+        const unsigned it = item_s;
+        __syncthreads();
+        if (it >= total) break;
+        if (it < nX) {
+            int lo = 0, hi = ng - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (static_cast<unsigned>(gd[mid].xi_begin) <= it) lo = mid;
+                else hi = mid - 1;
+            }
+            const GridDesc &G = gd[lo];
+            const int64_t rows = static_cast<int64_t>(G.Y) * G.Z;
+            const int64_t r0 = static_cast<int64_t>(it - G.xi_begin) * rows_per_item;
+            const int64_t r1 = min(rows, r0 + rows_per_item);
+            const bool vec = (G.X & 7) == 0 && (reinterpret_cast<uintptr_t>(G.occ) & 7) == 0;
+            for (int64_t r = r0 + warp; r < r1; r += NB)
+                pass_x_small_row(static_cast<uint8_t *>(G.xs), G.row_has, G.Xp, r, lane,
+                                 row_bytes8(G.occ + r * G.X, G.X, 8 * lane, vec));
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(cnt.done_x + lo, 1u);
+            }
+        } else {
+            const bool is_y = it < nX + nY;
+            const int64_t t = is_y ? it - nX : it - nX - nY;
+            const int g = find_grid(gd, ng, t, is_y ? 0 : 1);
+            const GridDesc &G = gd[g];
+            if (tid == 0) {
+                const unsigned need =
+                    is_y ? static_cast<unsigned>((static_cast<int64_t>(G.Y) * G.Z + rows_per_item - 1) / rows_per_item)
+                         : static_cast<unsigned>(static_cast<int64_t>(G.Xp / kCols) * G.Z);
+                ok_s = wait_count(is_y ? cnt.done_x + g : cnt.done_y + g, need, err);
+                __threadfence();
+                asm volatile("fence.proxy.async.global;" ::: "memory");   // generic writes -> TMA reads
+            }
+            __syncthreads();
+            if (ok_s) {
+                if (is_y) lenv::tile_y<NB, false>(G, &tm[2 * g], static_cast<int>(t - G.ty_begin), smem, &bar, phase, err);
+                else lenv::tile_z<NB, false>(G, &tm[2 * g + 1], static_cast<int>(t - G.tz_begin), smem, &bar, phase, err);
+                phase ^= 1u;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (is_y && tid == 0) {
+                __threadfence();
+                atomicAdd(cnt.done_y + g, 1u);
+            }
+        }
+    }
+}
+
+template <int NB>
+static cudaError_t launch_env_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm,
+                                         int rows_per_item, cudaStream_t s) {
+    const size_t sy = static_cast<size_t>(lenv::Layout<NB, uint8_t>(t.maxY).bytes);
+    const size_t sz = static_cast<size_t>(lenv::Layout<NB, uint16_t>(t.maxZ).bytes);
+    const size_t sm = sy > sz ? sy : sz;
+    cudaError_t e = ensure_dyn_smem<k_env_persistent<NB>>(sm);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_env_persistent<NB>, NB * 32, sm);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int per_sm = ctas_per_sm > 0 && ctas_per_sm < occ ? ctas_per_sm : occ;
+    const int64_t total = static_cast<int64_t>(c.n_x) + c.n_y + c.n_z;
+    int64_t blocks = static_cast<int64_t>(sm_count()) * per_sm;
+    if (blocks > total) blocks = total;
+    if (blocks < 1) return cudaSuccess;
+    // a plain launch: the queue's first items read the occupancy the previous kernels wrote
+    k_env_persistent<NB><<<static_cast<unsigned>(blocks), NB * 32, sm, s>>>(t.desc, t.tmaps, t.n, c, rows_per_item,
+                                                                           t.err);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------
@@ -1640,7 +1736,14 @@ static cudaError_t launch_persistent_impl(const GridTable &t, const PersistCount
 
 cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm, int rows_per_item,
                               cudaStream_t s) {
-    if (!t.large) return launch_persistent_impl<8, true>(t, c, ctas_per_sm, rows_per_item, s);
+    if (!t.large) {
+        switch (t.bands) {
+            case 1: return launch_env_persistent<1>(t, c, ctas_per_sm, rows_per_item, s);
+            case 2: return launch_env_persistent<2>(t, c, ctas_per_sm, rows_per_item, s);
+            case 8: return launch_env_persistent<8>(t, c, ctas_per_sm, rows_per_item, s);
+            default: return launch_env_persistent<4>(t, c, ctas_per_sm, rows_per_item, s);
+        }
+    }
     if (t.maxXp <= 256) return launch_persistent_impl<8, false>(t, c, ctas_per_sm, rows_per_item, s);
     if (t.maxXp <= 512) return launch_persistent_impl<16, false>(t, c, ctas_per_sm, rows_per_item, s);
     return launch_persistent_impl<32, false>(t, c, ctas_per_sm, rows_per_item, s);

@@ -1,0 +1,575 @@
+// Device code of passes Y and Z of the exact EDT (Sec. III-C, Alg. 1 Steps 2-4) for grids
+// whose every dimension is at most 256; the stand-alone kernels are in envelope.cu, the
+// persistent batch kernel in edt.cu.
+//
+// A tile is 32 adjacent columns of one line family (pass Y: columns (x, z) along y of
+// slice z; pass Z: columns (x, y) along z of row y) over the whole line, one lane per
+// column, NB warps per tile (the m2 / m3 banding of Alg. 1): warp b owns band b, the
+// positions [b * bl, (b + 1) * bl) of every line, bl = ceil(n / NB).  Every global access
+// is coalesced across x.  The line tile is staged into shared memory by one TMA box load
+// (no multicast).
+//
+//   build   every warp sweeps the valid positions of its band (rows / slices that hold a
+//           site: the same for all 32 columns, so the sweep is warp-uniform) and keeps the
+//           band's stack of proximate sites in place: entry t's input word moves to slot
+//           lo + t of the tile (a slot the sweep has read already) and its position to the
+//           byte array `pos`.  With h(p) = f(p) + p^2, site b (between a and c) is popped
+//           when c overtakes b no later than b overtakes a:
+//               (h_c - h_b)(b - a) <= (h_b - h_a)(c - b)            (ComputeProximateSite)
+//   merge   warp 0 joins the bands' stacks of each column left to right (PBA's merge of the
+//           band envelopes): the top T of the joined prefix is dropped while the entry S
+//           below it and the next band's first entry F dominate it, and F while T and the
+//           entry G above F dominate it.  Both stacks are lower convex hulls of the points
+//           (2p, h_p), so this alternation stops at their bridge.  The kept range of every
+//           band is published through shared memory.
+//   query   every warp walks the joined envelope over its own band (QueryNearestSite):
+//           it finds the entry nearest to the band's first voxel (the values at a fixed
+//           voxel are unimodal along the envelope), then advances one voxel at a time;
+//           the next entry q+1 is strictly nearer to voxel j than entry q iff
+//               h_(q+1) - h_q < 2 j (p_(q+1) - p_q),
+//           whose right side grows by a constant per voxel (ties keep the lower site).
+//
+// Pass Z's in-plane distance g = (x - x')^2 + (y - y')^2 of a packed site x' | y' << 8 is
+// K + (x'^2 + y'^2) - 2 (x x' + y y') with K = x^2 + y^2: two byte dot products.
+#pragma once
+#include <climits>
+
+#include "vedt_internal.h"
+
+namespace vedt {
+namespace lenv {
+
+constexpr int kC = 32;   // columns per tile (lanes)
+
+__device__ __forceinline__ int find_tile_grid(const GridDesc *__restrict__ gd, int ng, int64_t t, bool z) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((z ? gd[mid].tz_begin : gd[mid].ty_begin) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Pass Y: input word = the row's nearest site x' (pass X); f(p) = (x - x')^2.
+struct PolY {
+    using In = uint8_t;
+    int x;
+    __device__ __forceinline__ int g(uint32_t r) const {
+        const int d = x - static_cast<int>(r);
+        return d * d;
+    }
+    __device__ __forceinline__ int h(uint32_t r, int p) const { return g(r) + p * p; }
+};
+
+// Pass Z: input word = the slice's nearest 2-D site x' | y' << 8 (pass Y);
+// f(p) = (x - x')^2 + (y - y')^2 = K + dp(r, r) - 2 dp(r, x | y << 8).
+struct PolZ {
+    using In = uint16_t;
+    uint32_t xy8;
+    int K;
+    __device__ __forceinline__ int g(uint32_t r) const {
+        return static_cast<int>(__dp4a(r, r, static_cast<unsigned>(K))) - 2 * static_cast<int>(__dp4a(r, xy8, 0u));
+    }
+    __device__ __forceinline__ int h(uint32_t r, int p) const {
+        return static_cast<int>(__dp4a(r, r, static_cast<unsigned>(K + p * p))) -
+               2 * static_cast<int>(__dp4a(r, xy8, 0u));
+    }
+};
+
+// b (between a and c) is dropped: c overtakes b no later than b overtakes a.
+__device__ __forceinline__ bool dominated(int ca, int ha, int cb, int hb, int cc, int hc) {
+    return (hc - hb) * (cb - ca) <= (hb - ha) * (cc - cb);
+}
+
+template <int NB>
+struct Geo {
+    static constexpr int kWords = (256 / NB + 31) / 32;   // valid-mask words per band
+    static __host__ __device__ constexpr int len(int n) { return (n + NB - 1) / NB; }
+};
+
+// Shared memory of one tile of n positions: the staged line tile [n][32], the stack
+// positions [NB * bl][32] (bytes) and the published kept ranges (j, then i + 1, NB x 32
+// bytes each).  The TMA barrier lives in the first 8 bytes of the j ranges, which are
+// written only after every thread has passed its wait and the barrier is invalidated.
+// A 256-long pass-Z tile with four bands takes 24,832 bytes (nine CTAs per SM), a pass-Y
+// tile 16,640 (thirteen).
+template <int NB, class In>
+struct Layout {
+    int pos_off, rng_off, bar_off, bytes;
+    __host__ __device__ Layout(int n) {
+        const int in_b = n * kC * static_cast<int>(sizeof(In));
+        pos_off = (in_b + 15) & ~15;
+        rng_off = pos_off + ((Geo<NB>::len(n) * NB * kC + 15) & ~15);
+        bar_off = rng_off;
+        bytes = rng_off + 2 * NB * kC;
+    }
+};
+
+// valid-position bitmask of band [lo, hi) from per-position byte flags (warp-uniform)
+template <int W>
+__device__ __forceinline__ void band_mask(const uint8_t *__restrict__ flags, int lo, int hi, int lane,
+                                          uint32_t (&vm)[W]) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int q = lo + 32 * w + lane;
+        vm[w] = __ballot_sync(0xffffffffu, q < hi && flags[q] != 0);
+    }
+}
+
+// Stack of proximate sites of one band over its valid positions lo + 32 w + (bit of
+// vm[w]), ascending; entry t ends in slot lo + t (input word in col, position in cp).
+//
+// The two top entries a (below) and b stay in registers.  While the stack holds fewer
+// than two entries, a is a sentinel that nothing dominates against (position b - 1,
+// h_b + 2^20: the right side of the test is then below -2^20, the left side above
+// -2^19), so the pop test needs no size check; a pop reloads a from the slot two below
+// the top, clamped to the band's first slot, and replaces it by the sentinel when the
+// stack has become too small.
+template <int W, class P>
+__device__ __forceinline__ int build(const P &pol, typename P::In *col, uint8_t *cp, int lo, const uint32_t (&vm)[W],
+                                     int cap, int32_t *err) {
+    constexpr int kBig = 1 << 20;
+    typename P::In *const in0 = col + lo * kC;   // the band's first slot
+    uint8_t *const ps0 = cp + lo * kC;
+    // before the first push: a fake b at position -1 with h = 0 and a sentinel a below it,
+    // so that no candidate (position >= 0, h >= 0) can pop it
+    int k = 0, cb = -1, hb = 0, ca = -2, ha = kBig;
+    auto step = [&](int c) {
+        const uint32_t r = col[c * kC];
+        const int hc = pol.h(r, c);
+        while (dominated(ca, ha, cb, hb, c, hc)) {
+            --k;
+            cb = ca;
+            hb = ha;
+            const int s = max(k - 2, 0) * kC;
+            const int c2 = ps0[s];
+            const int h2 = pol.h(in0[s], c2);
+            const bool real = k >= 2;
+            ca = real ? c2 : cb - 1;
+            ha = real ? h2 : hb + kBig;
+        }
+        if (in_range(k, cap, err)) {   // debug builds: the stack never outgrows its band
+            in0[k * kC] = static_cast<typename P::In>(r);
+            ps0[k * kC] = static_cast<uint8_t>(c);
+        }
+        const bool first = k == 0;
+        ca = first ? c - 1 : cb;
+        ha = first ? hc + kBig : hb;
+        cb = c;
+        hb = hc;
+        ++k;
+    };
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        uint32_t bits = vm[w];
+        const int base = lo + 32 * w;
+        if (bits == 0xFFFFFFFFu) {   // 32 valid positions in a row (warp-uniform)
+#pragma unroll 4
+            for (int c = base; c < base + 32; ++c) step(c);
+        } else {
+            while (bits) {
+                const int c = base + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                step(c);
+            }
+        }
+    }
+    return k;
+}
+
+// a[b] for a band index known only at run time (selects, no local memory)
+template <int NB>
+__device__ __forceinline__ int pick(const int (&a)[NB], int b) {
+    int v = a[0];
+#pragma unroll
+    for (int u = 1; u < NB; ++u)
+        if (b == u) v = a[u];
+    return v;
+}
+
+// The joined envelope of one column: band b keeps its stack entries j[b] .. i[b] (none if
+// j[b] > i[b]); the envelope is their concatenation in band order.
+template <int NB, class P>
+struct Joined {
+    const typename P::In *col;   // this column's slots (stride kC)
+    const uint8_t *cp;
+    int bl;
+    int j[NB], i[NB];
+    int32_t *err;
+    __device__ __forceinline__ void at(int s, int &c, uint32_t &r) const {
+        if (!in_range(s, NB * bl, err)) {
+            c = 0;
+            r = 0;
+            return;
+        }
+        r = col[s * kC];
+        c = cp[s * kC];
+    }
+    __device__ __forceinline__ bool nonempty(int b) const { return pick<NB>(j, b) <= pick<NB>(i, b); }
+    // largest non-empty band below b, or -1
+    __device__ __forceinline__ int prev_band(int b) const {
+        int s = -1;
+#pragma unroll
+        for (int u = 0; u < NB; ++u)
+            if (u < b && j[u] <= i[u]) s = u;
+        return s;
+    }
+    // smallest non-empty band above b, or -1
+    __device__ __forceinline__ int next_band(int b) const {
+        int s = -1;
+#pragma unroll
+        for (int u = NB - 1; u >= 0; --u)
+            if (u > b && j[u] <= i[u]) s = u;
+        return s;
+    }
+    // PBA-style merge of the band stacks of sizes k[b] (see the file comment)
+    __device__ __forceinline__ void merge(const P &pol, const int (&k)[NB]) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            j[b] = 0;
+            i[b] = k[b] - 1;
+        }
+        int tb = -1;   // top band of the joined prefix
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (k[b] == 0) continue;
+            if (tb >= 0) {
+                int jb = 0;
+                const int ib = k[b] - 1;
+                for (;;) {
+                    const int ti = pick<NB>(i, tb);
+                    int sb = tb, si = ti - 1;   // entry below the top
+                    if (si < pick<NB>(j, tb)) {
+                        sb = prev_band(tb);
+                        si = sb >= 0 ? pick<NB>(i, sb) : 0;
+                    }
+                    int cT, cF;
+                    uint32_t rT, rF;
+                    at(tb * bl + ti, cT, rT);
+                    at(b * bl + jb, cF, rF);
+                    const int hT = pol.h(rT, cT), hF = pol.h(rF, cF);
+                    if (sb >= 0) {
+                        int cS;
+                        uint32_t rS;
+                        at(sb * bl + si, cS, rS);
+                        if (dominated(cS, pol.h(rS, cS), cT, hT, cF, hF)) {
+#pragma unroll
+                            for (int u = 0; u < NB; ++u)
+                                if (u == tb) i[u] = ti - 1;
+                            if (ti - 1 < pick<NB>(j, tb)) tb = sb;
+                            continue;
+                        }
+                    }
+                    if (jb < ib) {
+                        int cG;
+                        uint32_t rG;
+                        at(b * bl + jb + 1, cG, rG);
+                        if (dominated(cT, hT, cF, hF, cG, pol.h(rG, cG))) {
+                            ++jb;
+                            continue;
+                        }
+                    }
+                    break;
+                }
+#pragma unroll
+                for (int u = 0; u < NB; ++u)
+                    if (u == b) j[u] = jb;
+            }
+            tb = b;
+        }
+    }
+    // The entry of the joined envelope nearest to voxel lo, starting from band `band`'s
+    // first kept entry (or the next non-empty band's, else the last entry): steps down
+    // while the entry below is no farther.  Returns its slot and band; c, r, hq its
+    // position, input word and h.
+    __device__ __forceinline__ void start(const P &pol, int band, int lo, int &s, int &sb, int &c, uint32_t &r,
+                                          int &hq) const {
+        int b = nonempty(band) ? band : next_band(band);
+        if (b < 0) {
+            b = prev_band(band);
+            s = b * bl + pick<NB>(i, b);
+        } else {
+            s = b * bl + pick<NB>(j, b);
+        }
+        at(s, c, r);
+        hq = pol.h(r, c);
+        for (;;) {
+            int pb = b, ps = s - 1;
+            if (ps < b * bl + pick<NB>(j, b)) {
+                pb = prev_band(b);
+                if (pb < 0) break;
+                ps = pb * bl + pick<NB>(i, pb);
+            }
+            int c2;
+            uint32_t r2;
+            at(ps, c2, r2);
+            const int h2 = pol.h(r2, c2);
+            if (h2 - 2 * lo * c2 > hq - 2 * lo * c) break;
+            b = pb;
+            s = ps;
+            c = c2;
+            r = r2;
+            hq = h2;
+        }
+        sb = b;
+    }
+    // next slot after s (in band sb) along the envelope; false at its end
+    __device__ __forceinline__ bool next(int &s, int &sb, int &se) const {
+        if (s < se) {
+            ++s;
+            return true;
+        }
+        const int nb = next_band(sb);
+        if (nb < 0) return false;
+        sb = nb;
+        s = nb * bl + pick<NB>(j, nb);
+        se = nb * bl + pick<NB>(i, nb);
+        return true;
+    }
+};
+
+// Line tile staging: one TMA box of n positions x 32 columns.
+template <class In>
+__device__ __forceinline__ void load_tile(In *in, const CUtensorMap *map, int n, int x0, int c1, bool along_y,
+                                          uint64_t *bar) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(n * kC * sizeof(In)));
+    if (along_y) tma_load_3d(in, map, x0, 0, c1, bar);
+    else tma_load_3d(in, map, x0, c1, 0, bar);
+}
+
+__device__ __forceinline__ void drain_after_timeout(uint64_t *bar, uint32_t phase) {
+    for (uint32_t i = 0; i < (1u << 20); ++i)
+        if (mbar_try_wait(bar, phase)) return;
+}
+
+// Builds the bands, merges (warp 0) and publishes the kept ranges of a staged tile.
+// Returns false when no position of the line is valid (the same for every column).
+// kOwnBar: the TMA barrier lives in the first bytes of the range area (stand-alone
+// kernels, one tile per CTA) and is invalidated before the ranges overwrite it; else it
+// is a separate barrier that the caller reuses with alternating phases.
+template <int NB, bool kOwnBar, class P>
+__device__ __forceinline__ bool envelope(const P &pol, typename P::In *in, uint8_t *pos, uint8_t *rng,
+                                         const uint8_t *__restrict__ flags, int n, Joined<NB, P> &J, int &lo, int &hi,
+                                         uint64_t *bar, uint32_t phase, int32_t *err, bool &ok) {
+    const int tid = threadIdx.x, lane = tid & 31, band = tid >> 5;
+    const int bl = Geo<NB>::len(n);
+    lo = band * bl;
+    hi = min(n, lo + bl);
+    uint32_t vm[Geo<NB>::kWords];
+    band_mask(flags, lo, hi, lane, vm);
+    ok = mbar_wait_bounded(bar, phase, err);
+    if (!ok) {
+        drain_after_timeout(bar, phase);
+        (void)__syncthreads_or(0);
+        return false;
+    }
+    const int k = build(pol, in + lane, pos + lane, lo, vm, bl, err);
+    J.col = in + lane;
+    J.cp = pos + lane;
+    J.bl = bl;
+    J.err = err;
+    if constexpr (NB == 1) {
+        J.j[0] = 0;
+        J.i[0] = k - 1;
+        return __syncthreads_or(k) != 0;
+    } else {
+        uint8_t *rj = rng, *ri = rng + NB * kC;   // first kept entry; stack size, then last kept + 1
+        ri[tid] = static_cast<uint8_t>(k);         // (ri starts at byte 64 or later, past the barrier)
+        if (!__syncthreads_or(k)) return false;
+        if (band == 0) {
+            if constexpr (kOwnBar) {
+                if (tid == 0) mbar_inval(bar);   // every thread has passed its wait; rj overwrites it
+                __syncwarp();
+            }
+            int kk[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) kk[b] = ri[b * kC + lane];
+            J.merge(pol, kk);
+            __syncwarp();   // every lane of warp 0 has read the sizes before they are overwritten
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                rj[b * kC + lane] = static_cast<uint8_t>(J.j[b]);
+                ri[b * kC + lane] = static_cast<uint8_t>(J.i[b] + 1);
+            }
+        }
+        __syncthreads();
+        if (band != 0) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                J.j[b] = rj[b * kC + lane];
+                J.i[b] = static_cast<int>(ri[b * kC + lane]) - 1;
+            }
+        }
+        return true;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// pass Y: tile = (grid, slice z, columns x0 .. x0 + 31), line along y; writes the 2-D
+// site x' | y' << 8 of every voxel and the slice's flag
+// ------------------------------------------------------------------------------------
+// One pass-Y tile (grid g, tile lt of that grid) with NB warps, staged into `smem` (layout
+// Layout<NB, uint8_t>(Y)) through `bar` (current parity `phase`).  Returns false if the
+// staging wait timed out (flagged in err).
+template <int NB, bool kOwnBar>
+__device__ __forceinline__ bool tile_y(const GridDesc &G, const CUtensorMap *tmap, int lt, uint8_t *smem,
+                                       uint64_t *bar, uint32_t phase, int32_t *err) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int Y = G.Y, Xp = G.Xp;
+    const int tiles_x = Xp / kC;
+    const int z = lt / tiles_x, x0 = (lt % tiles_x) * kC;
+    const Layout<NB, uint8_t> L(Y);
+    uint8_t *in = smem;
+    uint8_t *pos = smem + L.pos_off;
+    uint8_t *rng = smem + L.rng_off;
+    if (tid == 0) load_tile(in, tmap, Y, x0, z, true, bar);
+    const PolY pol{x0 + lane};
+    Joined<NB, PolY> J;
+    int lo, hi;
+    bool ok;
+    const bool any = envelope<NB, kOwnBar>(pol, in, pos, rng, G.row_has + static_cast<int64_t>(z) * Y, Y, J, lo, hi, bar,
+                                                   phase, err, ok);
+    if (!ok) return false;
+    if (x0 == 0 && tid == 0) G.slice_has[z] = any ? 1 : 0;
+    if (!any || lo >= hi) return true;   // an empty slice writes nothing: pass Z skips it
+    int s, sb, c0;
+    uint32_t r0;
+    int h0;
+    J.start(pol, tid >> 5, lo, s, sb, c0, r0, h0);
+    int se = sb * J.bl + pick<NB>(J.i, sb);
+    // next entry: dh = h1 - h0, dc2 = 2 (c1 - c0); no next entry: dh = INT_MAX
+    int c1 = 0, h1 = 0, dh = INT_MAX, dc2 = 0;
+    uint32_t r1 = 0;
+    auto fetch = [&]() {
+        if (J.next(s, sb, se)) {
+            J.at(s, c1, r1);
+            h1 = pol.h(r1, c1);
+            dh = h1 - h0;
+            dc2 = 2 * (c1 - c0);
+        } else {
+            dh = INT_MAX;
+            dc2 = 0;
+        }
+    };
+    fetch();
+    int thr = lo * dc2;
+    uint16_t site = static_cast<uint16_t>(r0 | (static_cast<uint32_t>(c0) << 8));
+    uint16_t *out = static_cast<uint16_t *>(G.s2);
+    uint32_t off = static_cast<uint32_t>((z * Y + lo) * Xp + x0 + lane);
+    const uint32_t lim = static_cast<uint32_t>(Xp * Y * G.Z);
+    for (int jv = lo; jv < hi; ++jv) {
+        if (dh < thr) {
+            do {
+                c0 = c1;
+                r0 = r1;
+                h0 = h1;
+                fetch();
+                thr = jv * dc2;
+            } while (dh < thr);
+            site = static_cast<uint16_t>(r0 | (static_cast<uint32_t>(c0) << 8));
+        }
+        if (in_range(off, lim, err)) out[off] = site;
+        off += Xp;
+        thr += dc2;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------------------------
+// pass Z: tile = (grid, row y, columns x0 .. x0 + 31), line along z; writes sqdist and
+// the nearest voxel's linear index
+// ------------------------------------------------------------------------------------
+// One pass-Z tile (grid g, tile lt of that grid), as tile_y (layout Layout<NB, uint16_t>(Z)).
+template <int NB, bool kOwnBar>
+__device__ __forceinline__ bool tile_z(const GridDesc &G, const CUtensorMap *tmap, int lt, uint8_t *smem,
+                                       uint64_t *bar, uint32_t phase, int32_t *err) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int X = G.X, Y = G.Y, Z = G.Z, Xp = G.Xp;
+    const int tiles_x = Xp / kC;
+    const int y = lt / tiles_x, x0 = (lt % tiles_x) * kC;
+    const Layout<NB, uint16_t> L(Z);
+    uint16_t *in = reinterpret_cast<uint16_t *>(smem);
+    uint8_t *pos = smem + L.pos_off;
+    uint8_t *rng = smem + L.rng_off;
+    if (tid == 0) load_tile(in, tmap, Z, x0, y, false, bar);
+    const int x = x0 + lane;
+    const PolZ pol{static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 8), x * x + y * y};
+    Joined<NB, PolZ> J;
+    int lo, hi;
+    bool ok;
+    const bool any = envelope<NB, kOwnBar>(pol, in, pos, rng, G.slice_has, Z, J, lo, hi, bar, phase, err, ok);
+    if (!ok) return false;
+    const bool live = x < X;
+    const uint32_t plane = static_cast<uint32_t>(X * Y);
+    uint32_t off = static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(y * X + (live ? x : 0));
+    const uint32_t lim = plane * static_cast<uint32_t>(Z);
+    int32_t *sq = G.sqdist, *ix = G.idx;
+    if (!any) {   // empty grid
+        for (int jv = lo; jv < hi; ++jv) {
+            if (live && in_range(off, lim, err)) {
+                sq[off] = INT_MAX;
+                ix[off] = -1;
+            }
+            off += plane;
+        }
+        return true;
+    }
+    if (lo >= hi) return true;
+    const uint32_t coef = 1u | (static_cast<uint32_t>(X) << 16);   // x' + X y' as a 2-way dot product
+    const int XY = X * Y;
+    int s, sb, c0;
+    uint32_t r0;
+    int h0;
+    J.start(pol, tid >> 5, lo, s, sb, c0, r0, h0);
+    int se = sb * J.bl + pick<NB>(J.i, sb);
+    int c1 = 0, h1 = 0, dh = INT_MAX, dc2 = 0;
+    uint32_t r1 = 0;
+    auto fetch = [&]() {
+        if (J.next(s, sb, se)) {
+            J.at(s, c1, r1);
+            h1 = pol.h(r1, c1);
+            dh = h1 - h0;
+            dc2 = 2 * (c1 - c0);
+        } else {
+            dh = INT_MAX;
+            dc2 = 0;
+        }
+    };
+    fetch();
+    int thr = lo * dc2;
+    // value at voxel jv of entry c0: v = g0 + (jv - c0)^2, kept incrementally
+    int d = lo - c0;
+    int v = h0 - c0 * c0 + d * d;
+    int inc = 2 * d + 1;
+    int id = static_cast<int>(__dp2a_lo(coef, r0, static_cast<unsigned>(XY * c0)));
+    for (int jv = lo; jv < hi; ++jv) {
+        if (dh < thr) {
+            do {
+                c0 = c1;
+                r0 = r1;
+                h0 = h1;
+                fetch();
+                thr = jv * dc2;
+            } while (dh < thr);
+            d = jv - c0;
+            v = h0 - c0 * c0 + d * d;
+            inc = 2 * d + 1;
+            id = static_cast<int>(__dp2a_lo(coef, r0, static_cast<unsigned>(XY * c0)));
+        }
+        if (live && in_range(off, lim, err)) {
+            sq[off] = v;
+            ix[off] = id;
+        }
+        off += plane;
+        v += inc;
+        inc += 2;
+        thr += dc2;
+    }
+    return true;
+}
+
+}  // namespace lenv
+}  // namespace vedt

@@ -82,6 +82,7 @@ _sig = {
     "vedt_batch_create": [_P, _I32, _P, _P],
     "vedt_batch_destroy": [_P],
     "vedt_batch_set_tuning": [_P, _I32, _I32, _I32],
+    "vedt_batch_set_bands": [_P, _I32],
     "vedt_batch_compute_edt": [_P],
     "vedt_batch_register_links": [_P, _I32, _P, _P],
     "vedt_batch_set_frame": [_P, _P, _P, _P, _U32, _P, _P, _I32, _P],
@@ -520,6 +521,9 @@ class Batch:
     def set_tuning(self, ctas_per_sm=0, rows_per_item=32, persistent=True):
         _chk(_lib.vedt_batch_set_tuning(self._h, int(ctas_per_sm), int(rows_per_item), 1 if persistent else 0),
              "vedt_batch_set_tuning")
+
+    def set_bands(self, bands=0):
+        _chk(_lib.vedt_batch_set_bands(self._h, int(bands)), "vedt_batch_set_bands")
 
     def compute_edt(self):
         _chk(_lib.vedt_batch_compute_edt(self._h), "vedt_batch_compute_edt")
