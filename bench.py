@@ -93,7 +93,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch-steps", type=int, default=50, help="graph replays timed for the 64-map batch (0: skip)")
     p.add_argument("--sur-train", type=int, default=2 * 1024 * 1024, help="surrogate training configurations (0: skip)")
-    p.add_argument("--sur-steps", type=int, default=20000, help="surrogate AdamW steps (batch 8192)")
+    p.add_argument("--sur-steps", type=int, default=40000, help="surrogate AdamW steps (batch 8192)")
     p.add_argument("--serve-frames", type=int, default=80, help="frames per arrival rate in the serving leg (0: skip)")
     p.add_argument("--paper-reps", type=int, default=50, help="EDT launches per map size in the paper-sizes leg (0: skip)")
     p.add_argument("--loop-frames", type=int, default=150,
@@ -820,10 +820,15 @@ def run_surrogate(args, v, dev):
     flops = 2.0 * 65536 * sum(i * o for i, o in zip(omlp.SIZES[:-1], omlp.SIZES[1:]))
     lab.close()
     net.close()
+    near_rate = float((np.where(valid, d_te, np.inf) < 0.05).any(axis=1).mean())
     return {"workload": "surrogate: MLP 14 -> 4x256 -> 24 (BF16, fp32 accumulate, tcgen05), trained on "
                         f"{args.sur_train} uniform joint configs labelled by the exact 128^3 / 2 cm self-map EDT "
-                        f"({args.sur_steps} AdamW steps of 8192); inference batch 65536; distances clipped at "
-                        f"{sg.DIST_CLIP} m",
+                        f"({args.sur_steps} AdamW steps of 8192, cosine learning rate from 2e-3, loss weighted "
+                        f"1 + 3 exp(-d / 5 cm)); inference batch 65536; distances clipped at {sg.DIST_CLIP} m",
+            "true_near_5cm_rate": near_rate,
+            "gain_ceiling": 1.0 / max(near_rate, 1e-9),
+            "gain_ceiling_what": "configurations with an exact distance under 5 cm must fall back under any "
+                                 "safe margin, so the hybrid gain over exact is at most 1 / that rate",
             "train_seconds": t_fit, "final_train_loss": hist[-1][1] if hist else None,
             "test": {"max_err_mm": r_plain.max_err_mm, "p99_err_mm": r_plain.p99_err_mm,
                      "mean_err_mm": r_plain.mean_err_mm, "n": r_plain.n},

@@ -173,10 +173,19 @@ def cached_labels(lab, q, path):
     return d, s
 
 
-def fit(lab, net, n_train, n_val, seed, steps, batch=8192, lr=3e-3, log_every=0):
+def near_weights(y, near_weight=3.0, scale=0.05):
+    """Per-entry loss weights: 1 + near_weight exp(-y / scale), so errors on distances
+    that decide a fallback (a few cm) count up to 1 + near_weight times more.  The
+    kernels' masked loss takes the weight as its mask: the gradient is that of the
+    weighted mean squared error."""
+    return 1.0 + near_weight * np.exp(-np.asarray(y) / scale)
+
+
+def fit(lab, net, n_train, n_val, seed, steps, batch=8192, lr=2e-3, near_weight=3.0, log_every=0):
     """Labels n_train + n_val seeded configurations on the exact path, trains `net` on
-    the clipped valid distances and returns (history, validation EvalResult, the safety
-    margin = 5 cm + validation max error, label throughput in configurations/s)."""
+    the clipped valid distances (weighted toward small distances, `near_weights`) and
+    returns (history, validation EvalResult, the safety margin = 5 cm + validation max
+    error, label throughput in configurations/s)."""
     import torch
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
     q_tr = synth.joint_states(seed, n_train)
@@ -184,8 +193,9 @@ def fit(lab, net, n_train, n_val, seed, steps, batch=8192, lr=3e-3, log_every=0)
     d_tr, s_tr = lab(q_tr)
     label_qps = n_train / (time.perf_counter() - t0)
     m_tr = lab.valid_mask(s_tr)
-    hist = train(net, dev(q_tr), dev(np.where(m_tr, clip(d_tr), 0)), dev(m_tr), steps=steps, batch=batch, lr=lr,
-                 log_every=log_every)
+    y_tr = np.where(m_tr, clip(d_tr), 0)
+    w_tr = np.where(m_tr, near_weights(y_tr, near_weight), 0.0)
+    hist = train(net, dev(q_tr), dev(y_tr), dev(w_tr), steps=steps, batch=batch, lr=lr, log_every=log_every)
     q_va = synth.joint_states(seed + 1, n_val)
     d_va, s_va = lab(q_va)
     r_va = evaluate(clip(predict(net, dev(q_va)).cpu().numpy()), clip(d_va), lab.valid_mask(s_va))

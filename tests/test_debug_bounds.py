@@ -1,5 +1,5 @@
-"""The bounds-checked debug build (libvedt_debug.so, -DVEDT_DEBUG_BOUNDS): the EDT parity
-tests and the batched-EDT tests run again in a child process that loads it.  Every index
+"""The bounds-checked debug build (libvedt_debug.so, -DVEDT_DEBUG_BOUNDS): the EDT parity,
+batched-EDT, incremental and band-junction tests run again in a child process that loads it.  Every index
 the EDT passes compute is checked against its buffer there; an out-of-range one would set
 the error word, which every test reads through vedt_check, so the run passing shows that
 no pass computed a bad index on these inputs (and the fields still match the oracle)."""
@@ -25,6 +25,6 @@ def test_parity_suites_pass_on_the_index_checked_build():
     assert "index checks" in probe.stdout
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-p", "no:cacheprovider",
                         os.path.join(HERE, "test_parity_edt.py"), os.path.join(HERE, "test_batch.py"),
-                        os.path.join(HERE, "test_incremental.py")],
+                        os.path.join(HERE, "test_incremental.py"), os.path.join(HERE, "test_junctions.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
     assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
