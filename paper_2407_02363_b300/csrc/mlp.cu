@@ -359,6 +359,16 @@ __host__ __device__ constexpr int layer_chunk_begin(int l) {
 }
 static_assert(wchunk(kNumWChunks - 1).off + kOutPad * kHidden * 2 == kWImageBytes, "weight image size");
 
+// The order a CTA consumes a tile pair's chunks in: a hidden layer's four K chunks start
+// at chunk `rot` of the layer (CTA index mod 4; the accumulation order does not matter to
+// the result beyond fp32 rounding), so at any time the CTAs read four different chunks and
+// the L2 lines of one chunk are not requested by every SM at once.
+__host__ __device__ constexpr int chunk_order(int p, int rot) {
+    return (p == 0 || p == kNumWChunks - 1)
+               ? p
+               : 1 + ((p - 1) / kChunksPerHidden) * kChunksPerHidden + ((p - 1) % kChunksPerHidden + rot) % kChunksPerHidden;
+}
+
 // packs the bf16 weights W_l [N_l][K_l] into the chunk images
 __global__ void k_pack_w(const bf16 *w0, const bf16 *w1, const bf16 *w2, const bf16 *w3, const bf16 *w4,
                          uint8_t *__restrict__ img) {
@@ -474,6 +484,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     __shared__ uint32_t tmem_base;
     uint8_t *stage = smem + 2 * kActBytes;    // activation tile of slot s at smem + s * kActBytes
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rot = static_cast<int>(blockIdx.x) % kChunksPerHidden;   // see chunk_order
     const int n_tiles = (B + 127) / 128;
     const int T = static_cast<int>(blockIdx.x) < n_tiles ? (n_tiles - 1 - static_cast<int>(blockIdx.x)) / gridDim.x + 1 : 0;
     const int pairs = (T + 1) / 2;
@@ -506,7 +517,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         for (; it < total && ok; ++it) {
             const uint32_t k = it % kStages;
             if (it >= kStages && !(ok = mbar_wait_bounded(&empty[k], ((it / kStages) - 1) & 1, err))) break;
-            const WChunk ch = wchunk(static_cast<int>(it % kNumWChunks));
+            const WChunk ch = wchunk(chunk_order(static_cast<int>(it % kNumWChunks), rot));
             const uint32_t bytes = static_cast<uint32_t>(ch.n * ch.kc * 2);
             mbar_arrive_expect_tx(&full[k], bytes);
             bulk_load(stage + k * kStageBytes, a.wimg + ch.off, bytes, &full[k]);
@@ -560,9 +571,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     for (int c = 0; c < kChunksPerHidden; ++c) {
                         if (!wait_full()) break;
                         const uint64_t b0 = b_h + k * kStageStep;
+                        const int cr = (c + rot) % kChunksPerHidden;   // the K chunk this stage holds
                         for (int s = 0; s < ns; ++s) {
                             if (c == 0 && !wait_ready(s)) break;
-                            const uint64_t a0 = a_h + s * kSlotStep + static_cast<uint64_t>(c * (kWKC / 16) * 16);
+                            const uint64_t a0 = a_h + s * kSlotStep + static_cast<uint64_t>(cr * (kWKC / 16) * 16);
                             const uint32_t d = taddr + s * 256;
 #pragma unroll
                             for (int st = 0; st < kWKC / 16; ++st)
@@ -597,8 +609,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         // ---- epilogue.  Warps 2..9 serve slot 0 and 10..17 slot 1; in a slot, warps e and
         // e + 4 share TMEM lane quadrant warp % 4 and take the lower / upper 128 columns.
         // At the output layer the lower half stores the outputs while the upper half stores
-        // the slot's next tile's features, computed a layer ahead (their global loads and
-        // sin / cos stay off the MMA thread's critical path).
+        // the slot's next tile's features, computed after the layer-1 epilogue while the
+        // layer-2 MMAs run (their global loads and sin / cos stay off the layer boundaries).
         const int e = warp - 2;
         const int s = e >> 3, half = (e >> 2) & 1, quad = warp & 3;
         const int rl = quad * 32 + lane;
@@ -623,7 +635,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             if (s < T) {
                 if (HALF) store_features(my_act, rl, features_of(tile_row0(s) + rl, q, B));
                 release();
-                if (HALF && s + 2 < T) f = features_of(tile_row0(s + 2) + rl, q, B);
             }
             uint32_t accn = 0;
             bool ok = true;
@@ -675,7 +686,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                         if (HALF) store_features(my_act, rl, f);
                     }
                     release();
-                    if (l == kLayers - 1 && HALF && i + 4 < T) f = features_of(tile_row0(i + 4) + rl, q, B);
+                    // the slot's next tile's features, for its output-layer epilogue: computed
+                    // while this tile's layer-2 MMAs run, off the layer boundaries
+                    if (l == 1 && HALF && i + 2 < T) f = features_of(tile_row0(i + 2) + rl, q, B);
                 }
             }
         };
