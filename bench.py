@@ -88,6 +88,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=("vedt", "reference"), default="vedt")
     p.add_argument("--e2e-steps", type=int, default=200)
+    p.add_argument("--bands", type=int, default=0,
+                   help="bands per line for the frame workload (0: the autotuner's pick; fixed for profiling runs)")
     p.add_argument("--frames", type=int, default=60, help="distinct synthetic frames, cycled")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -375,8 +377,12 @@ def run_vedt(args):
     # bands per line for this frame workload: the autotuner's pick (a short sweep of
     # frames at every band count; cached per GPU and dims), kept for the timed region
     import paper_2407_02363_b300.autotune as at
-    tuned_bands, tuned_ms = at.tune_map(m, stream, grid.dims, op=lambda: [step(j) for j in range(10)], reps=3,
-                                        force=True, kind="frame")
+    if args.bands:
+        m.set_bands(args.bands)
+        tuned_bands, tuned_ms = args.bands, {}
+    else:
+        tuned_bands, tuned_ms = at.tune_map(m, stream, grid.dims, op=lambda: [step(j) for j in range(10)], reps=3,
+                                            force=True, kind="frame")
     # ---- timed region: K frames back to back, device time with CUDA events on the
     # library's stream at its two ends only (an event between two frames would end the
     # programmatic overlap of one frame's last kernel with the next frame's first) ----
