@@ -121,6 +121,8 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
     int64_t rows = 0, ty = 0, tz = 0;
     t.large = 0;
     t.maxY = t.maxZ = t.maxXp = 0;
+    for (const GridDesc &g : d) t.large |= g.X > kSmallMax || g.Y > kSmallMax || g.Z > kSmallMax;
+    const bool big = t.large != 0;
     for (size_t i = 0; i < d.size(); ++i) {
         GridDesc &g = d[i];
         g.row_begin = rows;
@@ -128,9 +130,7 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
         g.tz_begin = tz;
         rows += static_cast<int64_t>(g.Y) * g.Z;
         ty += static_cast<int64_t>(g.Xp / kEnvCols) * g.Z;
-        tz += static_cast<int64_t>(g.Xp / kEnvCols) * g.Y;
-        const bool large = g.X > kSmallMax || g.Y > kSmallMax || g.Z > kSmallMax;
-        t.large |= large;
+        tz += big ? static_cast<int64_t>(g.Xp / kEnvCols) * g.Y : small_tiles_z(g.Xp, g.Y);
         t.maxY = g.Y > t.maxY ? g.Y : t.maxY;
         t.maxZ = g.Z > t.maxZ ? g.Z : t.maxZ;
         t.maxXp = g.Xp > t.maxXp ? g.Xp : t.maxXp;
@@ -138,13 +138,16 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
     for (size_t i = 0; i < d.size(); ++i) {
         GridDesc &g = d[i];
         const uint32_t by = g.Y > kBox ? kBox : g.Y, bz = g.Z > kBox ? kBox : g.Z;
-        const bool big = t.large != 0;
         if (encode_tmap(&tm[2 * i], big ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
                         big ? 2 : 1, g.xs, g.Xp, g.Y, g.Z, kEnvCols, by, 1) != CUDA_SUCCESS)
             return VEDT_ECUDA;
-        if (encode_tmap(&tm[2 * i + 1], big ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
-                        big ? 4 : 2, g.s2, g.Xp, g.Y, g.Z, kEnvCols, 1, bz) != CUDA_SUCCESS)
-            return VEDT_ECUDA;
+        // small tables: a kPZX x kPZY patch of columns (rows y >= Y of a ragged last patch
+        // read as zeros); large tables: 32 columns of one row
+        const CUresult r = big ? encode_tmap(&tm[2 * i + 1], CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, g.s2, g.Xp, g.Y, g.Z,
+                                             kEnvCols, 1, bz)
+                               : encode_tmap(&tm[2 * i + 1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, g.s2, g.Xp, g.Y, g.Z,
+                                             kPZX, kPZY, bz);
+        if (r != CUDA_SUCCESS) return VEDT_ECUDA;
     }
     VCHECK(cudaMemcpy(dev_desc, d.data(), sizeof(GridDesc) * d.size(), cudaMemcpyHostToDevice));
     VCHECK(cudaMemcpy(dev_tmaps, tm.data(), sizeof(CUtensorMap) * tm.size(), cudaMemcpyHostToDevice));

@@ -2,12 +2,12 @@
 // whose every dimension is at most 256; the stand-alone kernels are in envelope.cu, the
 // persistent batch kernel in edt.cu.
 //
-// A tile is 32 adjacent columns of one line family (pass Y: columns (x, z) along y of
-// slice z; pass Z: columns (x, y) along z of row y) over the whole line, one lane per
-// column, NB warps per tile (the m2 / m3 banding of Alg. 1): warp b owns band b, the
-// positions [b * bl, (b + 1) * bl) of every line, bl = ceil(n / NB).  Every global access
-// is coalesced across x.  The line tile is staged into shared memory by one TMA box load
-// (no multicast).
+// A tile is 32 columns of one line family over the whole line (pass Y: 32 adjacent columns
+// (x, z) of slice z, along y; pass Z: a patch of kPZX x kPZY columns (x, y), along z), one
+// lane per column, NB warps per tile (the m2 / m3 banding of Alg. 1): warp b owns band b,
+// the positions [b * bl, (b + 1) * bl) of every line, bl = ceil(n / NB).  Global accesses
+// are runs along x (32 columns in pass Y, kPZX in pass Z).  The line tile is staged into
+// shared memory by one TMA box load (no multicast).
 //
 //   build   every warp sweeps the valid positions of its band (rows / slices that hold a
 //           site: the same for all 32 columns, so the sweep is warp-uniform) and keeps the
@@ -479,32 +479,37 @@ __device__ __forceinline__ bool tile_y(const GridDesc &G, const CUtensorMap *tma
 }
 
 // ------------------------------------------------------------------------------------
-// pass Z: tile = (grid, row y, columns x0 .. x0 + 31), line along z; writes sqdist and
-// the nearest voxel's linear index
+// pass Z: tile = (grid, patch of kPZX x kPZY columns (x, y) at (x0, y0)), line along z;
+// writes sqdist and the nearest voxel's linear index
 // ------------------------------------------------------------------------------------
 // One pass-Z tile (grid g, tile lt of that grid), as tile_y (layout Layout<NB, uint16_t>(Z)).
+// Lane l owns column (x0 + l % kPZX, y0 + l / kPZX); the TMA box lands as [z][kPZY][kPZX],
+// i.e. [z][lane], the same staged layout as a 32 x 1 row.  The valid positions (slices
+// holding a site) are the same for every column, so the build stays warp-uniform; lanes
+// past the grid's last row (a ragged last patch, read as zero words) compute but store
+// nothing.
 template <int NB, bool kOwnBar>
 __device__ __forceinline__ bool tile_z(const GridDesc &G, const CUtensorMap *tmap, int lt, uint8_t *smem,
                                        uint64_t *bar, uint32_t phase, int32_t *err) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int X = G.X, Y = G.Y, Z = G.Z, Xp = G.Xp;
-    const int tiles_x = Xp / kC;
-    const int y = lt / tiles_x, x0 = (lt % tiles_x) * kC;
+    const int tiles_x = Xp / kPZX;
+    const int y0 = (lt / tiles_x) * kPZY, x0 = (lt % tiles_x) * kPZX;
     const Layout<NB, uint16_t> L(Z);
     uint16_t *in = reinterpret_cast<uint16_t *>(smem);
     uint8_t *pos = smem + L.pos_off;
     uint8_t *rng = smem + L.rng_off;
-    if (tid == 0) load_tile(in, tmap, Z, x0, y, false, bar);
-    const int x = x0 + lane;
+    if (tid == 0) load_tile(in, tmap, Z, x0, y0, false, bar);
+    const int x = x0 + lane % kPZX, y = y0 + lane / kPZX;
     const PolZ pol{static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 8), x * x + y * y};
     Joined<NB, PolZ> J;
     int lo, hi;
     bool ok;
     const bool any = envelope<NB, kOwnBar>(pol, in, pos, rng, G.slice_has, Z, J, lo, hi, bar, phase, err, ok);
     if (!ok) return false;
-    const bool live = x < X;
+    const bool live = x < X && y < Y;
     const uint32_t plane = static_cast<uint32_t>(X * Y);
-    uint32_t off = static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(y * X + (live ? x : 0));
+    uint32_t off = static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(live ? y * X + x : 0);
     const uint32_t lim = plane * static_cast<uint32_t>(Z);
     int32_t *sq = G.sqdist, *ix = G.idx;
     if (!any) {   // empty grid

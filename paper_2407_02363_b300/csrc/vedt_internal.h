@@ -15,6 +15,14 @@ constexpr int kEnvCols = 32;         // columns per pass-Y/Z tile (one warp per 
 constexpr int kBox = 256;            // max TMA box extent along one dimension
 constexpr uint16_t kNoX = 0xFFFF;    // pass-X "row has no site"
 constexpr int kSmallMax = 256;       // all dims <= 256: 16-bit packed 2-D sites, 8-bit links
+// Pass-Z tile of small tables: a patch of kPZX x kPZY columns (x fastest), one lane per
+// column.  Columns close in both x and y have similar envelopes along z, so a square-ish
+// patch keeps the lanes of a warp in step more often than a 32 x 1 row.
+constexpr int kPZX = 8;
+constexpr int kPZY = kEnvCols / kPZX;
+inline int64_t small_tiles_z(int Xp, int Y) {
+    return static_cast<int64_t>(Xp / kPZX) * ((Y + kPZY - 1) / kPZY);
+}
 
 // error word bits (device-side guards)
 constexpr int kErrTimeout = 1;
@@ -34,7 +42,7 @@ struct GridDesc {
     int32_t X, Y, Z, Xp;
     int64_t row_begin;      // prefix over rows (Y*Z) of the grids before this one
     int64_t ty_begin;       // prefix over pass-Y tiles ((Xp/32)*Z)
-    int64_t tz_begin;       // prefix over pass-Z tiles ((Xp/32)*Y)
+    int64_t tz_begin;       // prefix over pass-Z tiles (small tables: small_tiles_z; else (Xp/32)*Y)
     int64_t xi_begin;       // prefix over persistent pass-X items (ceil(Y*Z / rows_per_item))
     const uint32_t *changed;  // NULL, or a device word: 0 = occupancy unchanged since this
                               // grid's last EDT (incremental maps), so the passes skip it
@@ -50,7 +58,8 @@ struct PersistCounters {
 
 struct GridTable {
     GridDesc *desc;              // device array [n]
-    CUtensorMap *tmaps;          // device array [2n]: {xs box (32, by, 1), s2 box (32, 1, bz)}
+    CUtensorMap *tmaps;          // device array [2n]: {xs box (32, by, 1), s2 box (32, 1, bz);
+                                 // small tables: s2 box (kPZX, kPZY, Z)}
     int n;
     int large;                   // 0: every grid has dims <= 256
     int maxY, maxZ, maxXp;
