@@ -46,7 +46,7 @@ WORKLOAD = ("frame256: 256^3 grid at 1 cm; 300k-point synthetic depth-camera clo
 # launches, one map per launch) with a hash of the kernel
 # sources it was taken from (comments and blank space excluded) and the algorithmic bytes
 # of the captured launch; reported only while both still match.
-NCU_TRAFFIC = {"edt_z": {"bytes": 111569472, "alg_bytes_per_launch": 167772160, "src": "3721a733be8047ed"}}
+NCU_TRAFFIC = {"edt_z": {"bytes": 111543936, "alg_bytes_per_launch": 167772160, "src": "298c825381eb27f9"}}
 KERNEL_SOURCES = ("paper_2407_02363_b300/csrc/envelope.cuh", "paper_2407_02363_b300/csrc/envelope.cu",
                   "paper_2407_02363_b300/csrc/edt.cu", "paper_2407_02363_b300/csrc/vedt_internal.h")
 
@@ -90,6 +90,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=200)
     p.add_argument("--bands", type=int, default=0,
                    help="bands per line for the frame workload (0: the autotuner's pick; fixed for profiling runs)")
+    p.add_argument("--tile-z", type=int, default=0,
+                   help="pass-Z tile width for the frame workload with --bands (8: 8 x 4 columns, 32: 32 x 1, "
+                        "0: the default shape)")
     p.add_argument("--frames", type=int, default=60, help="distinct synthetic frames, cycled")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -374,15 +377,17 @@ def run_vedt(args):
     for i in range(args.warmup):
         step(i)
     m.check()
-    # bands per line for this frame workload: the autotuner's pick (a short sweep of
-    # frames at every band count; cached per GPU and dims), kept for the timed region
+    # bands per line and pass-Z tile shape for this frame workload: the autotuner's pick
+    # (a short sweep of frames under every candidate; cached per GPU and dims), kept for
+    # the timed region
     import paper_2407_02363_b300.autotune as at
     if args.bands:
-        m.set_bands(args.bands)
-        tuned_bands, tuned_ms = args.bands, {}
+        tuned, tuned_ms = at.MapTuning(args.bands, args.tile_z), {}
+        tuned.apply(m)
     else:
-        tuned_bands, tuned_ms = at.tune_map(m, stream, grid.dims, op=lambda: [step(j) for j in range(10)], reps=3,
-                                            force=True, kind="frame")
+        tuned, tuned_ms = at.tune_map(m, stream, grid.dims, op=lambda: [step(j) for j in range(10)], reps=3,
+                                      force=True, kind="frame")
+    frame_tile_z = m.tile_z()
     # ---- timed region: K frames back to back, device time with CUDA events on the
     # library's stream at its two ends only (an event between two frames would end the
     # programmatic overlap of one frame's last kernel with the next frame's first) ----
@@ -487,8 +492,9 @@ def run_vedt(args):
             "config": {"workload": WORKLOAD, "dims": list(DIMS), "voxel_size_m": VOXEL, "points": N_POINTS,
                        "maps_per_step": 2, "distinct_frames": n_frames, "parallelism": f"replicas x{world}",
                        "l2": "no flush: each step writes 268 MB of fields plus ~134 MB of scratch, > 126 MB L2",
-                       "bands": tuned_bands,
-                       "bands_sweep_ms_per_10_frames": {str(k): t for k, t in tuned_ms.items()}},
+                       "bands": tuned.bands, "tile_z": frame_tile_z,
+                       "tuning_sweep_ms_per_10_frames": {t.label(): ms for t, ms in tuned_ms.items()},
+                       "tuning_key": "bands/tile_z (pass-Z tile width in x: 8 = 8 x 4 columns, 32 = 32 x 1)"},
             "latency_ms": {"p50": frame_ms[len(frame_ms) // 2], "p99": frame_ms[min(len(frame_ms) - 1,
                                                                                      int(0.99 * len(frame_ms)))],
                            "max": frame_ms[-1], "what": "device time per frame (events around each frame, "
@@ -700,13 +706,14 @@ def run_paper_sizes(args, v):
             m.set_bands(nb)
             by_bands[str(nb)] = time_edt()
         # the autotuner's pick for this map size (its own short sweep), then the full timing
-        nb, _ = at.tune_map(m, stream, dims, op=lambda: m.compute_edt(v.MAP_ENV), reps=5, force=True,
-                            kind="edt_env")
+        best, _ = at.tune_map(m, stream, dims, op=lambda: m.compute_edt(v.MAP_ENV), reps=5, force=True,
+                              kind="edt_env")
         tuned_ms = time_edt()
-        m.set_bands(0)
+        tz = m.tile_z()
+        at.MapTuning(0, 0).apply(m)
         out.append({"dims": list(dims), "occupied_voxels": occupied, "edt_ms": ms,
                     "gvoxel_s": n / (ms * 1e-3) / 1e9, "edt_ms_by_bands": by_bands,
-                    "tuned": {"bands": nb, "edt_ms": tuned_ms},
+                    "tuned": {"bands": best.bands, "tile_z": tz, "edt_ms": tuned_ms},
                     "paper": {"occupied_voxels": paper_occ, "pba_ms_stage_table": paper_ms,
                               "pba_ms_edt_table": paper_cmp_ms, "gpu": "GTX 1080 Ti"}})
         m.close()
@@ -752,7 +759,8 @@ def run_batched(args, v, dev):
     b.set_frame(xyz, offs, np.stack(poses), SELF_MASK, cen, radii, m_sph, out)
     b.run()
     b.check()
-    best, times = at.tune(b, stream, dims_list, reps=3, force=True)   # launch shapes x band counts
+    best, times = at.tune(b, stream, dims_list, reps=3, force=True)   # launch shapes x bands x tile shapes
+    b_tile_z = b.tile_z()
     b.capture()
     for _ in range(3):
         b.replay()
@@ -775,9 +783,11 @@ def run_batched(args, v, dev):
             "maps": len(dims_list), "voxels_per_frame": vox, "ms_per_frame": ms,
             "gvoxel_s": vox / (ms * 1e-3) / 1e9, "replays": args.batch_steps,
             "tuning": {"persistent": best.persistent, "ctas_per_sm": best.ctas_per_sm,
-                       "rows_per_item": best.rows_per_item, "bands": best.bands, "edt_ms": times[best]},
+                       "rows_per_item": best.rows_per_item, "bands": best.bands, "tile_z": b_tile_z,
+                       "edt_ms": times[best]},
             "edt_ms_by_tuning": {t.label(): ms_ for t, ms_ in times.items()},
-            "tuning_key": "persistent/ctas_per_sm/rows_per_item/bands (0 = three plain launches)"}
+            "tuning_key": "persistent/ctas_per_sm/rows_per_item/bands/tile_z (persistent 0 = three plain "
+                          "launches; tile_z = pass-Z tile width in x, 8 x 4 or 32 x 1 columns)"}
 
 
 def run_surrogate(args, v, dev):

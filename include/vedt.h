@@ -107,6 +107,18 @@ vedt_status vedt_map_set_stream(vedt_map *map, void *stream);
  * vedt_compute_edt on.  Errors: EINVAL (NULL map, other values). */
 vedt_status vedt_map_set_bands(vedt_map *map, int bands);
 
+/* Tile shape of pass Z (Alg. 1 Step 4; a launch shape, the fields do not depend on it)
+ * for grids with every dim <= 256: cols_x = 8 makes each warp's 32 columns an 8 x 4
+ * patch of (x, y), cols_x = 32 a row of 32 x-adjacent columns, 0 the default (8 x 4 if X
+ * is a multiple of 8, else 32 x 1).  Larger grids always take 32 x 1 (cols_x 0 or 32).
+ * Synchronises the map's streams and rewrites its launch tables; a CUDA graph that holds
+ * this map's EDT launches must be recorded again.  Errors: EINVAL (NULL map, other
+ * values), ECUDA. */
+vedt_status vedt_map_set_tile_z(vedt_map *map, int cols_x);
+
+/* The map's current pass-Z tile width (8 or 32; 0 for a NULL map). */
+int vedt_map_tile_z(const vedt_map *map);
+
 /* Bayesian occupancy of M_I (Sec. III-A names a Bayesian per-voxel update and gives
  * no model), in integer log-odds.  With on = 1 the map keeps an int8 log-odds value per
  * voxel of M_I, 0 (unknown) at the start.  Each
@@ -280,6 +292,16 @@ vedt_status vedt_batch_set_tuning(vedt_batch *batch, int ctas_per_sm, int rows_p
  * with a larger dim keep 4 / 8 by line length, or take 4 or 8).  Applies to the plain
  * and the persistent launches.  Drops a recorded graph.  Errors: EINVAL. */
 vedt_status vedt_batch_set_bands(vedt_batch *batch, int bands);
+
+/* Pass-Z tile shape of the batch's grids with every dim <= 256, as vedt_map_set_tile_z
+ * (the default looks at every such grid's X).  Applies to the plain and the persistent
+ * launches.  Synchronises the batch's stream, rewrites its launch tables and drops a
+ * recorded graph.  Errors: EINVAL, ECUDA. */
+vedt_status vedt_batch_set_tile_z(vedt_batch *batch, int cols_x);
+
+/* The batch's current pass-Z tile width for its grids with every dim <= 256 (8 or 32; 0
+ * if it has none). */
+int vedt_batch_tile_z(const vedt_batch *batch);
 
 /* PBA_EDT (Alg. 2 line 9) of the selected grids (default both) of every map in the batch. */
 vedt_status vedt_batch_compute_edt(vedt_batch *batch);

@@ -4,10 +4,12 @@ The exact result never depends on these knobs, only the time does (the m1 / m2 /
 of Alg. 1 are PBA's tunables, Sec. III-C; Tab. 2 compares band settings).
 
 * Single maps and frames (`tune_map`): the bands per line of passes Y and Z
-  (vedt_map_set_bands: 1, 2, 4 or 8 for grids with every dim <= 256; 4 or 8 above).
+  (vedt_map_set_bands: 1, 2, 4 or 8 for grids with every dim <= 256; 4 or 8 above) and
+  the pass-Z tile shape (vedt_map_set_tile_z: 8 x 4 or 32 x 1 columns, dims <= 256).
 * Batches (`tune`): three plain launches (one per sweep) versus one persistent launch
-  over a work queue, the bands per line of either, and for the persistent launch the
-  CTAs per SM and the pass-X rows per work item (vedt_batch_set_tuning / _set_bands).
+  over a work queue, the bands per line and pass-Z tile shape of either, and for the
+  persistent launch the CTAs per SM and the pass-X rows per work item
+  (vedt_batch_set_tuning / _set_bands / _set_tile_z).
 
 Each candidate is timed with CUDA events on the workload's stream over a few repetitions
 (after warm-up); the fastest wins.  Winners are cached per (GPU name, grid-dimension
@@ -23,6 +25,7 @@ from dataclasses import asdict, dataclass
 
 BANDS_SMALL = (1, 2, 4, 8)    # grids with every dim <= 256
 BANDS_LARGE = (4, 8)
+TILES_Z = (8, 32)             # pass-Z tile widths (8 x 4, 32 x 1 columns), dims <= 256
 
 
 @dataclass(frozen=True)
@@ -31,22 +34,39 @@ class Tuning:
     ctas_per_sm: int
     rows_per_item: int
     bands: int = 0
+    tile_z: int = 0
 
     def apply(self, batch):
+        batch.set_tile_z(self.tile_z)
         batch.set_tuning(self.ctas_per_sm, self.rows_per_item, self.persistent)
         batch.set_bands(self.bands)
 
     def label(self) -> str:
-        return f"{self.persistent}/{self.ctas_per_sm}/{self.rows_per_item}/{self.bands}"
+        return f"{self.persistent}/{self.ctas_per_sm}/{self.rows_per_item}/{self.bands}/{self.tile_z}"
 
 
-def batch_candidates(large=False, bands=None):
-    """Plain launches and persistent shapes, each at every admitted band count."""
+@dataclass(frozen=True)
+class MapTuning:
+    bands: int
+    tile_z: int = 0
+
+    def apply(self, m):
+        m.set_tile_z(self.tile_z)
+        m.set_bands(self.bands)
+
+    def label(self) -> str:
+        return f"{self.bands}/{self.tile_z}"
+
+
+def batch_candidates(large=False, bands=None, tiles=None):
+    """Plain launches and persistent shapes, each at every admitted band count and pass-Z
+    tile shape."""
     bs = bands or (BANDS_LARGE if large else BANDS_SMALL)
     out = []
-    for b in bs:
-        out.append((0, 0, 32, b))
-        out += [(1, c, r, b) for c in (0, 4) for r in (16, 64)]
+    for tz in (tiles or TILES_Z):
+        for b in bs:
+            out.append((0, 0, 32, b, tz))
+            out += [(1, c, r, b, tz) for c in (0, 4) for r in (16, 64)]
     return out
 
 
@@ -129,7 +149,8 @@ def tune(batch, stream, dims_list, candidates=None, reps=5, path=None, force=Fal
     """Returns (best Tuning, {Tuning: ms}) and applies the best to `batch`.  A cached
     winner for the same GPU, dims and kind is applied without timing unless force=True."""
     large = any(max(int(v) for v in d) > 256 for d in dims_list)
-    cands = [_as_tuning(c) for c in (candidates or batch_candidates(large))]
+    small = any(max(int(v) for v in d) <= 256 for d in dims_list)
+    cands = [_as_tuning(c) for c in (candidates or batch_candidates(large, tiles=None if small else (0,)))]
     key = signature(_gpu(), dims_list, kind)
     cache = load_cache(path)
     if not force and key in cache:
@@ -156,37 +177,51 @@ def apply_cached(batch, dims_list, path=None, kind="batch"):
 
 
 def map_candidates(dims):
+    """Band counts admitted for a map of these dims."""
     return BANDS_LARGE if max(int(v) for v in dims) > 256 else BANDS_SMALL
 
 
+def map_tunings(dims):
+    """Every (bands, pass-Z tile shape) pair admitted for a map of these dims."""
+    tiles = TILES_Z if max(int(v) for v in dims) <= 256 else (0,)
+    return [MapTuning(b, tz) for tz in tiles for b in map_candidates(dims)]
+
+
+def _map_entry(e) -> MapTuning:
+    return MapTuning(**e["tuning"]) if "tuning" in e else MapTuning(int(e["bands"]))
+
+
 def tune_map(m, stream, dims, op=None, candidates=None, reps=5, warmup=2, path=None, force=False, kind="edt"):
-    """Bands per line for one map: times `op` (default: the EDT of both grids) at every
-    candidate band count, applies and caches the fastest.  Returns (bands, {bands: ms})."""
+    """Bands per line and pass-Z tile shape for one map: times `op` (default: the EDT of
+    both grids) under every candidate (MapTuning, or a band count for the default shape),
+    applies and caches the fastest.  Returns (MapTuning, {MapTuning: ms})."""
     import paper_2407_02363_b300.vedt as v
     run = op or (lambda: m.compute_edt(v.MAP_BOTH))
     key = signature(_gpu(), [dims], kind)
     cache = load_cache(path)
     if not force and key in cache:
-        nb = int(cache[key]["bands"])
-        m.set_bands(nb)
-        return nb, {}
+        t = _map_entry(cache[key])
+        t.apply(m)
+        return t, {}
+    cands = [c if isinstance(c, MapTuning) else MapTuning(int(c)) for c in (candidates or map_tunings(dims))]
     times = {}
-    for nb in (candidates or map_candidates(dims)):
-        m.set_bands(nb)
-        times[nb] = _time(run, stream, reps, warmup)
+    for t in cands:
+        t.apply(m)
+        times[t] = _time(run, stream, reps, warmup)
     m.check()
     best = pick(times)
-    m.set_bands(best)
-    cache[key] = {"bands": best, "ms": times[best], "swept": {str(k): t for k, t in times.items()}}
+    best.apply(m)
+    cache[key] = {"tuning": asdict(best), "ms": times[best], "swept": {t.label(): ms for t, ms in times.items()}}
     store_cache(cache, path)
     return best, times
 
 
 def apply_cached_map(m, dims, path=None, kind="edt"):
-    """Sets a map's bands from the cache (a winner of tune_map for these dims and kind on
-    this GPU); returns the band count or None."""
+    """Applies a map's cached winner of tune_map for these dims and kind on this GPU;
+    returns it (a MapTuning) or None."""
     e = load_cache(path).get(signature(_gpu(), [dims], kind))
     if not e:
         return None
-    m.set_bands(int(e["bands"]))
-    return int(e["bands"])
+    t = _map_entry(e)
+    t.apply(m)
+    return t

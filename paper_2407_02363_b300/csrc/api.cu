@@ -113,9 +113,16 @@ CUresult encode_tmap(CUtensorMap *m, CUtensorMapDataType t, int elem, void *base
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
+int default_pzx(const GridDesc *grids, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (grids[i].X % 8 != 0) return 32;
+    return 8;
+}
+
 // Fills desc/tmaps for grids (host copies) and uploads them; used by maps and batches.
+// pzx: pass-Z tile width of a small table (8 or 32; 0: default_pzx).
 vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *dev_desc, void *dev_tmaps,
-                        int32_t *err) {
+                        int32_t *err, int pzx) {
     std::vector<GridDesc> d(grids);
     std::vector<CUtensorMap> tm(2 * grids.size());
     int64_t rows = 0, ty = 0, tz = 0;
@@ -123,6 +130,8 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
     t.maxY = t.maxZ = t.maxXp = 0;
     for (const GridDesc &g : d) t.large |= g.X > kSmallMax || g.Y > kSmallMax || g.Z > kSmallMax;
     const bool big = t.large != 0;
+    t.pzx = big ? kEnvCols : (pzx ? pzx : default_pzx(d.data(), d.size()));
+    const int px = t.pzx, py = kEnvCols / px;
     for (size_t i = 0; i < d.size(); ++i) {
         GridDesc &g = d[i];
         g.row_begin = rows;
@@ -130,7 +139,7 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
         g.tz_begin = tz;
         rows += static_cast<int64_t>(g.Y) * g.Z;
         ty += static_cast<int64_t>(g.Xp / kEnvCols) * g.Z;
-        tz += big ? static_cast<int64_t>(g.Xp / kEnvCols) * g.Y : small_tiles_z(g.Xp, g.Y);
+        tz += big ? static_cast<int64_t>(g.Xp / kEnvCols) * g.Y : small_tiles_z(g.Xp, g.Y, px);
         t.maxY = g.Y > t.maxY ? g.Y : t.maxY;
         t.maxZ = g.Z > t.maxZ ? g.Z : t.maxZ;
         t.maxXp = g.Xp > t.maxXp ? g.Xp : t.maxXp;
@@ -141,12 +150,12 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
         if (encode_tmap(&tm[2 * i], big ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
                         big ? 2 : 1, g.xs, g.Xp, g.Y, g.Z, kEnvCols, by, 1) != CUDA_SUCCESS)
             return VEDT_ECUDA;
-        // small tables: a kPZX x kPZY patch of columns (rows y >= Y of a ragged last patch
-        // read as zeros); large tables: 32 columns of one row
+        // small tables: a px x py patch of columns (rows y >= Y of a ragged last patch read
+        // as zeros); large tables: 32 columns of one row
         const CUresult r = big ? encode_tmap(&tm[2 * i + 1], CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, g.s2, g.Xp, g.Y, g.Z,
                                              kEnvCols, 1, bz)
                                : encode_tmap(&tm[2 * i + 1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, g.s2, g.Xp, g.Y, g.Z,
-                                             kPZX, kPZY, bz);
+                                             static_cast<uint32_t>(px), static_cast<uint32_t>(py), bz);
         if (r != CUDA_SUCCESS) return VEDT_ECUDA;
     }
     VCHECK(cudaMemcpy(dev_desc, d.data(), sizeof(GridDesc) * d.size(), cudaMemcpyHostToDevice));
@@ -220,6 +229,22 @@ GridDesc grid_of(const vedt_map *m, int i) {
     g.Xp = m->Xp;
     g.changed = m->changed + i;
     return g;
+}
+
+// The map's three EDT tables, ENV = {0}, SELF = {1}, BOTH = {0, 1}, in tab_mem: four
+// descriptors, then the tensor maps (128-byte aligned).  pzx: pass-Z tile width (0:
+// default).  Keeps the tables' band counts.
+vedt_status build_map_tables(vedt_map *m, int pzx) {
+    char *base = static_cast<char *>(m->tab_mem);
+    char *tmb = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(base + sizeof(GridDesc) * 4) + 127) &
+                                         ~uintptr_t(127));
+    const std::vector<GridDesc> g0{grid_of(m, 0)}, g1{grid_of(m, 1)}, g01{grid_of(m, 0), grid_of(m, 1)};
+    vedt_status st = build_table(m->tab[0], g0, base, tmb, m->err, pzx);
+    if (st == VEDT_OK)
+        st = build_table(m->tab[1], g1, base + sizeof(GridDesc), tmb + 2 * sizeof(CUtensorMap), m->err, pzx);
+    if (st == VEDT_OK)
+        st = build_table(m->tab[2], g01, base + 2 * sizeof(GridDesc), tmb + 4 * sizeof(CUtensorMap), m->err, pzx);
+    return st;
 }
 
 }  // namespace
@@ -300,15 +325,7 @@ vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float
         free_map(m);
         return from_cuda(e);
     }
-    // tables: ENV = {0}, SELF = {1}, BOTH = {0, 1}; descriptors then tensor maps (64B aligned)
-    char *base = static_cast<char *>(m->tab_mem);
-    char *tmb = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(base + desc_bytes) + 127) & ~uintptr_t(127));
-    const std::vector<GridDesc> g0{grid_of(m, 0)}, g1{grid_of(m, 1)}, g01{grid_of(m, 0), grid_of(m, 1)};
-    vedt_status st = build_table(m->tab[0], g0, base, tmb, m->err);
-    if (st == VEDT_OK)
-        st = build_table(m->tab[1], g1, base + sizeof(GridDesc), tmb + 2 * sizeof(CUtensorMap), m->err);
-    if (st == VEDT_OK)
-        st = build_table(m->tab[2], g01, base + 2 * sizeof(GridDesc), tmb + 4 * sizeof(CUtensorMap), m->err);
+    vedt_status st = build_map_tables(m, 0);
     const QueryGrid qg[4] = {{m->sq[0], m->ix[0]}, {m->sq[1], m->ix[1]}, {m->sq[0], m->ix[0]}, {m->sq[1], m->ix[1]}};
     if (st == VEDT_OK) st = from_cuda(cudaMemcpy(m->qgrids, qg, sizeof(qg), cudaMemcpyHostToDevice));
     if (st != VEDT_OK) {
@@ -406,6 +423,19 @@ vedt_status vedt_map_set_bands(vedt_map *m, int bands) {
     for (GridTable &t : m->tab) t.bands = bands;
     return VEDT_OK;
 }
+
+vedt_status vedt_map_set_tile_z(vedt_map *m, int cols_x) {
+    if (!m || !(cols_x == 0 || cols_x == 8 || cols_x == 32)) return VEDT_EINVAL;
+    if (m->tab[0].large) return cols_x == 0 || cols_x == 32 ? VEDT_OK : VEDT_EINVAL;
+    // the tables' device descriptors and tensor maps are rewritten: nothing of this map
+    // may be in flight
+    VCHECK(cudaStreamSynchronize(m->stream));
+    if (m->side_stream) VCHECK(cudaStreamSynchronize(m->side_stream));
+    if (m->copy_stream) VCHECK(cudaStreamSynchronize(m->copy_stream));
+    return build_map_tables(m, cols_x);
+}
+
+int vedt_map_tile_z(const vedt_map *m) { return m ? m->tab[0].pzx : 0; }
 
 vedt_status vedt_map_info(const vedt_map *m, int32_t dims_out[3], float *vs, float origin_out[3]) {
     if (!m) return VEDT_EINVAL;

@@ -142,7 +142,7 @@ vedt_status from_cuda(cudaError_t e) {
 
 namespace vedt {
 vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *dev_desc, void *dev_tmaps,
-                        int32_t *err);
+                        int32_t *err, int pzx);
 }
 
 struct vedt_batch {
@@ -157,6 +157,7 @@ struct vedt_batch {
     int32_t *err = nullptr;
     int ctas_per_sm = 0, rows_per_item = 32, persistent = 1;
     int bands = 0;                       // bands per line of passes Y and Z (0: default)
+    int pzx = 0;                         // pass-Z tile width of the small table (0: default)
     int which = VEDT_MAP_BOTH;           // grids the EDT covers
     // pipeline
     MapRef *refs = nullptr;
@@ -230,7 +231,7 @@ vedt_status build_tables(vedt_batch *b) {
         off += (sizeof(GridDesc) * nd + 127) / 128 * 128;
         char *tm = base + off;
         off += sizeof(CUtensorMap) * 2 * nd;
-        vedt_status st = build_table(b->tab[md], mode[md], desc, tm, b->err);
+        vedt_status st = build_table(b->tab[md], mode[md], desc, tm, b->err, md == 0 ? b->pzx : 0);
         if (st != VEDT_OK) return st;
         b->tab[md].bands = md == 0 ? b->bands : ((b->bands == 4 || b->bands == 8) ? b->bands : 0);
     }
@@ -331,6 +332,21 @@ vedt_status vedt_batch_set_bands(vedt_batch *b, int bands) {
     }
     return VEDT_OK;
 }
+
+vedt_status vedt_batch_set_tile_z(vedt_batch *b, int cols_x) {
+    if (!b || !(cols_x == 0 || cols_x == 8 || cols_x == 32)) return VEDT_EINVAL;
+    BCHECK(cudaStreamSynchronize(b->stream));
+    b->pzx = cols_x;
+    if (b->exec) {   // a recorded graph holds the old launch shapes
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+    }
+    return build_tables(b);
+}
+
+int vedt_batch_tile_z(const vedt_batch *b) { return b && b->ngrid[0] ? b->tab[0].pzx : 0; }
 
 vedt_status vedt_batch_set_grids(vedt_batch *b, int which) {
     if (!b || (which != VEDT_MAP_ENV && which != VEDT_MAP_SELF && which != VEDT_MAP_BOTH)) return VEDT_EINVAL;

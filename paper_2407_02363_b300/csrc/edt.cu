@@ -1564,7 +1564,7 @@ __global__ void __launch_bounds__(kLanes) k_edt_persistent(const GridDesc *__res
 // tile area of shared memory is reused from tile to tile: every thread fences its generic
 // accesses of a tile against the async proxy before the CTA barrier that precedes the
 // next tile's TMA load, which writes the same bytes.
-template <int NB>
+template <int NB, int PX>
 __global__ void __launch_bounds__(NB * 32) k_env_persistent(const GridDesc *__restrict__ gd,
                                                             const CUtensorMap *__restrict__ tm, int ng,
                                                             PersistCounters cnt, int rows_per_item, int32_t *err) {
@@ -1618,7 +1618,8 @@ __global__ void __launch_bounds__(NB * 32) k_env_persistent(const GridDesc *__re
             __syncthreads();
             if (ok_s) {
                 if (is_y) lenv::tile_y<NB, false>(G, &tm[2 * g], static_cast<int>(t - G.ty_begin), smem, &bar, phase, err);
-                else lenv::tile_z<NB, false>(G, &tm[2 * g + 1], static_cast<int>(t - G.tz_begin), smem, &bar, phase, err);
+                else lenv::tile_z<NB, false, PX>(G, &tm[2 * g + 1], static_cast<int>(t - G.tz_begin), smem, &bar, phase,
+                                                 err);
                 phase ^= 1u;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1631,16 +1632,16 @@ __global__ void __launch_bounds__(NB * 32) k_env_persistent(const GridDesc *__re
     }
 }
 
-template <int NB>
+template <int NB, int PX>
 static cudaError_t launch_env_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm,
                                          int rows_per_item, cudaStream_t s) {
     const size_t sy = static_cast<size_t>(lenv::Layout<NB, uint8_t>(t.maxY).bytes);
     const size_t sz = static_cast<size_t>(lenv::Layout<NB, uint16_t>(t.maxZ).bytes);
     const size_t sm = sy > sz ? sy : sz;
-    cudaError_t e = ensure_dyn_smem<k_env_persistent<NB>>(sm);
+    cudaError_t e = ensure_dyn_smem<k_env_persistent<NB, PX>>(sm);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_env_persistent<NB>, NB * 32, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_env_persistent<NB, PX>, NB * 32, sm);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int per_sm = ctas_per_sm > 0 && ctas_per_sm < occ ? ctas_per_sm : occ;
@@ -1649,7 +1650,7 @@ static cudaError_t launch_env_persistent(const GridTable &t, const PersistCounte
     if (blocks > total) blocks = total;
     if (blocks < 1) return cudaSuccess;
     // a plain launch: the queue's first items read the occupancy the previous kernels wrote
-    k_env_persistent<NB><<<static_cast<unsigned>(blocks), NB * 32, sm, s>>>(t.desc, t.tmaps, t.n, c, rows_per_item,
+    k_env_persistent<NB, PX><<<static_cast<unsigned>(blocks), NB * 32, sm, s>>>(t.desc, t.tmaps, t.n, c, rows_per_item,
                                                                            t.err);
     return cudaGetLastError();
 }
@@ -1737,11 +1738,17 @@ static cudaError_t launch_persistent_impl(const GridTable &t, const PersistCount
 cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm, int rows_per_item,
                               cudaStream_t s) {
     if (!t.large) {
+        if (t.pzx != 8 && t.pzx != 32) return cudaErrorInvalidValue;
+        const bool p8 = t.pzx == 8;
         switch (t.bands) {
-            case 1: return launch_env_persistent<1>(t, c, ctas_per_sm, rows_per_item, s);
-            case 2: return launch_env_persistent<2>(t, c, ctas_per_sm, rows_per_item, s);
-            case 8: return launch_env_persistent<8>(t, c, ctas_per_sm, rows_per_item, s);
-            default: return launch_env_persistent<4>(t, c, ctas_per_sm, rows_per_item, s);
+            case 1: return p8 ? launch_env_persistent<1, 8>(t, c, ctas_per_sm, rows_per_item, s)
+                              : launch_env_persistent<1, 32>(t, c, ctas_per_sm, rows_per_item, s);
+            case 2: return p8 ? launch_env_persistent<2, 8>(t, c, ctas_per_sm, rows_per_item, s)
+                              : launch_env_persistent<2, 32>(t, c, ctas_per_sm, rows_per_item, s);
+            case 8: return p8 ? launch_env_persistent<8, 8>(t, c, ctas_per_sm, rows_per_item, s)
+                              : launch_env_persistent<8, 32>(t, c, ctas_per_sm, rows_per_item, s);
+            default: return p8 ? launch_env_persistent<4, 8>(t, c, ctas_per_sm, rows_per_item, s)
+                               : launch_env_persistent<4, 32>(t, c, ctas_per_sm, rows_per_item, s);
         }
     }
     if (t.maxXp <= 256) return launch_persistent_impl<8, false>(t, c, ctas_per_sm, rows_per_item, s);

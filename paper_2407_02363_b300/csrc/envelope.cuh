@@ -3,11 +3,11 @@
 // persistent batch kernel in edt.cu.
 //
 // A tile is 32 columns of one line family over the whole line (pass Y: 32 adjacent columns
-// (x, z) of slice z, along y; pass Z: a patch of kPZX x kPZY columns (x, y), along z), one
-// lane per column, NB warps per tile (the m2 / m3 banding of Alg. 1): warp b owns band b,
-// the positions [b * bl, (b + 1) * bl) of every line, bl = ceil(n / NB).  Global accesses
-// are runs along x (32 columns in pass Y, kPZX in pass Z).  The line tile is staged into
-// shared memory by one TMA box load (no multicast).
+// (x, z) of slice z, along y; pass Z: a patch of 8 x 4 or 32 x 1 columns (x, y), along z),
+// one lane per column, NB warps per tile (the m2 / m3 banding of Alg. 1): warp b owns band
+// b, the positions [b * bl, (b + 1) * bl) of every line, bl = ceil(n / NB).  Global
+// accesses are runs along x (32 columns in pass Y, 8 or 32 in pass Z).  The line tile is
+// staged into shared memory by one TMA box load (no multicast).
 //
 //   build   every warp sweeps the valid positions of its band (rows / slices that hold a
 //           site: the same for all 32 columns, so the sweep is warp-uniform) and keeps the
@@ -479,28 +479,29 @@ __device__ __forceinline__ bool tile_y(const GridDesc &G, const CUtensorMap *tma
 }
 
 // ------------------------------------------------------------------------------------
-// pass Z: tile = (grid, patch of kPZX x kPZY columns (x, y) at (x0, y0)), line along z;
+// pass Z: tile = (grid, patch of PX x (32 / PX) columns (x, y) at (x0, y0)), line along z;
 // writes sqdist and the nearest voxel's linear index
 // ------------------------------------------------------------------------------------
 // One pass-Z tile (grid g, tile lt of that grid), as tile_y (layout Layout<NB, uint16_t>(Z)).
-// Lane l owns column (x0 + l % kPZX, y0 + l / kPZX); the TMA box lands as [z][kPZY][kPZX],
-// i.e. [z][lane], the same staged layout as a 32 x 1 row.  The valid positions (slices
-// holding a site) are the same for every column, so the build stays warp-uniform; lanes
-// past the grid's last row (a ragged last patch, read as zero words) compute but store
-// nothing.
-template <int NB, bool kOwnBar>
+// Lane l owns column (x0 + l % PX, y0 + l / PX); the TMA box (PX, 32 / PX, Z) lands as
+// [z][lane] for either shape.  The valid positions (slices holding a site) are the same
+// for every column, so the build stays warp-uniform; lanes past the grid's last row (a
+// ragged last patch, read as zero words) compute but store nothing.
+template <int NB, bool kOwnBar, int PX>
 __device__ __forceinline__ bool tile_z(const GridDesc &G, const CUtensorMap *tmap, int lt, uint8_t *smem,
                                        uint64_t *bar, uint32_t phase, int32_t *err) {
+    static_assert(PX == 8 || PX == 32, "pass-Z tiles are 8 x 4 or 32 x 1 columns");
+    constexpr int PY = kC / PX;
     const int tid = threadIdx.x, lane = tid & 31;
     const int X = G.X, Y = G.Y, Z = G.Z, Xp = G.Xp;
-    const int tiles_x = Xp / kPZX;
-    const int y0 = (lt / tiles_x) * kPZY, x0 = (lt % tiles_x) * kPZX;
+    const int tiles_x = Xp / PX;
+    const int y0 = (lt / tiles_x) * PY, x0 = (lt % tiles_x) * PX;
     const Layout<NB, uint16_t> L(Z);
     uint16_t *in = reinterpret_cast<uint16_t *>(smem);
     uint8_t *pos = smem + L.pos_off;
     uint8_t *rng = smem + L.rng_off;
     if (tid == 0) load_tile(in, tmap, Z, x0, y0, false, bar);
-    const int x = x0 + lane % kPZX, y = y0 + lane / kPZX;
+    const int x = x0 + lane % PX, y = y0 + lane / PX;
     const PolZ pol{static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 8), x * x + y * y};
     Joined<NB, PolZ> J;
     int lo, hi;

@@ -117,8 +117,10 @@ extern "C" vedt_status vedt_edt_noalloc(const uint8_t *occ_dev, int32_t X, int32
     g.Xp = Xp;
     g.row_begin = g.ty_begin = g.tz_begin = 0;
     const uint32_t by = static_cast<uint32_t>(Y), bz = static_cast<uint32_t>(Z);
+    const int px = default_pzx(&g, 1);
     if (encode_tmap(&h.tm[0], CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, xs, Xp, Y, Z, kEnvCols, by, 1) != CUDA_SUCCESS ||
-        encode_tmap(&h.tm[1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s2, Xp, Y, Z, kPZX, kPZY, bz) != CUDA_SUCCESS)
+        encode_tmap(&h.tm[1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, s2, Xp, Y, Z, static_cast<uint32_t>(px),
+                    static_cast<uint32_t>(kEnvCols / px), bz) != CUDA_SUCCESS)
         return VEDT_ECUDA;
     k_noalloc_header<<<1, 32, 0, s>>>(h, d_hdr, d_err);
     if (cudaGetLastError() != cudaSuccess) return VEDT_ECUDA;
@@ -133,7 +135,8 @@ extern "C" vedt_status vedt_edt_noalloc(const uint8_t *occ_dev, int32_t X, int32
     t.maxXp = Xp;
     t.rows = static_cast<int64_t>(Y) * Z;
     t.tiles_y = static_cast<int64_t>(Xp / kEnvCols) * Z;
-    t.tiles_z = small_tiles_z(Xp, Y);
+    t.tiles_z = small_tiles_z(Xp, Y, px);
+    t.pzx = px;
     t.err = d_err;
     if (launch_pass_x(t, s) != cudaSuccess || launch_pass_y(t, s) != cudaSuccess ||
         launch_pass_z(t, s) != cudaSuccess)

@@ -15,13 +15,14 @@ constexpr int kEnvCols = 32;         // columns per pass-Y/Z tile (one warp per 
 constexpr int kBox = 256;            // max TMA box extent along one dimension
 constexpr uint16_t kNoX = 0xFFFF;    // pass-X "row has no site"
 constexpr int kSmallMax = 256;       // all dims <= 256: 16-bit packed 2-D sites, 8-bit links
-// Pass-Z tile of small tables: a patch of kPZX x kPZY columns (x fastest), one lane per
-// column.  Columns close in both x and y have similar envelopes along z, so a square-ish
-// patch keeps the lanes of a warp in step more often than a 32 x 1 row.
-constexpr int kPZX = 8;
-constexpr int kPZY = kEnvCols / kPZX;
-inline int64_t small_tiles_z(int Xp, int Y) {
-    return static_cast<int64_t>(Xp / kPZX) * ((Y + kPZY - 1) / kPZY);
+// Pass-Z tile of small tables: a patch of px x (32 / px) columns (x fastest), one lane per
+// column, px = 8 or 32 (GridTable::pzx).  Columns close in both x and y have similar
+// envelopes along z, so an 8 x 4 patch keeps the lanes of a warp in step more often than a
+// 32 x 1 row; a row writes whole 128-byte lines of the field where an 8-wide run of a grid
+// whose X is no multiple of 8 straddles two 32-byte sectors.
+inline int64_t small_tiles_z(int Xp, int Y, int px) {
+    const int py = kEnvCols / px;
+    return static_cast<int64_t>(Xp / px) * ((Y + py - 1) / py);
 }
 
 // error word bits (device-side guards)
@@ -59,13 +60,14 @@ struct PersistCounters {
 struct GridTable {
     GridDesc *desc;              // device array [n]
     CUtensorMap *tmaps;          // device array [2n]: {xs box (32, by, 1), s2 box (32, 1, bz);
-                                 // small tables: s2 box (kPZX, kPZY, Z)}
+                                 // small tables: s2 box (pzx, 32 / pzx, Z)}
     int n;
     int large;                   // 0: every grid has dims <= 256
     int maxY, maxZ, maxXp;
     int64_t rows, tiles_y, tiles_z;
     int32_t *err;                // device error word
     int bands;                   // bands per line in passes Y and Z (0: the default)
+    int pzx;                     // small tables: pass-Z tile width in x, 8 or 32 (see small_tiles_z)
     int incr;                    // 1: pass X honours GridDesc::changed (incremental maps)
 };
 
@@ -106,6 +108,9 @@ cudaError_t ensure_dyn_smem(size_t bytes) {
 // host-side helpers (api.cu)
 CUresult encode_tmap(CUtensorMap *m, CUtensorMapDataType t, int elem, void *base,
                      uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1, uint32_t b2);
+// Pass-Z tile width of a small table when none is set: 8 x 4 patches if every grid's X
+// is a multiple of 8 (whole 32-byte sectors per run), else 32 x 1 rows.
+int default_pzx(const GridDesc *grids, size_t n);
 
 // SM count of the current device, cached per device (insert.cu)
 int sm_count();
@@ -120,7 +125,7 @@ cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s);
 cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s);
 // small-mode envelope passes (envelope.cu), `bands` per line = 1, 2, 4 or 8
 cudaError_t launch_env_y(const GridTable &t, int bands, cudaStream_t s);
-cudaError_t launch_env_z(const GridTable &t, int bands, cudaStream_t s);
+cudaError_t launch_env_z(const GridTable &t, int bands, cudaStream_t s);   // tile shape t.pzx
 cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm, int rows_per_item,
                               cudaStream_t s);
 cudaError_t launch_wait_selftest(const unsigned *counter, uint32_t limit, int32_t *err, cudaStream_t s);

@@ -51,6 +51,8 @@ _sig = {
     "vedt_map_destroy": [_P],
     "vedt_map_set_stream": [_P, _P],
     "vedt_map_set_bands": [_P, _I32],
+    "vedt_map_set_tile_z": [_P, _I32],
+    "vedt_map_tile_z": [_P],
     "vedt_map_set_incremental": [_P, _I32],
     "vedt_map_set_logodds": [_P, _I32, _I32, _I32, _I32, _I32, _I32],
     "vedt_update_occupancy": [_P],
@@ -83,6 +85,8 @@ _sig = {
     "vedt_batch_destroy": [_P],
     "vedt_batch_set_tuning": [_P, _I32, _I32, _I32],
     "vedt_batch_set_bands": [_P, _I32],
+    "vedt_batch_set_tile_z": [_P, _I32],
+    "vedt_batch_tile_z": [_P],
     "vedt_batch_compute_edt": [_P],
     "vedt_batch_register_links": [_P, _I32, _P, _P],
     "vedt_batch_set_frame": [_P, _P, _P, _P, _U32, _P, _P, _I32, _P],
@@ -281,6 +285,14 @@ class Map:
         """Bands per line of EDT passes Y and Z (0: default; 1/2/4/8 for dims <= 256, 4/8
         above)."""
         _chk(_lib.vedt_map_set_bands(self._h, int(bands)), "vedt_map_set_bands")
+
+    def set_tile_z(self, cols_x=0):
+        """Pass-Z tile shape: 8 (8 x 4 columns), 32 (32 x 1) or 0 (default); see
+        vedt_map_set_tile_z.  Synchronises the map's streams."""
+        _chk(_lib.vedt_map_set_tile_z(self._h, int(cols_x)), "vedt_map_set_tile_z")
+
+    def tile_z(self):
+        return int(_lib.vedt_map_tile_z(self._h))
 
     def set_logodds(self, on=True, l_hit=9, l_miss=4, l_min=-20, l_max=40, threshold=15):
         """Bayesian (log-odds) occupancy of the environment grid; see vedt_map_set_logodds."""
@@ -524,6 +536,12 @@ class Batch:
 
     def set_bands(self, bands=0):
         _chk(_lib.vedt_batch_set_bands(self._h, int(bands)), "vedt_batch_set_bands")
+
+    def set_tile_z(self, cols_x=0):
+        _chk(_lib.vedt_batch_set_tile_z(self._h, int(cols_x)), "vedt_batch_set_tile_z")
+
+    def tile_z(self):
+        return int(_lib.vedt_batch_tile_z(self._h))
 
     def compute_edt(self):
         _chk(_lib.vedt_batch_compute_edt(self._h), "vedt_batch_compute_edt")

@@ -19,11 +19,12 @@ from gpu_helpers import check_idx_valid, lib
 pytestmark = pytest.mark.gpu
 
 
-def _run(v, occ, bands):
+def _run(v, occ, bands, tile_z=0):
     import oracle
     Z, Y, X = occ.shape
     m = v.Map((X, Y, Z), 0.01)
     m.set_bands(bands)
+    m.set_tile_z(tile_z)
     m.upload_occupancy(v.MAP_ENV, occ)
     m.compute_edt(v.MAP_ENV)
     m.check()
@@ -60,14 +61,15 @@ def _z_cases(X, Y, Z, rng):
     return out
 
 
+@pytest.mark.parametrize("tile_z", [8, 32])
 @pytest.mark.parametrize("bands", [1, 2, 4, 8])
-def test_pass_z_junctions(bands):
+def test_pass_z_junctions(bands, tile_z):
     """256-long z lines; x spans 256 so that the far sites of the cascade (in-plane
-    distance 255) lose to the near site over the whole line."""
+    distance 255) lose to the near site over the whole line.  Both pass-Z tile shapes."""
     v = lib()
     rng = np.random.default_rng(bands)
     for name, occ in _z_cases(256, 8, 256, rng).items():
-        _run(v, occ, bands)
+        _run(v, occ, bands, tile_z)
 
 
 @pytest.mark.parametrize("bands", [1, 2, 4, 8])
@@ -86,5 +88,6 @@ def test_ragged_lines_junctions(bands):
     rng = np.random.default_rng(20 + bands)
     for n in (7, 33, 129, 250):
         for occ in _z_cases(40, 24, n, rng).values():
-            _run(v, occ, bands)
+            _run(v, occ, bands, 8)
+            _run(v, occ, bands, 32)
             _run(v, np.ascontiguousarray(occ.transpose(1, 0, 2)), bands)

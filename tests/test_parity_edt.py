@@ -11,11 +11,12 @@ from gpu_helpers import INT32_MAX, check_idx_valid, lib
 pytestmark = pytest.mark.gpu
 
 
-def run_gpu_edt(occ_env, occ_self=None, which=None, bands=0):
+def run_gpu_edt(occ_env, occ_self=None, which=None, bands=0, tile_z=0):
     v = lib()
     Z, Y, X = occ_env.shape
     m = v.Map((X, Y, Z), 0.01)
     m.set_bands(bands)
+    m.set_tile_z(tile_z)
     m.upload_occupancy(v.MAP_ENV, occ_env)
     if occ_self is not None:
         m.upload_occupancy(v.MAP_SELF, occ_self)
@@ -66,14 +67,36 @@ def test_edt_large_mode(dims, density):
     assert_parity(occ, sq, ix)
 
 
+@pytest.mark.parametrize("tile_z", [8, 32])
 @pytest.mark.parametrize("bands", [1, 2, 4, 8])
-def test_edt_band_count_does_not_change_the_field(bands):
-    """Bands per line (Alg. 1's m2 / m3, the ablation of Tab. 2) change speed only: lines
-    shorter than, equal to and longer than a band multiple, sparse and dense, ragged x."""
+def test_edt_band_count_does_not_change_the_field(bands, tile_z):
+    """Bands per line (Alg. 1's m2 / m3, the ablation of Tab. 2) and the pass-Z tile shape
+    change speed only: lines shorter than, equal to and longer than a band multiple,
+    sparse and dense, X a multiple of 8 and not (8 x 4 patches cut by the grid's edge),
+    Y no multiple of 4 (a ragged last patch)."""
     for dims, dens in (((96, 70, 37), 0.01), ((256, 33, 256), 0.002), ((45, 256, 129), 0.3), ((7, 5, 3), 0.2)):
         occ = synth.random_occupancy(31 + bands + sum(dims), dims, dens)
-        (sq, ix), = run_gpu_edt(occ, bands=bands)
+        (sq, ix), = run_gpu_edt(occ, bands=bands, tile_z=tile_z)
         assert_parity(occ, sq, ix)
+
+
+def test_tile_z_default_and_values():
+    v = lib()
+    aligned, ragged, large = v.Map((64, 30, 20), 0.01), v.Map((45, 30, 20), 0.01), v.Map((300, 8, 8), 0.01)
+    assert aligned.tile_z() == 8 and ragged.tile_z() == 32 and large.tile_z() == 32
+    for m in (aligned, ragged):
+        for tz in (8, 32, 0):
+            m.set_tile_z(tz)
+        for bad in (4, 16, -1, 64):
+            with pytest.raises(v.VedtError):
+                m.set_tile_z(bad)
+    assert aligned.tile_z() == 8 and ragged.tile_z() == 32
+    large.set_tile_z(32)
+    large.set_tile_z(0)
+    with pytest.raises(v.VedtError):
+        large.set_tile_z(8)   # grids above 256 keep 32 x 1 rows
+    for m in (aligned, ragged, large):
+        m.close()
 
 
 @pytest.mark.parametrize("bands", [4, 8])
