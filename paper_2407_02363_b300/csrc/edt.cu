@@ -1317,23 +1317,13 @@ __device__ __forceinline__ bool tile_y_generic(const GridDesc *__restrict__ gd, 
     return true;
 }
 
+// a pass-Y tile of the persistent kernel for tables with a grid above 256 (small tables
+// run k_env_persistent)
 template <bool SMALL>
 __device__ __forceinline__ bool tile_y(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
                                        int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
-    if constexpr (SMALL) return tile_y_small<2, false, false>(gd, tm, g, lt, smem, bar, phase, err);
-    else return tile_y_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
-}
-
-template <bool SMALL>
-__global__ void __launch_bounds__(kLanes) k_pass_y(const GridDesc *__restrict__ gd,
-                                                   const CUtensorMap *__restrict__ tm, int ng, int32_t *err) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint64_t bar;
-    const int64_t t = blockIdx.x;
-    const int g = find_grid(gd, ng, t, 0);
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    __syncthreads();
-    tile_y<SMALL>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, 0, err);
+    static_assert(!SMALL, "tables with every dim <= 256 run k_env_persistent");
+    return tile_y_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1423,23 +1413,12 @@ __device__ __forceinline__ bool tile_z_generic(const GridDesc *__restrict__ gd, 
     return true;
 }
 
+// a pass-Z tile of the persistent kernel for tables with a grid above 256
 template <bool SMALL>
 __device__ __forceinline__ bool tile_z(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
                                        int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
-    if constexpr (SMALL) return tile_z_small<2, false, false>(gd, tm, g, lt, smem, bar, phase, err);
-    else return tile_z_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
-}
-
-template <bool SMALL>
-__global__ void __launch_bounds__(kLanes) k_pass_z(const GridDesc *__restrict__ gd,
-                                                   const CUtensorMap *__restrict__ tm, int ng, int32_t *err) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ uint64_t bar;
-    const int64_t t = blockIdx.x;
-    const int g = find_grid(gd, ng, t, 1);
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    __syncthreads();
-    tile_z<SMALL>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, 0, err);
+    static_assert(!SMALL, "tables with every dim <= 256 run k_env_persistent");
+    return tile_z_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1659,8 +1638,8 @@ static cudaError_t launch_env_persistent(const GridTable &t, const PersistCounte
 // launchers
 // ------------------------------------------------------------------------------------
 
+// shared memory of k_edt_persistent's tiles (tables with a grid above 256)
 static size_t smem_y(const GridTable &t) {
-    if (!t.large) return static_cast<size_t>(small_smem<2, PolY<false>>(t.maxY));
     const int by = t.maxY > kBox ? kBox : t.maxY;
     const size_t rows = static_cast<size_t>((t.maxY + by - 1) / by) * by;
     const size_t xs = t.large ? 2 : 1, link = t.large ? 2 : 1;
@@ -1668,7 +1647,6 @@ static size_t smem_y(const GridTable &t) {
 }
 
 static size_t smem_z(const GridTable &t) {
-    if (!t.large) return static_cast<size_t>(small_smem<2, PolZ<false>>(t.maxZ));
     const int bz = t.maxZ > kBox ? kBox : t.maxZ;
     const size_t rows = static_cast<size_t>((t.maxZ + bz - 1) / bz) * bz;
     const size_t site = t.large ? 4 : 2, link = t.large ? 2 : 1;
