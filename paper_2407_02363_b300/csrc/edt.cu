@@ -409,8 +409,8 @@ __device__ __forceinline__ uint2 row_logodds8(uint8_t *row, int8_t *lrow, int X,
     return make_uint2(lo, hi);
 }
 
-__device__ __forceinline__ void pass_x_small_row(uint8_t *xs, uint8_t *row_has, int Xp, int64_t lr, int lane,
-                                                 uint2 w) {
+template <class I>   // row index type: int64_t for tables, int for one grid
+__device__ __forceinline__ void pass_x_small_row(uint8_t *xs, uint8_t *row_has, int Xp, I lr, int lane, uint2 w) {
     constexpr int kNoLeft = -1024, kNoRight = 2048;
     const uint32_t m = nz_nibble(w.x) | (nz_nibble(w.y) << 4);
     const uint32_t B = __ballot_sync(0xffffffffu, m != 0);
@@ -542,6 +542,47 @@ __global__ void __launch_bounds__(256) k_pass_x_small(const GridDesc *__restrict
             }
         }
         if (rn >= rows_total) break;
+        r = rn;
+#pragma unroll
+        for (int q = 0; q < kXRows; ++q) w[q] = wn[q];
+    }
+}
+
+// Pass X of a table with one grid and no per-row options (a frame's map, or one map's
+// EDT): the same rows and sweeps as k_pass_x_small, with the grid's descriptor in
+// registers and 32-bit row offsets (dims <= 256: at most 65,536 rows of 256 bytes), which
+// removes the per-row table bookkeeping from the instruction stream.
+__global__ void __launch_bounds__(256) k_pass_x_one(const GridDesc *__restrict__ gd, int rows) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = static_cast<int>((gridDim.x * blockDim.x) >> 5);
+    int r = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    pdl_trigger();
+    if (r >= rows) return;
+    // the descriptor comes from the host, not from the previous kernels
+    const uint8_t *occ = gd->occ;
+    uint8_t *xs = static_cast<uint8_t *>(gd->xs);
+    uint8_t *row_has = gd->row_has;
+    const int X = gd->X, Xp = gd->Xp;
+    const bool vec = (X & 7) == 0 && (reinterpret_cast<uintptr_t>(occ) & 7) == 0;
+    pdl_wait();   // the occupancy comes from the previous kernels
+    auto load = [&](int rr) {
+        return rr < rows ? row_bytes8(occ + rr * X, X, 8 * lane, vec) : make_uint2(0u, 0u);
+    };
+    const int stride = nwarps * kXRows;
+    uint2 w[kXRows];
+#pragma unroll
+    for (int q = 0; q < kXRows; ++q) w[q] = load(r + q * nwarps);
+    for (;;) {
+        const int rn = r + stride;
+        uint2 wn[kXRows];
+#pragma unroll
+        for (int q = 0; q < kXRows; ++q) wn[q] = load(rn + q * nwarps);
+#pragma unroll
+        for (int q = 0; q < kXRows; ++q) {
+            const int rr = r + q * nwarps;
+            if (rr < rows) pass_x_small_row(xs, row_has, Xp, rr, lane, w[q]);
+        }
+        if (rn >= rows) break;
         r = rn;
 #pragma unroll
         for (int q = 0; q < kXRows; ++q) w[q] = wn[q];
@@ -1674,6 +1715,19 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s, int8_t *logodds, c
         const int nb = static_cast<int>(want_small < cap_small ? want_small : cap_small);
         const LogOdds p = lo_param ? LogOdds{lo_param[0], lo_param[1], lo_param[2], lo_param[3], lo_param[4]}
                                    : LogOdds{0, 0, 0, 0, 0};
+        if (t.n == 1 && !t.incr && !logodds) {
+            static int per_sm_one = 0;
+            if (per_sm_one == 0) {
+                int occ = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass_x_one, 256, 0) != cudaSuccess ||
+                    occ < 1)
+                    occ = 1;
+                per_sm_one = occ;
+            }
+            const int64_t cap_one = static_cast<int64_t>(sm_count()) * per_sm_one;
+            const int nb1 = static_cast<int>(want_small < cap_one ? want_small : cap_one);
+            return launch_pdl(k_pass_x_one, dim3(nb1), dim3(256), 0, s, t.desc, static_cast<int>(t.rows));
+        }
         if (logodds) {
             if (t.n != 1 || t.incr) return cudaErrorInvalidValue;
             return launch_pdl(k_pass_x_small<false, true>, dim3(nb), dim3(256), 0, s, t.desc, t.n, t.rows, logodds, p);
