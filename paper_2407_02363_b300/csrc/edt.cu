@@ -412,12 +412,13 @@ __device__ __forceinline__ uint2 row_logodds8(uint8_t *row, int8_t *lrow, int X,
 template <class I>   // row index type: int64_t for tables, int for one grid
 __device__ __forceinline__ void pass_x_small_row(uint8_t *xs, uint8_t *row_has, int Xp, I lr, int lane, uint2 w) {
     constexpr int kNoLeft = -1024, kNoRight = 2048;
-    const uint32_t m = nz_nibble(w.x) | (nz_nibble(w.y) << 4);
-    const uint32_t B = __ballot_sync(0xffffffffu, m != 0);
+    // segments holding a site; an empty row (most rows of a sparse grid) stops here
+    const uint32_t B = __ballot_sync(0xffffffffu, (w.x | w.y) != 0u);
     if (B == 0) {
         if (lane == 0) row_has[lr] = 0;
         return;
     }
+    const uint32_t m = nz_nibble(w.x) | (nz_nibble(w.y) << 4);
     const int x0 = 8 * lane;
     const uint32_t below = B & ((1u << lane) - 1u);
     const uint32_t above = B & ~((2u << lane) - 1u);
