@@ -259,9 +259,11 @@ vedt_status vedt_frame(vedt_map *map, const float *xyz_dev, int64_t n_points,
 /* The same cycle from host buffers: copies xyz_host (n_points x 3 fp32; page-locked memory
  * makes the copy asynchronous) into one of the map's two device staging buffers (grown on
  * demand, ENOMEM if that fails) on the map's own copy stream, and centres/radii into
- * device scratch; runs vedt_frame on the map's stream once the upload has landed, copies
+ * device scratch; runs vedt_frame on the map's stream once the upload has landed, delivers
  * the 2m results (ENV block first) to out_host and synchronises the stream, reporting any
- * pending in-kernel error.  1 <= m <= 4096 or m == 0. */
+ * pending in-kernel error.  If out_host is page-locked memory the device can address (for
+ * instance from cudaHostAlloc), the query kernel writes the results into it directly;
+ * otherwise they are copied after the frame.  1 <= m <= 4096 or m == 0. */
 vedt_status vedt_frame_host(vedt_map *map, const float *xyz_host, int64_t n_points,
                             const float *T_world_sensor_host, const vedt_chain *chain, const double *q,
                             uint32_t link_mask, const float *centres_host, const float *radii_host,
@@ -339,7 +341,8 @@ vedt_status vedt_batch_replay(vedt_batch *batch);
 /* Synchronises the batch's stream; ETIMEOUT if an in-kernel wait expired. */
 vedt_status vedt_batch_check(vedt_batch *batch);
 
-/* Asynchronous vedt_frame_host: the frame and the copy of the 2m results out are queued on
+/* Asynchronous vedt_frame_host: the frame and the delivery of the 2m results (written by
+ * the query kernel into a page-locked out_host, else copied after the frame) are queued on
  * the map's stream and the call returns at once.  The cloud upload goes to the staging
  * buffer the previous frame did not use, on the map's copy stream, after the frame that
  * last read that buffer has finished; so a frame queued behind a running one uploads while

@@ -789,10 +789,25 @@ vedt_status queue_host_frame(vedt_map *m, const float *xyz, int64_t n, const flo
         VCHECK(cudaEventRecord(m->copied[b], m->copy_stream));
         VCHECK(cudaStreamWaitEvent(m->stream, m->copied[b], 0));
     }
-    vedt_status st = vedt_frame(m, m->stage[b], n, T, chain, q, mask, qin, qin + 3 * kMaxQuery, nq, m->q_out);
+    // The results go straight into the caller's buffer when it is page-locked host memory
+    // the device can address: the query kernel's stores then reach the host with the
+    // frame, and no copy sits on the map's stream between this frame's query and the next
+    // frame's first kernel.  Other buffers get a copy after the frame.
+    vedt_sphere_result *direct = nullptr;
+    if (nq > 0) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, out) == cudaSuccess) {
+            if (pa.type == cudaMemoryTypeHost && pa.devicePointer)
+                direct = static_cast<vedt_sphere_result *>(pa.devicePointer);
+        } else {
+            (void)cudaGetLastError();   // an address the runtime does not know: copy
+        }
+    }
+    vedt_status st =
+        vedt_frame(m, m->stage[b], n, T, chain, q, mask, qin, qin + 3 * kMaxQuery, nq, direct ? direct : m->q_out);
     if (st != VEDT_OK) return st;
     VCHECK(cudaEventRecord(m->consumed[b], m->stream));
-    if (nq > 0)
+    if (nq > 0 && !direct)
         VCHECK(cudaMemcpyAsync(out, m->q_out, sizeof(vedt_sphere_result) * 2 * nq, cudaMemcpyDeviceToHost,
                                m->stream));
     return VEDT_OK;

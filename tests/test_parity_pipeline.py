@@ -177,7 +177,9 @@ def test_async_host_frames_back_to_back_match_sync_frames():
     """Frames queued back to back with vedt_frame_host_async alternate the two staging
     buffers, each upload running on the copy stream while the previous frame computes;
     frame by frame they give the results of the synchronous call on the same inputs.  A
-    larger cloud midway grows the staging buffers while frames are in flight."""
+    larger cloud midway grows the staging buffers while frames are in flight.  The
+    asynchronous frames' outputs are page-locked (the query kernel writes them directly),
+    the synchronous frames' are numpy arrays (copied after the frame)."""
     v = lib()
     grid = synth.GridSpec((96, 96, 96), 0.02)
     chain = synth.make_chain(4321, (0.96, 0.96, 0.96))
