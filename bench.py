@@ -706,7 +706,7 @@ def run_paper_sizes(args, v):
             m.set_bands(nb)
             by_bands[str(nb)] = time_edt()
         # the autotuner's pick for this map size (its own short sweep), then the full timing
-        best, _ = at.tune_map(m, stream, dims, op=lambda: m.compute_edt(v.MAP_ENV), reps=5, force=True,
+        best, _ = at.tune_map(m, stream, dims, op=lambda: m.compute_edt(v.MAP_ENV), reps=15, warmup=3, force=True,
                               kind="edt_env")
         tuned_ms = time_edt()
         tz = m.tile_z()
