@@ -107,13 +107,12 @@ vedt_status vedt_map_set_stream(vedt_map *map, void *stream);
  * vedt_compute_edt on.  Errors: EINVAL (NULL map, other values). */
 vedt_status vedt_map_set_bands(vedt_map *map, int bands);
 
-/* Tile shape of pass Z (Alg. 1 Step 4; a launch shape, the fields do not depend on it)
- * for grids with every dim <= 256: cols_x = 8 makes each warp's 32 columns an 8 x 4
- * patch of (x, y), cols_x = 32 a row of 32 x-adjacent columns, 0 the default (8 x 4 if X
- * is a multiple of 8, else 32 x 1).  Larger grids always take 32 x 1 (cols_x 0 or 32).
- * Synchronises the map's streams and rewrites its launch tables; a CUDA graph that holds
- * this map's EDT launches must be recorded again.  Errors: EINVAL (NULL map, other
- * values), ECUDA. */
+/* Tile shape of pass Z (Alg. 1 Step 4; a launch shape, the fields do not depend on it):
+ * cols_x = 8 makes each warp's 32 columns an 8 x 4 patch of (x, y), cols_x = 32 a row of
+ * 32 x-adjacent columns, 0 the default (grids with every dim <= 256: 8 x 4 if X is a
+ * multiple of 8, else 32 x 1; larger grids: 32 x 1).  Synchronises the map's streams and
+ * rewrites its launch tables; a CUDA graph that holds this map's EDT launches must be
+ * recorded again.  Errors: EINVAL (NULL map, other values), ECUDA. */
 vedt_status vedt_map_set_tile_z(vedt_map *map, int cols_x);
 
 /* The map's current pass-Z tile width (8 or 32; 0 for a NULL map). */
@@ -296,8 +295,8 @@ vedt_status vedt_batch_set_tuning(vedt_batch *batch, int ctas_per_sm, int rows_p
 vedt_status vedt_batch_set_bands(vedt_batch *batch, int bands);
 
 /* Pass-Z tile shape of the batch's grids with every dim <= 256, as vedt_map_set_tile_z
- * (the default looks at every such grid's X).  Applies to the plain and the persistent
- * launches.  Synchronises the batch's stream, rewrites its launch tables and drops a
+ * (the default looks at every such grid's X; the batch's larger grids keep 32 x 1, the
+ * shape of their persistent kernel).  Applies to the plain and the persistent launches.  Synchronises the batch's stream, rewrites its launch tables and drops a
  * recorded graph.  Errors: EINVAL, ECUDA. */
 vedt_status vedt_batch_set_tile_z(vedt_batch *batch, int cols_x);
 

@@ -4,8 +4,9 @@ The exact result never depends on these knobs, only the time does (the m1 / m2 /
 of Alg. 1 are PBA's tunables, Sec. III-C; Tab. 2 compares band settings).
 
 * Single maps and frames (`tune_map`): the bands per line of passes Y and Z
-  (vedt_map_set_bands: 1, 2, 4 or 8 for grids with every dim <= 256; 4 or 8 above) and
-  the pass-Z tile shape (vedt_map_set_tile_z: 8 x 4 or 32 x 1 columns, dims <= 256).
+  (vedt_map_set_bands: 1, 2, 4 or 8 for grids with every dim <= 256; above, 4, 8 or the
+  default, which takes eight bands for lines over 256 and four for the others) and
+  the pass-Z tile shape (vedt_map_set_tile_z: 8 x 4 or 32 x 1 columns).
 * Batches (`tune`): three plain launches (one per sweep) versus one persistent launch
   over a work queue, the bands per line and pass-Z tile shape of either, and for the
   persistent launch the CTAs per SM and the pass-X rows per work item
@@ -24,8 +25,8 @@ import os
 from dataclasses import asdict, dataclass
 
 BANDS_SMALL = (1, 2, 4, 8)    # grids with every dim <= 256
-BANDS_LARGE = (4, 8)
-TILES_Z = (8, 32)             # pass-Z tile widths (8 x 4, 32 x 1 columns), dims <= 256
+BANDS_LARGE = (0, 4, 8)       # 0: four or eight bands per pass by its line length
+TILES_Z = (8, 32)             # pass-Z tile widths (8 x 4, 32 x 1 columns)
 
 
 @dataclass(frozen=True)
@@ -183,8 +184,7 @@ def map_candidates(dims):
 
 def map_tunings(dims):
     """Every (bands, pass-Z tile shape) pair admitted for a map of these dims."""
-    tiles = TILES_Z if max(int(v) for v in dims) <= 256 else (0,)
-    return [MapTuning(b, tz) for tz in tiles for b in map_candidates(dims)]
+    return [MapTuning(b, tz) for tz in TILES_Z for b in map_candidates(dims)]
 
 
 def _map_entry(e) -> MapTuning:

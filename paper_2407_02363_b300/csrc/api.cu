@@ -130,7 +130,7 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
     t.maxY = t.maxZ = t.maxXp = 0;
     for (const GridDesc &g : d) t.large |= g.X > kSmallMax || g.Y > kSmallMax || g.Z > kSmallMax;
     const bool big = t.large != 0;
-    t.pzx = big ? kEnvCols : (pzx ? pzx : default_pzx(d.data(), d.size()));
+    t.pzx = pzx ? pzx : (big ? kEnvCols : default_pzx(d.data(), d.size()));
     const int px = t.pzx, py = kEnvCols / px;
     for (size_t i = 0; i < d.size(); ++i) {
         GridDesc &g = d[i];
@@ -139,7 +139,7 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
         g.tz_begin = tz;
         rows += static_cast<int64_t>(g.Y) * g.Z;
         ty += static_cast<int64_t>(g.Xp / kEnvCols) * g.Z;
-        tz += big ? static_cast<int64_t>(g.Xp / kEnvCols) * g.Y : small_tiles_z(g.Xp, g.Y, px);
+        tz += small_tiles_z(g.Xp, g.Y, px);
         t.maxY = g.Y > t.maxY ? g.Y : t.maxY;
         t.maxZ = g.Z > t.maxZ ? g.Z : t.maxZ;
         t.maxXp = g.Xp > t.maxXp ? g.Xp : t.maxXp;
@@ -150,12 +150,10 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
         if (encode_tmap(&tm[2 * i], big ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
                         big ? 2 : 1, g.xs, g.Xp, g.Y, g.Z, kEnvCols, by, 1) != CUDA_SUCCESS)
             return VEDT_ECUDA;
-        // small tables: a px x py patch of columns (rows y >= Y of a ragged last patch read
-        // as zeros); large tables: 32 columns of one row
-        const CUresult r = big ? encode_tmap(&tm[2 * i + 1], CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, g.s2, g.Xp, g.Y, g.Z,
-                                             kEnvCols, 1, bz)
-                               : encode_tmap(&tm[2 * i + 1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, g.s2, g.Xp, g.Y, g.Z,
-                                             static_cast<uint32_t>(px), static_cast<uint32_t>(py), bz);
+        // a px x py patch of columns (rows y >= Y of a ragged last patch read as zeros)
+        const CUresult r = encode_tmap(&tm[2 * i + 1], big ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                                       big ? 4 : 2, g.s2, g.Xp, g.Y, g.Z, static_cast<uint32_t>(px),
+                                       static_cast<uint32_t>(py), bz);
         if (r != CUDA_SUCCESS) return VEDT_ECUDA;
     }
     VCHECK(cudaMemcpy(dev_desc, d.data(), sizeof(GridDesc) * d.size(), cudaMemcpyHostToDevice));
@@ -426,7 +424,6 @@ vedt_status vedt_map_set_bands(vedt_map *m, int bands) {
 
 vedt_status vedt_map_set_tile_z(vedt_map *m, int cols_x) {
     if (!m || !(cols_x == 0 || cols_x == 8 || cols_x == 32)) return VEDT_EINVAL;
-    if (m->tab[0].large) return cols_x == 0 || cols_x == 32 ? VEDT_OK : VEDT_EINVAL;
     // the tables' device descriptors and tensor maps are rewritten: nothing of this map
     // may be in flight
     VCHECK(cudaStreamSynchronize(m->stream));

@@ -1196,29 +1196,31 @@ __device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, co
 }
 
 // One pass-Z tile (grid g, row y, columns x0..x0+31) with NB * 32 threads.
-template <int NB, bool L, bool kOwnBar>
+template <int NB, bool L, bool kOwnBar, int PX>
 __device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
                                              int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
                                              int32_t *err) {
     using P = PolZ<L>;
     using In = typename P::In;
+    static_assert(PX == 8 || PX == kCols, "pass-Z tiles are 8 x 4 or 32 x 1 columns");
+    constexpr int PY = kCols / PX;   // the tile is PX x PY columns (x, y); lane l owns (l % PX, l / PX)
     const int tid = threadIdx.x, lane = tid & (kTile - 1);
     const int X = gd[g].X, Y = gd[g].Y, Z = gd[g].Z, Xp = gd[g].Xp;
-    const int tiles_x = Xp / kCols;
-    const int y = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x));
-    const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
+    const int tiles_x = Xp / PX;
+    const int y0 = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x)) * PY;
+    const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * PX;
     In *in = reinterpret_cast<In *>(smem);                                        // [Z][32]
     auto *pos = reinterpret_cast<typename P::Pos *>(smem + align16(tile_in_bytes<NB, P>(Z)));
     uint8_t *region = smem + small_region_off<NB, P>(Z);
-    if (tid == 0) load_line_tile(in, &tm[2 * g + 1], Z, x0, y, false, bar);
+    if (tid == 0) load_line_tile(in, &tm[2 * g + 1], Z, x0, y0, false, bar);
     const int bl = Bands<NB, P::kMax>::len(Z);
     const int lo = (tid >> 5) * bl, hi = min(Z, lo + bl);
-    const int x = x0 + lane;
-    const bool live = x < X;
+    const int x = x0 + lane % PX, y = y0 + lane / PX;
+    const bool live = x < X && y < Y;   // a ragged last patch reads zero words past row Y - 1
     const uint32_t plane = static_cast<uint32_t>(X * Y);
     const P pol{x, y};
     EmitZs<L> e{gd[g].sqdist, gd[g].idx,
-                static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(y * X + (live ? x : 0)), plane, X, X * Y,
+                static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(live ? y * X + x : 0), plane, X, X * Y,
                 live, 0, plane * static_cast<uint32_t>(Z), err};
     bool ok;
     const int total = small_envelope<NB, P, kOwnBar>(in, pos, region, gd[g].slice_has, Z, pol, e, bar, phase, err,
@@ -1257,7 +1259,7 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_y_small(const GridDesc *__r
     tile_y_small<NB, L, true>(gd, tm, g, t - gd[g].ty_begin, smem, bar, 0, err);
 }
 
-template <int NB, bool L>
+template <int NB, bool L, int PX>
 __global__ void __launch_bounds__(NB * kTile) k_pass_z_small(const GridDesc *__restrict__ gd,
                                                              const CUtensorMap *__restrict__ tm, int ng,
                                                              int32_t *err) {
@@ -1270,7 +1272,7 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_z_small(const GridDesc *__r
     __syncthreads();
     pdl_wait();   // the staged tile and the validity flags come from the previous pass
     if (gd[g].changed && *gd[g].changed == 0) return;   // unchanged since its last EDT
-    tile_z_small<NB, L, true>(gd, tm, g, t - gd[g].tz_begin, smem, bar, 0, err);
+    tile_z_small<NB, L, true, PX>(gd, tm, g, t - gd[g].tz_begin, smem, bar, 0, err);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1784,6 +1786,7 @@ cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int 
                                : launch_env_persistent<4, 32>(t, c, ctas_per_sm, rows_per_item, s);
         }
     }
+    if (t.pzx != kCols) return cudaErrorInvalidValue;   // its pass-Z tiles are 32 x 1 rows
     if (t.maxXp <= 256) return launch_persistent_impl<8, false>(t, c, ctas_per_sm, rows_per_item, s);
     if (t.maxXp <= 512) return launch_persistent_impl<16, false>(t, c, ctas_per_sm, rows_per_item, s);
     return launch_persistent_impl<32, false>(t, c, ctas_per_sm, rows_per_item, s);
@@ -1818,8 +1821,13 @@ cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s) {
     if (t.tiles_z == 0) return cudaSuccess;
     const int nb = bands_for(t, t.maxZ);
     if (!t.large) return launch_env_z(t, nb, s);
-    if (nb == 4) return launch_small<4, k_pass_z_small<4, true>>(t.tiles_z, small_smem<4, PolZ<true>>(t.maxZ), t, s);
-    return launch_small<8, k_pass_z_small<8, true>>(t.tiles_z, small_smem<8, PolZ<true>>(t.maxZ), t, s);
+    const size_t s4 = small_smem<4, PolZ<true>>(t.maxZ), s8 = small_smem<8, PolZ<true>>(t.maxZ);
+    if (t.pzx == 8)
+        return nb == 4 ? launch_small<4, k_pass_z_small<4, true, 8>>(t.tiles_z, s4, t, s)
+                       : launch_small<8, k_pass_z_small<8, true, 8>>(t.tiles_z, s8, t, s);
+    if (t.pzx != kCols) return cudaErrorInvalidValue;   // tiles counted for another shape
+    return nb == 4 ? launch_small<4, k_pass_z_small<4, true, kCols>>(t.tiles_z, s4, t, s)
+                   : launch_small<8, k_pass_z_small<8, true, kCols>>(t.tiles_z, s8, t, s);
 }
 
 }  // namespace vedt

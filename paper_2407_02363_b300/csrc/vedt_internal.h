@@ -15,8 +15,9 @@ constexpr int kEnvCols = 32;         // columns per pass-Y/Z tile (one warp per 
 constexpr int kBox = 256;            // max TMA box extent along one dimension
 constexpr uint16_t kNoX = 0xFFFF;    // pass-X "row has no site"
 constexpr int kSmallMax = 256;       // all dims <= 256: 16-bit packed 2-D sites, 8-bit links
-// Pass-Z tile of small tables: a patch of px x (32 / px) columns (x fastest), one lane per
-// column, px = 8 or 32 (GridTable::pzx).  Columns close in both x and y have similar
+// Pass-Z tile: a patch of px x (32 / px) columns (x fastest), one lane per column, px = 8
+// or 32 (GridTable::pzx; tables with a grid above 256 default to 32 and run the persistent
+// batch kernel only with 32).  Columns close in both x and y have similar
 // envelopes along z, so an 8 x 4 patch keeps the lanes of a warp in step more often than a
 // 32 x 1 row; a row writes whole 128-byte lines of the field where an 8-wide run of a grid
 // whose X is no multiple of 8 straddles two 32-byte sectors.
@@ -43,7 +44,7 @@ struct GridDesc {
     int32_t X, Y, Z, Xp;
     int64_t row_begin;      // prefix over rows (Y*Z) of the grids before this one
     int64_t ty_begin;       // prefix over pass-Y tiles ((Xp/32)*Z)
-    int64_t tz_begin;       // prefix over pass-Z tiles (small tables: small_tiles_z; else (Xp/32)*Y)
+    int64_t tz_begin;       // prefix over pass-Z tiles (small_tiles_z)
     int64_t xi_begin;       // prefix over persistent pass-X items (ceil(Y*Z / rows_per_item))
     const uint32_t *changed;  // NULL, or a device word: 0 = occupancy unchanged since this
                               // grid's last EDT (incremental maps), so the passes skip it
@@ -59,15 +60,14 @@ struct PersistCounters {
 
 struct GridTable {
     GridDesc *desc;              // device array [n]
-    CUtensorMap *tmaps;          // device array [2n]: {xs box (32, by, 1), s2 box (32, 1, bz);
-                                 // small tables: s2 box (pzx, 32 / pzx, Z)}
+    CUtensorMap *tmaps;          // device array [2n]: {xs box (32, by, 1), s2 box (pzx, 32 / pzx, bz)}
     int n;
     int large;                   // 0: every grid has dims <= 256
     int maxY, maxZ, maxXp;
     int64_t rows, tiles_y, tiles_z;
     int32_t *err;                // device error word
     int bands;                   // bands per line in passes Y and Z (0: the default)
-    int pzx;                     // small tables: pass-Z tile width in x, 8 or 32 (see small_tiles_z)
+    int pzx;                     // pass-Z tile width in x, 8 or 32 (see small_tiles_z)
     int incr;                    // 1: pass X honours GridDesc::changed (incremental maps)
 };
 

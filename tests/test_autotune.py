@@ -24,12 +24,12 @@ def test_candidates_cover_bands_and_shapes():
     assert any(t[0] == 0 for t in small) and any(t[0] == 1 for t in small)
     # every (launch shape, bands) pair at both tile shapes
     assert {t[:4] for t in small if t[4] == 8} == {t[:4] for t in small if t[4] == 32}
-    assert {t[3] for t in autotune.batch_candidates(large=True)} == {4, 8}
+    assert {t[3] for t in autotune.batch_candidates(large=True)} == {0, 4, 8}
     assert autotune.map_candidates((256, 256, 256)) == (1, 2, 4, 8)
-    assert autotune.map_candidates((512, 512, 128)) == (4, 8)
+    assert autotune.map_candidates((512, 512, 128)) == (0, 4, 8)
     mt = autotune.map_tunings((256, 256, 256))
     assert set(mt) == {autotune.MapTuning(b, z) for b in (1, 2, 4, 8) for z in (8, 32)}
-    assert set(autotune.map_tunings((512, 512, 128))) == {autotune.MapTuning(4, 0), autotune.MapTuning(8, 0)}
+    assert set(autotune.map_tunings((512, 512, 128))) == {autotune.MapTuning(b, z) for b in (0, 4, 8) for z in (8, 32)}
 
 
 def test_pick_smallest_and_cache_roundtrip(tmp_path):

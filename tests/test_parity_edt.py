@@ -91,19 +91,22 @@ def test_tile_z_default_and_values():
             with pytest.raises(v.VedtError):
                 m.set_tile_z(bad)
     assert aligned.tile_z() == 8 and ragged.tile_z() == 32
-    large.set_tile_z(32)
-    large.set_tile_z(0)
-    with pytest.raises(v.VedtError):
-        large.set_tile_z(8)   # grids above 256 keep 32 x 1 rows
+    for tz, got in ((8, 8), (0, 32), (32, 32)):   # grids above 256 default to 32 x 1
+        large.set_tile_z(tz)
+        assert large.tile_z() == got
     for m in (aligned, ragged, large):
         m.close()
 
 
+@pytest.mark.parametrize("tile_z", [8, 32])
 @pytest.mark.parametrize("bands", [4, 8])
-def test_edt_band_count_large_mode(bands):
-    for dims, dens in (((300, 40, 250), 0.002), ((40, 513, 20), 0.01)):
+def test_edt_band_count_large_mode(bands, tile_z):
+    """Grids above 256 (16-bit row sites, 32-bit 2-D sites): lines longer than one TMA box
+    (z = 300: two boxes, the second read past the grid), Y no multiple of 4, X no multiple
+    of 8, at both pass-Z tile shapes."""
+    for dims, dens in (((300, 40, 250), 0.002), ((40, 513, 20), 0.01), ((100, 30, 300), 0.01)):
         occ = synth.random_occupancy(41 + bands + sum(dims), dims, dens)
-        (sq, ix), = run_gpu_edt(occ, bands=bands)
+        (sq, ix), = run_gpu_edt(occ, bands=bands, tile_z=tile_z)
         assert_parity(occ, sq, ix)
 
 
