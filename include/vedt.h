@@ -109,8 +109,8 @@ vedt_status vedt_map_set_bands(vedt_map *map, int bands);
 
 /* Tile shape of pass Z (Alg. 1 Step 4; a launch shape, the fields do not depend on it):
  * cols_x = 8 makes each warp's 32 columns an 8 x 4 patch of (x, y), cols_x = 32 a row of
- * 32 x-adjacent columns, 0 the default (grids with every dim <= 256: 8 x 4 if X is a
- * multiple of 8, else 32 x 1; larger grids: 32 x 1).  Synchronises the map's streams and
+ * 32 x-adjacent columns, 0 the default (8 x 4 if X is a multiple of 8, else 32 x 1).
+ * Synchronises the map's streams and
  * rewrites its launch tables; a CUDA graph that holds this map's EDT launches must be
  * recorded again.  Errors: EINVAL (NULL map, other values), ECUDA. */
 vedt_status vedt_map_set_tile_z(vedt_map *map, int cols_x);

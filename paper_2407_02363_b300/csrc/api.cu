@@ -130,7 +130,7 @@ vedt_status build_table(GridTable &t, const std::vector<GridDesc> &grids, void *
     t.maxY = t.maxZ = t.maxXp = 0;
     for (const GridDesc &g : d) t.large |= g.X > kSmallMax || g.Y > kSmallMax || g.Z > kSmallMax;
     const bool big = t.large != 0;
-    t.pzx = pzx ? pzx : (big ? kEnvCols : default_pzx(d.data(), d.size()));
+    t.pzx = pzx ? pzx : default_pzx(d.data(), d.size());
     const int px = t.pzx, py = kEnvCols / px;
     for (size_t i = 0; i < d.size(); ++i) {
         GridDesc &g = d[i];

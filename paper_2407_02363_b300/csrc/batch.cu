@@ -231,7 +231,8 @@ vedt_status build_tables(vedt_batch *b) {
         off += (sizeof(GridDesc) * nd + 127) / 128 * 128;
         char *tm = base + off;
         off += sizeof(CUtensorMap) * 2 * nd;
-        vedt_status st = build_table(b->tab[md], mode[md], desc, tm, b->err, md == 0 ? b->pzx : 0);
+        // the large-grid table keeps 32 x 1 pass-Z tiles, the shape of its persistent kernel
+        vedt_status st = build_table(b->tab[md], mode[md], desc, tm, b->err, md == 0 ? b->pzx : kEnvCols);
         if (st != VEDT_OK) return st;
         b->tab[md].bands = md == 0 ? b->bands : ((b->bands == 4 || b->bands == 8) ? b->bands : 0);
     }

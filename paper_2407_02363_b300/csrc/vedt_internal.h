@@ -16,8 +16,8 @@ constexpr int kBox = 256;            // max TMA box extent along one dimension
 constexpr uint16_t kNoX = 0xFFFF;    // pass-X "row has no site"
 constexpr int kSmallMax = 256;       // all dims <= 256: 16-bit packed 2-D sites, 8-bit links
 // Pass-Z tile: a patch of px x (32 / px) columns (x fastest), one lane per column, px = 8
-// or 32 (GridTable::pzx; tables with a grid above 256 default to 32 and run the persistent
-// batch kernel only with 32).  Columns close in both x and y have similar
+// or 32 (GridTable::pzx; a batch's table of grids above 256 keeps 32, the shape of its
+// persistent kernel).  Columns close in both x and y have similar
 // envelopes along z, so an 8 x 4 patch keeps the lanes of a warp in step more often than a
 // 32 x 1 row; a row writes whole 128-byte lines of the field where an 8-wide run of a grid
 // whose X is no multiple of 8 straddles two 32-byte sectors.
@@ -108,8 +108,8 @@ cudaError_t ensure_dyn_smem(size_t bytes) {
 // host-side helpers (api.cu)
 CUresult encode_tmap(CUtensorMap *m, CUtensorMapDataType t, int elem, void *base,
                      uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1, uint32_t b2);
-// Pass-Z tile width of a small table when none is set: 8 x 4 patches if every grid's X
-// is a multiple of 8 (whole 32-byte sectors per run), else 32 x 1 rows.
+// Pass-Z tile width of a table when none is set: 8 x 4 patches if every grid's X is a
+// multiple of 8 (whole 32-byte sectors per run), else 32 x 1 rows.
 int default_pzx(const GridDesc *grids, size_t n);
 
 // SM count of the current device, cached per device (insert.cu)

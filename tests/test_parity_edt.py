@@ -81,20 +81,21 @@ def test_edt_band_count_does_not_change_the_field(bands, tile_z):
 
 
 def test_tile_z_default_and_values():
+    """The default pass-Z tile is 8 x 4 when X is a multiple of 8, else 32 x 1, for grids
+    up to 256 and above; 8 and 32 are settable, nothing else."""
     v = lib()
-    aligned, ragged, large = v.Map((64, 30, 20), 0.01), v.Map((45, 30, 20), 0.01), v.Map((300, 8, 8), 0.01)
-    assert aligned.tile_z() == 8 and ragged.tile_z() == 32 and large.tile_z() == 32
-    for m in (aligned, ragged):
-        for tz in (8, 32, 0):
+    maps = {dims: v.Map(dims, 0.01) for dims in ((64, 30, 20), (45, 30, 20), (304, 8, 8), (300, 8, 8))}
+    assert [m.tile_z() for m in maps.values()] == [8, 32, 8, 32]
+    for dims, m in maps.items():
+        default = m.tile_z()
+        for tz in (8, 32):
             m.set_tile_z(tz)
+            assert m.tile_z() == tz
+        m.set_tile_z(0)
+        assert m.tile_z() == default
         for bad in (4, 16, -1, 64):
             with pytest.raises(v.VedtError):
                 m.set_tile_z(bad)
-    assert aligned.tile_z() == 8 and ragged.tile_z() == 32
-    for tz, got in ((8, 8), (0, 32), (32, 32)):   # grids above 256 default to 32 x 1
-        large.set_tile_z(tz)
-        assert large.tile_z() == got
-    for m in (aligned, ragged, large):
         m.close()
 
 
