@@ -474,9 +474,9 @@ vedt_status vedt_sor_mean_distances(vedt_sor *f, const double **d_dev);
  * stream that is being captured (VEDT_ENOTSUP).  Scratch comes from one fixed array of
  * about 6.4 MB that the library keeps in every GPU's memory until the process exits: each
  * dimension must be <= 256 and ceil(X/32)*32*Y*Z <= 2^21 (a 128^3 grid fits), otherwise
- * the call returns VEDT_ENOTSUP without doing anything.  The first call on a device looks
- * the array up (cudaGetSymbolAddress); like every handle of this library, that address
- * does not survive cudaDeviceReset.  Calls share the array and leave their scratch in it;
+ * the call returns VEDT_ENOTSUP without doing anything.  Each call looks the array up on
+ * the current device (cudaGetSymbolAddress), so it is found again after a device reset.
+ * Calls share the array and leave their scratch in it;
  * calls that may overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.
  * Errors: EINVAL (null pointer, dims < 1), ENOTSUP (grid larger than the scratch, stream

@@ -16,7 +16,6 @@
 // so nothing refers to this call's stack once it returns).  The call waits for its
 // passes and reads the device error word back, so a bounds error flagged by the
 // index-checked build or an expired in-kernel wait is returned to the caller.
-#include <mutex>
 #include <vector>
 
 #include "vedt_internal.h"
@@ -32,29 +31,12 @@ constexpr size_t kScratchBytes = kHeader + 3 * kNoallocMaxVoxels + 256 * 256 + 1
 // file-scope scratch: [header | xs (1 B/voxel) | s2 (2 B/voxel) | row flags | slice flags]
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_base[kMaxDevices] = {};
-
-// Device address of the scratch array for the current device, looked up once per device.
-// In host code g_noalloc_scratch only names a host-side stand-in, so its device address
-// must come from cudaGetSymbolAddress with that device current.  (Like every handle of
-// this library, the address does not survive cudaDeviceReset of its device.)
-cudaError_t scratch_base(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_base[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_base[dev] = p;
-    }
-    *out = g_base[dev];
-    return cudaSuccess;
-}
+// Device address of the scratch array on the current device.  In host code
+// g_noalloc_scratch only names a host-side stand-in, so its device address comes from
+// cudaGetSymbolAddress with that device current.  It is looked up on every call (a
+// runtime table lookup; the call synchronises anyway), so a module that the runtime has
+// loaded again, after cudaDeviceReset or on another context, is found where it now is.
+cudaError_t scratch_base(void **out) { return cudaGetSymbolAddress(out, g_noalloc_scratch); }
 
 // The scratch header of one call: grid descriptor, the two tensor maps (64-byte aligned
 // for TMA) and the cleared error word, written by thread 0 from the launch parameters.
