@@ -10,23 +10,25 @@
 //   pass Z  (Step 4, the same along the stacking axis): per column (x, y) the lower
 //           envelope of g2(z') + (z - z')^2, producing sqdist and a nearest voxel index.
 //
-// Passes Y and Z run one CTA of NB warps per 32 adjacent columns (NB = 4 by default, 8
-// for lines longer than 256; the m2 / m3 banding of Alg. 1): lane t owns column t, warp b
-// the b-th band of every line, so every global access is coalesced across x and all lanes
-// of a warp scan the same positions.  The tile (32 columns x the whole line) is staged
-// into shared memory with TMA box loads.  Each warp builds its band's stacks of proximate
+// Passes Y and Z run one CTA of NB warps per tile of 32 columns (the m2 / m3 banding of
+// Alg. 1): lane t owns column t, warp b the b-th band of every line, so all lanes of a
+// warp scan the same positions.  The tile (32 columns x the whole line) is staged into
+// shared memory with TMA box loads.  Each warp builds its band's stacks of proximate
 // sites in place in the staged tile; after a CTA barrier warp 0 joins the bands of each
 // column (the junction repair) and publishes the kept ranges, and every warp walks the
-// merged envelope over its band.  The persistent batch kernel runs two-band tiles of 64
-// threads.  The domination test is exact integer arithmetic with h_s = f(s) + s^2:
+// merged envelope over its band.  The domination test is exact integer arithmetic with
+// h_s = f(s) + s^2:
 //   b (above a) is dropped under c  iff  (h_c - h_b)(b - a) <= (h_b - h_a)(c - b),
 // i.e. c overtakes b no later than b overtakes a.  In the query the next proximate site
 // p+1 is strictly nearer to voxel j iff h_(p+1) - h_p < 2 j (c_(p+1) - c_p).
 //
-// Small mode (every dim <= 256): pass X writes 8-bit row sites plus a per-row flag,
-// pass Y 16-bit packed 2-D sites (x | y << 8), stack positions are 8-bit.  Large mode
-// (dims up to 1024): 16-bit row sites, 32-bit packed sites (x | y << 16), 64-bit products
-// in the domination test; pass Z keeps stack positions in the sites' free bits.
+// This file holds pass X for every size (k_pass_x_one and k_pass_x_small for grids with
+// every dim <= 256: 8-bit row sites and a per-row flag; k_pass_x above: 16-bit row
+// sites), passes Y and Z for grids above 256 (tile_y_small / tile_z_small with L = true:
+// 16-bit row sites and stack positions, 32-bit packed 2-D sites x | y << 16, 64-bit
+// products in the domination test; NB = 4 bands for lines up to 256, 8 beyond), and the
+// two persistent batch kernels.  Passes Y and Z of grids with every dim <= 256 are in
+// envelope.cu / envelope.cuh.
 #include <climits>
 #include <type_traits>
 
@@ -148,209 +150,21 @@ __device__ __forceinline__ void drain_after_timeout(uint64_t *bar, uint32_t phas
 }
 
 constexpr int kCols = kEnvCols;   // columns per tile (one thread per column and half)
-constexpr int kLanes = 2 * kTile;  // threads per pass-Y/Z CTA; stride of the stack arrays
-
-template <bool SMALL>
-struct Env {
-    using Link = typename std::conditional<SMALL, uint8_t, uint16_t>::type;
-    using XS = typename std::conditional<SMALL, uint8_t, uint16_t>::type;     // pass-X site
-    using Site = typename std::conditional<SMALL, uint16_t, uint32_t>::type;  // pass-Y site
-    using Prod = typename std::conditional<SMALL, int, long long>::type;
-    static constexpr int kNoLink = SMALL ? 0xFF : 0xFFFF;
-    static constexpr int kShift = SMALL ? 8 : 16;
-    static constexpr uint32_t kMask = SMALL ? 0xFFu : 0xFFFFu;
-};
-
-// ------------------------------------------------------------------------------------
-// Envelope along one line (Steps 2-3) in two bands: each thread builds the stack of
-// proximate sites of its half of the line (stk[i * 64] = position of its i-th proximate
-// site from the bottom), sweeping its positions upward and popping dominated sites.
-//
-// `Line` supplies for position q: raw(q) (input word), valid(q, raw) and
-// h(raw, q^2) = f(q) + q^2.
-// ------------------------------------------------------------------------------------
-template <bool SMALL, class Line>
-__device__ __forceinline__ int build_stack(int lo, int hi, typename Env<SMALL>::Link *stk, const Line &L) {
-    using Prod = typename Env<SMALL>::Prod;
-    int k = 0, a = 0, b = 0, ha = 0, hb = 0, dab = 0, wab = 0;
-    int c2 = lo * lo;
-    for (int c = lo; c < hi; c2 += 2 * c + 1, ++c) {
-        const uint32_t r = L.raw(c);
-        if (!L.valid(c, r)) continue;
-        const int hc = L.h(r, c2);
-        while (k >= 2 && static_cast<Prod>(hc - hb) * wab <= static_cast<Prod>(dab) * (c - b)) {
-            --k;
-            b = a;
-            hb = ha;
-            if (k >= 2) {
-                a = stk[(k - 2) * kLanes];
-                ha = L.h(L.raw(a), a * a);
-                dab = hb - ha;
-                wab = b - a;
-            }
-        }
-        stk[k * kLanes] = static_cast<typename Env<SMALL>::Link>(c);
-        dab = hc - hb;
-        wab = c - b;
-        a = b;
-        ha = hb;
-        b = c;
-        hb = hc;
-        ++k;
-    }
-    return k;
-}
-
-// Merged envelope of the two halves of a line: the lower half's stack kept up to entry
-// i, then the upper half's stack from entry j on.  Only the junction can violate the
-// envelope's ordering, so the top of the lower stack is dropped while the next site up
-// dominates it, and the bottom of the upper stack while the site below does (both lanes
-// of a line compute the same result independently).
-template <bool SMALL, class Line>
-struct Merged {
-    const typename Env<SMALL>::Link *lo_stk, *up_stk;
-    int i, j, kU, m;      // m = merged length
-    __device__ __forceinline__ int at(int t) const {
-        return t <= i ? lo_stk[t * kLanes] : up_stk[(t - i - 1 + j) * kLanes];
-    }
-    __device__ __forceinline__ void build(const Line &L, int kL) {
-        using Prod = typename Env<SMALL>::Prod;
-        i = kL - 1;
-        j = 0;
-        for (;;) {
-            if (i >= 1 && j < kU) {
-                const int a = lo_stk[(i - 1) * kLanes], b = lo_stk[i * kLanes], c = up_stk[j * kLanes];
-                const int ha = L.h(L.raw(a), a * a), hb = L.h(L.raw(b), b * b), hc = L.h(L.raw(c), c * c);
-                if (static_cast<Prod>(hc - hb) * (b - a) <= static_cast<Prod>(hb - ha) * (c - b)) {
-                    --i;
-                    continue;
-                }
-            }
-            if (i >= 0 && j + 1 < kU) {
-                const int a = lo_stk[i * kLanes], b = up_stk[j * kLanes], c = up_stk[(j + 1) * kLanes];
-                const int ha = L.h(L.raw(a), a * a), hb = L.h(L.raw(b), b * b), hc = L.h(L.raw(c), c * c);
-                if (static_cast<Prod>(hc - hb) * (b - a) <= static_cast<Prod>(hb - ha) * (c - b)) {
-                    ++j;
-                    continue;
-                }
-            }
-            break;
-        }
-        m = (i + 1) + (kU - j);
-    }
-};
-
-// Walks the merged envelope forward over voxels [lo, hi) and calls emit.site(c, raw)
-// when the nearest proximate site changes and emit.put(val) per voxel, val = f(c) +
-// (j - c)^2 kept incrementally.  The next site p+1 is nearer to voxel j iff
-// h1 - h0 < 2 j (c1 - c0); that threshold is kept incrementally too.
-template <bool SMALL, class Line, class Emit>
-__device__ __forceinline__ void query_merged(const Merged<SMALL, Line> &M, int lo, int hi, bool upper,
-                                             const Line &L, Emit &emit) {
-    // starting entry: the bottom for the lower half; for the upper half the entry nearest
-    // to voxel lo, searched from the junction
-    int p = 0;
-    if (upper) {
-        p = M.i + 1 < M.m ? M.i + 1 : M.m - 1;
-        int c = M.at(p);
-        int v = L.h(L.raw(c), c * c) - 2 * lo * c;
-        while (p > 0) {
-            const int cb = M.at(p - 1);
-            const int vb = L.h(L.raw(cb), cb * cb) - 2 * lo * cb;
-            if (vb > v) break;
-            --p;
-            v = vb;
-        }
-    }
-    int c0 = M.at(p);
-    uint32_t r0 = L.raw(c0);
-    int h0 = L.h(r0, c0 * c0);
-    int c1 = 0, h1 = 0, dc2 = 0, dh = 0;
-    uint32_t r1 = 0;
-    const bool more0 = p + 1 < M.m;
-    if (more0) {
-        c1 = M.at(p + 1);
-        r1 = L.raw(c1);
-        h1 = L.h(r1, c1 * c1);
-        dc2 = 2 * (c1 - c0);
-        dh = h1 - h0;
-    }
-    bool more = more0;
-    int thr = lo * dc2;          // 2 j (c1 - c0)
-    int val = h0 - 2 * lo * c0 + lo * lo;
-    int inc = 2 * (lo - c0) + 1; // val(j+1) - val(j)
-    emit.site(c0, r0);
-    for (int j = lo; j < hi; ++j) {
-        if (more && dh < thr) {
-            do {
-                ++p;
-                c0 = c1;
-                r0 = r1;
-                h0 = h1;
-                more = p + 1 < M.m;
-                if (more) {
-                    c1 = M.at(p + 1);
-                    r1 = L.raw(c1);
-                    h1 = L.h(r1, c1 * c1);
-                    dc2 = 2 * (c1 - c0);
-                    dh = h1 - h0;
-                    thr = j * dc2;
-                }
-            } while (more && dh < thr);
-            val = h0 - 2 * j * c0 + j * j;
-            inc = 2 * (j - c0) + 1;
-            emit.site(c0, r0);
-        }
-        emit.put(val);
-        val += inc;
-        inc += 2;
-        thr += dc2;
-    }
-}
-
-// Both halves of 32 lines: thread tid owns line (tid & 31), warp (tid >> 5) the half.
-// The stacks are [entry][64 threads]; `ks` is 64 ints of shared scratch.
-template <bool SMALL, class Line, class Emit>
-__device__ __forceinline__ void envelope_two_warps(int n, int tid, typename Env<SMALL>::Link *stack, int *ks,
-                                                   const Line &L, Emit &emit, int &k_total) {
-    const bool upper = tid >= kTile;
-    const int half = (n + 1) >> 1;
-    const int lo = upper ? half : 0, hi = upper ? n : half;
-    typename Env<SMALL>::Link *own = stack + tid;
-    const int k = build_stack<SMALL>(lo, hi, own, L);
-    ks[tid] = k;
-    __syncthreads();
-    const int k_oth = ks[tid ^ kTile];
-    const int kL = upper ? k_oth : k, kU = upper ? k : k_oth;
-    k_total = kL + kU;
-    Merged<SMALL, Line> M;
-    M.lo_stk = stack + (tid & (kTile - 1));
-    M.up_stk = M.lo_stk + kTile;
-    M.kU = kU;
-    if (kL + kU == 0) {
-        for (int j = lo; j < hi; ++j) emit.put(INT_MAX);
-        return;
-    }
-    M.build(L, kL);
-    query_merged<SMALL>(M, lo, hi, upper, L, emit);
-}
+constexpr int kLanes = 2 * kTile;  // threads per CTA of the large-grid persistent kernel (two bands)
 
 // ====================================================================================
-// Small mode (every dim <= 256): lean passes.
+// Pass X of grids with every dim <= 256: one warp per row, lane l owning voxels
+// [8l, 8l + 8).  A ballot of the non-empty 8-byte segments ends an empty row (it only
+// clears its flag: pass Y never reads its sites); otherwise the row's occupancy becomes
+// one 8-bit mask per lane, and two shuffles give every lane the nearest occupied x left
+// and right of its segment.  A segment with no site splits at the midpoint of those two;
+// a segment with sites takes two register sweeps.
 //
-// Pass X: one warp per row, lane l owning voxels [8l, 8l + 8).  The row's occupancy
-// becomes one 8-bit mask per lane; a ballot of the non-empty segments and two shuffles
-// give every lane the nearest occupied x left and right of its segment.  A segment with
-// no site splits at the midpoint of those two; a segment with sites takes two register
-// sweeps.  Rows without a site only clear their flag (pass Y never reads their sites).
-//
-// Passes Y and Z: one 64-thread CTA per 32 columns of a line family; warp b owns band b
-// (the lower or upper half of every line), lane l column x0 + l.  The valid positions of
-// a band (rows / slices holding a site, the same for every column) are ballot bitmasks,
-// so the sweep visits only them, uniformly across the warp.  A band's stack of proximate
-// sites lives in place: entry k keeps its staged input word in slot lo + k of the tile
-// (a slot the sweep has already read) and its position in pos[k][tid], so a pop, the
-// junction merge and the query read both words directly.
+// Below it, the band tiles of passes Y and Z templated on the word sizes (L = true: grids
+// above 256).  A band's stack of proximate sites lives in place: entry k keeps its staged
+// input word in slot lo + k of the tile (a slot the sweep has already read) and its
+// position in pos[k][tid], so a pop, the junction merge and the query read both words
+// directly.
 // ====================================================================================
 __device__ __forceinline__ uint32_t nz_nibble(uint32_t w) {
     // bit i = (byte i != 0): set bit 7 of every non-zero byte, then gather bits 7, 15,
@@ -1276,196 +1090,6 @@ __global__ void __launch_bounds__(NB * kTile) k_pass_z_small(const GridDesc *__r
 }
 
 // ------------------------------------------------------------------------------------
-// pass Y: tile = (grid, slice z, 16 columns x0..x0+15), line along y
-// ------------------------------------------------------------------------------------
-
-template <bool SMALL>
-struct LineY {
-    const typename Env<SMALL>::XS *col;   // this thread's column of the staged tile (stride 32)
-    const uint8_t *rh;                    // small mode: row flags of the slice
-    int x;
-    __device__ __forceinline__ uint32_t raw(int q) const { return col[q * kCols]; }
-    __device__ __forceinline__ bool valid(int q, uint32_t r) const { return SMALL ? rh[q] != 0 : r != kNoX; }
-    __device__ __forceinline__ int h(uint32_t r, int q2) const {
-        const int d = x - static_cast<int>(r);
-        return d * d + q2;
-    }
-};
-
-template <bool SMALL>
-struct EmitY {
-    typename Env<SMALL>::Site *po;
-    int Xp;
-    typename Env<SMALL>::Site v;
-    int64_t left;   // elements from po to the end of the buffer (debug bounds checks)
-    int32_t *err;
-    __device__ __forceinline__ void site(int c, uint32_t r) {
-        v = static_cast<typename Env<SMALL>::Site>(r | (static_cast<uint32_t>(c) << Env<SMALL>::kShift));
-    }
-    __device__ __forceinline__ void put(int val) {
-        if (in_range(0, left, err)) *po = val == INT_MAX ? static_cast<typename Env<SMALL>::Site>(~0u) : v;
-        po += Xp;
-        if constexpr (kCheckBounds) left -= Xp;
-    }
-};
-
-// One pass-Y tile (grid g, tile lt of that grid).  `phase` is the parity of the tile
-// barrier's current phase; the barrier must have been initialised.  Returns false if
-// the staging wait timed out.  Ends with a CTA barrier so the caller may reuse smem.
-template <bool SMALL>
-__device__ __forceinline__ bool tile_y_generic(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
-                                               int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
-                                               int32_t *err) {
-    using E = Env<SMALL>;
-    using Link = typename E::Link;
-    using XS = typename E::XS;
-    using Site = typename E::Site;
-    const int tid = threadIdx.x;
-    const int Y = gd[g].Y, Xp = gd[g].Xp;
-    const int tiles_x = Xp / kCols;
-    const int z = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x));
-    const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
-    const int by = min(Y, kBox);
-    const int nbox = (Y + by - 1) / by;
-    const int half = (Y + 1) >> 1;
-    const size_t in_bytes = static_cast<size_t>(nbox) * by * kCols * sizeof(XS);
-    XS *in = reinterpret_cast<XS *>(smem);                                    // [nbox*by][32]
-    Link *stack = reinterpret_cast<Link *>(smem + in_bytes);                  // [half][64]
-    int *ks = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(stack + static_cast<size_t>(half) * kLanes) + 15) &
-                                      ~uintptr_t(15));                        // [64]
-    uint8_t *rh = reinterpret_cast<uint8_t *>(ks + kLanes);                   // [Y]
-    if (tid == 0) {
-        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(in_bytes));
-        for (int b = 0; b < nbox; ++b)
-            tma_load_3d(in + static_cast<size_t>(b) * by * kCols, &tm[2 * g], x0, b * by, z, bar);
-    }
-    if (SMALL) {
-        const uint8_t *src = gd[g].row_has + static_cast<int64_t>(z) * Y;
-        for (int q = tid; q < Y; q += kLanes) rh[q] = src[q];
-    }
-    __syncthreads();
-    if (!mbar_wait_bounded(bar, phase, err)) {
-        drain_after_timeout(bar, phase);
-        __syncthreads();
-        return false;
-    }
-    const int ci = tid & (kCols - 1);
-    const int lo = tid >= kTile ? half : 0;
-    const LineY<SMALL> L{in + ci, rh, x0 + ci};
-    const int64_t oy = (static_cast<int64_t>(z) * Y + lo) * Xp + x0 + ci;
-    EmitY<SMALL> emit{reinterpret_cast<Site *>(gd[g].s2) + oy, Xp, 0, static_cast<int64_t>(Xp) * Y * gd[g].Z - oy, err};
-    int k_total;
-    envelope_two_warps<SMALL>(Y, tid, stack, ks, L, emit, k_total);
-    if (x0 == 0 && tid == 0) gd[g].slice_has[z] = k_total > 0 ? 1 : 0;
-    __syncthreads();
-    return true;
-}
-
-// a pass-Y tile of the persistent kernel for tables with a grid above 256 (small tables
-// run k_env_persistent)
-template <bool SMALL>
-__device__ __forceinline__ bool tile_y(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
-                                       int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
-    static_assert(!SMALL, "tables with every dim <= 256 run k_env_persistent");
-    return tile_y_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
-}
-
-// ------------------------------------------------------------------------------------
-// pass Z: tile = (grid, row y, 16 columns x0..x0+15), line along z
-// ------------------------------------------------------------------------------------
-template <bool SMALL>
-struct LineZ {
-    const typename Env<SMALL>::Site *col;
-    const uint8_t *has;
-    int x, y;
-    __device__ __forceinline__ uint32_t raw(int q) const { return col[q * kCols]; }
-    __device__ __forceinline__ bool valid(int q, uint32_t) const { return has[q] != 0; }
-    __device__ __forceinline__ int h(uint32_t r, int q2) const {
-        const int dx = x - static_cast<int>(r & Env<SMALL>::kMask);
-        const int dy = y - static_cast<int>(r >> Env<SMALL>::kShift);
-        return dx * dx + dy * dy + q2;
-    }
-};
-
-template <bool SMALL>
-struct EmitZ {
-    int32_t *osq, *oix;
-    int64_t plane;
-    int X, XY;
-    int32_t id;
-    bool live;
-    int64_t left;   // voxels from osq to the end of the field (debug bounds checks)
-    int32_t *err;
-    __device__ __forceinline__ void site(int c, uint32_t r) {
-        id = static_cast<int32_t>(r & Env<SMALL>::kMask) + X * static_cast<int32_t>(r >> Env<SMALL>::kShift) + XY * c;
-    }
-    __device__ __forceinline__ void put(int val) {
-        if (live && in_range(0, left, err)) {
-            *osq = val;
-            *oix = val == INT_MAX ? -1 : id;
-        }
-        osq += plane;
-        oix += plane;
-        if constexpr (kCheckBounds) left -= plane;
-    }
-};
-
-template <bool SMALL>
-__device__ __forceinline__ bool tile_z_generic(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
-                                               int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
-                                               int32_t *err) {
-    using E = Env<SMALL>;
-    using Link = typename E::Link;
-    using Site = typename E::Site;
-    const int tid = threadIdx.x;
-    const int X = gd[g].X, Y = gd[g].Y, Z = gd[g].Z, Xp = gd[g].Xp;
-    const int tiles_x = Xp / kCols;
-    const int y = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x));
-    const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
-    const int bz = min(Z, kBox);
-    const int nbox = (Z + bz - 1) / bz;
-    const int half = (Z + 1) >> 1;
-    const size_t in_bytes = static_cast<size_t>(nbox) * bz * kCols * sizeof(Site);
-    Site *in = reinterpret_cast<Site *>(smem);                                  // [nbox*bz][32]
-    Link *stack = reinterpret_cast<Link *>(smem + in_bytes);                    // [half][64]
-    int *ks = reinterpret_cast<int *>((reinterpret_cast<uintptr_t>(stack + static_cast<size_t>(half) * kLanes) + 15) &
-                                      ~uintptr_t(15));                          // [64]
-    uint8_t *has = reinterpret_cast<uint8_t *>(ks + kLanes);                    // [Z]
-    if (tid == 0) {
-        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(in_bytes));
-        for (int b = 0; b < nbox; ++b)
-            tma_load_3d(in + static_cast<size_t>(b) * bz * kCols, &tm[2 * g + 1], x0, y, b * bz, bar);
-    }
-    for (int q = tid; q < Z; q += kLanes) has[q] = gd[g].slice_has[q];
-    __syncthreads();
-    if (!mbar_wait_bounded(bar, phase, err)) {
-        drain_after_timeout(bar, phase);
-        __syncthreads();
-        return false;
-    }
-    const int ci = tid & (kCols - 1);
-    const int lo = tid >= kTile ? half : 0;
-    const int x = x0 + ci;
-    const LineZ<SMALL> L{in + ci, has, x, y};
-    const int64_t plane = static_cast<int64_t>(X) * Y;
-    const int xc = x < X ? x : X - 1;   // padding columns build but never store
-    const int64_t off = static_cast<int64_t>(lo) * plane + static_cast<int64_t>(y) * X + xc;
-    EmitZ<SMALL> emit{gd[g].sqdist + off, gd[g].idx + off, plane, X, X * Y, -1, x < X, plane * Z - off, err};
-    int k_total;
-    envelope_two_warps<SMALL>(Z, tid, stack, ks, L, emit, k_total);
-    __syncthreads();
-    return true;
-}
-
-// a pass-Z tile of the persistent kernel for tables with a grid above 256
-template <bool SMALL>
-__device__ __forceinline__ bool tile_z(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm, int g,
-                                       int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase, int32_t *err) {
-    static_assert(!SMALL, "tables with every dim <= 256 run k_env_persistent");
-    return tile_z_generic<false>(gd, tm, g, lt, smem, bar, phase, err);
-}
-
-// ------------------------------------------------------------------------------------
 // persistent EDT over a whole table: one launch, work items dequeued in order
 //   [0, nX)            pass-X items (rows_per_item rows of one grid)
 //   [nX, nX + nY)      pass-Y tiles, each waiting for its grid's pass-X items
@@ -1500,7 +1124,12 @@ cudaError_t launch_wait_selftest(const unsigned *counter, uint32_t limit, int32_
     return cudaGetLastError();
 }
 
-template <int S, bool SMALL>
+// Persistent EDT for tables with a grid above 256: the large-grid pass X and two-band
+// large-grid tiles (tile_y_small / tile_z_small with 16-bit row sites and positions,
+// 32-bit 2-D sites, 32 x 1 pass-Z tiles).  The tile area of shared memory is reused from
+// tile to tile: every thread fences its generic accesses of a tile against the async
+// proxy before the CTA barrier that precedes the next tile's TMA load into the same bytes.
+template <int S>
 __global__ void __launch_bounds__(kLanes) k_edt_persistent(const GridDesc *__restrict__ gd,
                                                            const CUtensorMap *__restrict__ tm, int ng,
                                                            PersistCounters cnt, int rows_per_item, int32_t *err) {
@@ -1530,53 +1159,36 @@ __global__ void __launch_bounds__(kLanes) k_edt_persistent(const GridDesc *__res
             const int64_t rows = static_cast<int64_t>(gd[g].Y) * gd[g].Z;
             const int64_t r0 = static_cast<int64_t>(it - gd[g].xi_begin) * rows_per_item;
             const int64_t r1 = min(rows, r0 + rows_per_item);
-            for (int64_t r = r0 + warp; r < r1; r += kLanes / 32) {
-                if constexpr (SMALL) {
-                    const GridDesc &G = gd[g];
-                    const bool vec = (G.X & 7) == 0 && (reinterpret_cast<uintptr_t>(G.occ) & 7) == 0;
-                    pass_x_small_row(static_cast<uint8_t *>(G.xs), G.row_has, G.Xp, r, lane,
-                                     row_bytes8(G.occ + r * G.X, G.X, 8 * lane, vec));
-                } else {
-                    pass_x_row<S, SMALL>(gd[g], r, lane);
-                }
-            }
+            for (int64_t r = r0 + warp; r < r1; r += kLanes / 32) pass_x_row<S, false>(gd[g], r, lane);
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
                 atomicAdd(cnt.done_x + g, 1u);
             }
-        } else if (it < nX + nY) {
-            const int64_t t = it - nX;
-            const int g = find_grid(gd, ng, t, 0);
+        } else {
+            const bool is_y = it < nX + nY;
+            const int64_t t = is_y ? it - nX : it - nX - nY;
+            const int g = find_grid(gd, ng, t, is_y ? 0 : 1);
             if (tid == 0) {
-                const unsigned need = static_cast<unsigned>((static_cast<int64_t>(gd[g].Y) * gd[g].Z + rows_per_item - 1) /
-                                                            rows_per_item);
-                ok_s = wait_count(cnt.done_x + g, need, err);
+                const unsigned need =
+                    is_y ? static_cast<unsigned>((static_cast<int64_t>(gd[g].Y) * gd[g].Z + rows_per_item - 1) /
+                                                 rows_per_item)
+                         : static_cast<unsigned>(static_cast<int64_t>(gd[g].Xp / kCols) * gd[g].Z);
+                ok_s = wait_count(is_y ? cnt.done_x + g : cnt.done_y + g, need, err);
                 __threadfence();
-                asm volatile("fence.proxy.async.global;" ::: "memory");
+                asm volatile("fence.proxy.async.global;" ::: "memory");   // generic writes -> TMA reads
             }
             __syncthreads();
             if (ok_s) {
-                tile_y<SMALL>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, phase, err);
+                if (is_y) tile_y_small<2, true, false>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, phase, err);
+                else tile_z_small<2, true, false, kCols>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, phase, err);
                 phase ^= 1u;
             }
-            if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (is_y && tid == 0) {
                 __threadfence();
                 atomicAdd(cnt.done_y + g, 1u);
-            }
-        } else {
-            const int64_t t = it - nX - nY;
-            const int g = find_grid(gd, ng, t, 1);
-            if (tid == 0) {
-                const unsigned need = static_cast<unsigned>(static_cast<int64_t>(gd[g].Xp / kCols) * gd[g].Z);
-                ok_s = wait_count(cnt.done_y + g, need, err);
-                __threadfence();
-                asm volatile("fence.proxy.async.global;" ::: "memory");
-            }
-            __syncthreads();
-            if (ok_s) {
-                tile_z<SMALL>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, phase, err);
-                phase ^= 1u;
             }
         }
     }
@@ -1682,21 +1294,6 @@ static cudaError_t launch_env_persistent(const GridTable &t, const PersistCounte
 // launchers
 // ------------------------------------------------------------------------------------
 
-// shared memory of k_edt_persistent's tiles (tables with a grid above 256)
-static size_t smem_y(const GridTable &t) {
-    const int by = t.maxY > kBox ? kBox : t.maxY;
-    const size_t rows = static_cast<size_t>((t.maxY + by - 1) / by) * by;
-    const size_t xs = t.large ? 2 : 1, link = t.large ? 2 : 1;
-    return rows * kCols * xs + static_cast<size_t>((t.maxY + 1) / 2) * kLanes * link + 16 + kLanes * 4 + t.maxY;
-}
-
-static size_t smem_z(const GridTable &t) {
-    const int bz = t.maxZ > kBox ? kBox : t.maxZ;
-    const size_t rows = static_cast<size_t>((t.maxZ + bz - 1) / bz) * bz;
-    const size_t site = t.large ? 4 : 2, link = t.large ? 2 : 1;
-    return rows * kCols * site + static_cast<size_t>((t.maxZ + 1) / 2) * kLanes * link + 16 + kLanes * 4 + t.maxZ;
-}
-
 cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s, int8_t *logodds, const int *lo_param) {
     if (t.rows == 0) return cudaSuccess;
     const int64_t want = (t.rows + 7) / 8;
@@ -1749,13 +1346,13 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s, int8_t *logodds, c
     }
 }
 
-template <int S, bool SMALL>
+template <int S>
 static cudaError_t launch_persistent_impl(const GridTable &t, const PersistCounters &c, int ctas_per_sm,
                                           int rows_per_item, cudaStream_t s) {
-    const size_t sy = smem_y(t), sz = smem_z(t);
+    const size_t sy = small_smem<2, PolY<true>>(t.maxY), sz = small_smem<2, PolZ<true>>(t.maxZ);
     const size_t sm = sy > sz ? sy : sz;
-    auto k = k_edt_persistent<S, SMALL>;
-    cudaError_t e = ensure_dyn_smem<k_edt_persistent<S, SMALL>>(sm);
+    auto k = k_edt_persistent<S>;
+    cudaError_t e = ensure_dyn_smem<k_edt_persistent<S>>(sm);
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kLanes, sm);
@@ -1787,9 +1384,9 @@ cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int 
         }
     }
     if (t.pzx != kCols) return cudaErrorInvalidValue;   // its pass-Z tiles are 32 x 1 rows
-    if (t.maxXp <= 256) return launch_persistent_impl<8, false>(t, c, ctas_per_sm, rows_per_item, s);
-    if (t.maxXp <= 512) return launch_persistent_impl<16, false>(t, c, ctas_per_sm, rows_per_item, s);
-    return launch_persistent_impl<32, false>(t, c, ctas_per_sm, rows_per_item, s);
+    if (t.maxXp <= 256) return launch_persistent_impl<8>(t, c, ctas_per_sm, rows_per_item, s);
+    if (t.maxXp <= 512) return launch_persistent_impl<16>(t, c, ctas_per_sm, rows_per_item, s);
+    return launch_persistent_impl<32>(t, c, ctas_per_sm, rows_per_item, s);
 }
 
 template <int NB, auto K>
