@@ -10,25 +10,16 @@
 //   pass Z  (Step 4, the same along the stacking axis): per column (x, y) the lower
 //           envelope of g2(z') + (z - z')^2, producing sqdist and a nearest voxel index.
 //
-// Passes Y and Z run one CTA of NB warps per tile of 32 columns (the m2 / m3 banding of
-// Alg. 1): lane t owns column t, warp b the b-th band of every line, so all lanes of a
-// warp scan the same positions.  The tile (32 columns x the whole line) is staged into
-// shared memory with TMA box loads.  Each warp builds its band's stacks of proximate
-// sites in place in the staged tile; after a CTA barrier warp 0 joins the bands of each
-// column (the junction repair) and publishes the kept ranges, and every warp walks the
-// merged envelope over its band.  The domination test is exact integer arithmetic with
-// h_s = f(s) + s^2:
+// Passes Y and Z (envelope.cu / envelope.cuh) run one CTA of NB warps per tile of 32
+// columns (the m2 / m3 banding of Alg. 1): lane t owns column t, warp b the b-th band of
+// every line.  The domination test is exact integer arithmetic with h_s = f(s) + s^2:
 //   b (above a) is dropped under c  iff  (h_c - h_b)(b - a) <= (h_b - h_a)(c - b),
-// i.e. c overtakes b no later than b overtakes a.  In the query the next proximate site
-// p+1 is strictly nearer to voxel j iff h_(p+1) - h_p < 2 j (c_(p+1) - c_p).
+// i.e. c overtakes b no later than b overtakes a.
 //
 // This file holds pass X for every size (k_pass_x_one and k_pass_x_small for grids with
-// every dim <= 256: 8-bit row sites and a per-row flag; k_pass_x above: 16-bit row
-// sites), passes Y and Z for grids above 256 (tile_y_small / tile_z_small with L = true:
-// 16-bit row sites and stack positions, 32-bit packed 2-D sites x | y << 16, 64-bit
-// products in the domination test; NB = 4 bands for lines up to 256, 8 beyond), and the
-// two persistent batch kernels.  Passes Y and Z of grids with every dim <= 256 are in
-// envelope.cu / envelope.cuh.
+// every dim <= 256: 8-bit row sites and a per-row flag; k_pass_x above: 16-bit row sites,
+// 0xFFFF for an empty row, and the row flag), the two persistent batch kernels over the
+// envelope tiles, and the launchers of the three passes.
 #include <climits>
 #include <type_traits>
 
@@ -159,12 +150,6 @@ constexpr int kLanes = 2 * kTile;  // threads per CTA of the large-grid persiste
 // one 8-bit mask per lane, and two shuffles give every lane the nearest occupied x left
 // and right of its segment.  A segment with no site splits at the midpoint of those two;
 // a segment with sites takes two register sweeps.
-//
-// Below it, the band tiles of passes Y and Z templated on the word sizes (L = true: grids
-// above 256).  A band's stack of proximate sites lives in place: entry k keeps its staged
-// input word in slot lo + k of the tile (a slot the sweep has already read) and its
-// position in pos[k][tid], so a pop, the junction merge and the query read both words
-// directly.
 // ====================================================================================
 __device__ __forceinline__ uint32_t nz_nibble(uint32_t w) {
     // bit i = (byte i != 0): set bit 7 of every non-zero byte, then gather bits 7, 15,
@@ -404,690 +389,10 @@ __global__ void __launch_bounds__(256) k_pass_x_one(const GridDesc *__restrict__
     }
 }
 
-// Policies of the two envelope passes, for grids with every dim <= 256 (L = false: 8-bit
-// positions, 8-bit row sites, 16-bit 2-D sites x' | y' << 8, 32-bit products) and up to
-// 1024 (L = true: 16-bit positions, 16-bit row sites, 32-bit 2-D sites x' | y' << 16,
-// 64-bit products).  In = staged input word; h(raw, p) = f(p) + p^2 for that word at p.
-template <bool L>
-struct PolY {
-    using In = typename std::conditional<L, uint16_t, uint8_t>::type;   // pass-X site x' of row p
-    using Pos = typename std::conditional<L, uint16_t, uint8_t>::type;
-    using Prod = typename std::conditional<L, long long, int>::type;
-    static constexpr int kMax = L ? 1024 : 256;
-    static constexpr bool kPacked = false;   // stack positions in a separate array
-    int x;
-    // squared distance within the line's plane, and with the position p along the line
-    __device__ __forceinline__ int f(uint32_t r) const {
-        const int d = x - static_cast<int>(r);
-        return d * d;
-    }
-    __device__ __forceinline__ int h(uint32_t r, int p) const { return f(r) + p * p; }
-    static __device__ __forceinline__ uint32_t pack(uint32_t r, int) { return r; }
-    static __device__ __forceinline__ int pos_of(uint32_t) { return 0; }
-};
-
-template <bool L>
-struct PolZ {
-    using In = typename std::conditional<L, uint32_t, uint16_t>::type;  // pass-Y 2-D site of slice p
-    using Pos = typename std::conditional<L, uint16_t, uint8_t>::type;
-    using Prod = typename std::conditional<L, long long, int>::type;
-    static constexpr int kMax = L ? 1024 : 256;
-    static constexpr int kShift = L ? 16 : 8;
-    static constexpr uint32_t kMask = L ? 0x3FFu : 0xFFu;
-    // Large mode keeps a stack entry's position (< 1024) in the bits its site leaves free
-    // (10-15 and 26-29 of x' | y' << 16, x', y' < 1024), so the tile needs no position
-    // array; small mode's 16-bit site has no free bits.
-    static constexpr bool kPacked = L;
-    int x, y;
-    __device__ __forceinline__ int f(uint32_t r) const {
-        const int dx = x - static_cast<int>(r & kMask), dy = y - static_cast<int>((r >> kShift) & kMask);
-        return dx * dx + dy * dy;
-    }
-    __device__ __forceinline__ int h(uint32_t r, int p) const { return f(r) + p * p; }
-    static __device__ __forceinline__ uint32_t pack(uint32_t r, int c) {
-        return r | (static_cast<uint32_t>(c & 63) << 10) | (static_cast<uint32_t>(c >> 6) << 26);
-    }
-    static __device__ __forceinline__ int pos_of(uint32_t r) {
-        return static_cast<int>(((r >> 10) & 63u) | ((r >> 26) << 6));
-    }
-};
-
-// Banded line geometry of a tile: NB warps, warp b owns band [b * bl, min(n, (b + 1) * bl))
-// of every line, bl = ceil(n / NB); lines are at most MAX long.
-template <int NB, int MAX>
-struct Bands {
-    static constexpr int kWords = (MAX / NB + 31) / 32;   // valid-mask words per band
-    static __host__ __device__ constexpr int len(int n) { return (n + NB - 1) / NB; }
-};
-
-// b dropped between a and c (positions a < b < c, h = f + p^2): c overtakes b no later
-// than b overtakes a.  Products in Prod (64-bit once dims exceed 256).
-template <class Prod>
-__device__ __forceinline__ bool dominated(int ca, int ha, int cb, int hb, int cc, int hc) {
-    return static_cast<Prod>(hc - hb) * (cb - ca) <= static_cast<Prod>(hb - ha) * (cc - cb);
-}
-
-// Stack of proximate sites of one band (Steps 2 and 4) over its valid positions
-// lo + 32 w + (bit of vm[w]), ascending.  `col` = this column's input (stride kCols), the
-// stack's input words are written back in place from slot lo; `cpos` = this column's
-// positions (stride kTile), entry k's position kept in slot lo + k like its word.
-template <int NB, class P>
-__device__ __forceinline__ int small_build(const P &pol, typename P::In *col, typename P::Pos *cpos, int lo,
-                                           const uint32_t (&vm)[Bands<NB, P::kMax>::kWords], int cap,
-                                           int32_t *err) {
-    using Prod = typename P::Prod;
-    int k = 0, a = 0, b = 0, ha = 0, hb = 0, dab = 0, wab = 0;
-    auto step = [&](int c) {
-        if (!in_range(k, cap, err)) return;   // debug builds: the stack never outgrows its band
-        const uint32_t r = col[c * kCols];
-        const int hc = pol.h(r, c);
-        while (k >= 2 && static_cast<Prod>(hc - hb) * wab <= static_cast<Prod>(dab) * (c - b)) {
-            --k;
-            b = a;
-            hb = ha;
-            if (k >= 2) {
-                const uint32_t ra = col[(lo + k - 2) * kCols];
-                if constexpr (P::kPacked) a = P::pos_of(ra);
-                else a = cpos[(lo + k - 2) * kTile];
-                ha = pol.h(ra, a);
-                dab = hb - ha;
-                wab = b - a;
-            }
-        }
-        if constexpr (P::kPacked) {
-            col[(lo + k) * kCols] = static_cast<typename P::In>(P::pack(r, c));
-        } else {
-            col[(lo + k) * kCols] = static_cast<typename P::In>(r);
-            cpos[(lo + k) * kTile] = static_cast<typename P::Pos>(c);
-        }
-        dab = hc - hb;
-        wab = c - b;
-        a = b;
-        ha = hb;
-        b = c;
-        hb = hc;
-        ++k;
-    };
-#pragma unroll
-    for (int w = 0; w < Bands<NB, P::kMax>::kWords; ++w) {
-        uint32_t bits = vm[w];
-        const int base = lo + 32 * w;
-        if (bits == 0xFFFFFFFFu) {   // a run of 32 valid positions (warp-uniform)
-#pragma unroll 2
-            for (int c = base; c < base + 32; ++c) step(c);
-        } else {
-            while (bits) {
-                const int c = base + __ffs(bits) - 1;
-                bits &= bits - 1u;
-                step(c);
-            }
-        }
-    }
-    return k;
-}
-
-// a[b] for a band index known only at run time (selects; no local memory)
-template <int NB>
-__device__ __forceinline__ int pick(const int (&a)[NB], int b) {
-    int v = a[0];
-#pragma unroll
-    for (int u = 1; u < NB; ++u)
-        if (b == u) v = a[u];
-    return v;
-}
-
-// Merged envelope of a line's NB bands: band b keeps its stack entries j[b]..i[b] (none
-// if j[b] > i[b]); the envelope is their concatenation in band order.
-template <int NB, class P>
-struct SmallMerged {
-    typename P::In *in;         // this column's slots (stride kCols)
-    const typename P::Pos *pos; // this column's positions, slot by slot (stride kTile)
-    int bl;                     // band length
-    int j[NB], i[NB];
-    int last;                   // last non-empty band
-    int32_t *err;               // error word (debug bounds checks)
-    // entry of slot s = b * bl + t (band b's stack entry t)
-    __device__ __forceinline__ void at_slot(int s, int &c, uint32_t &r) const {
-        if (!in_range(s, NB * bl, err)) {
-            c = 0;
-            r = 0;
-            return;
-        }
-        r = in[s * kCols];
-        if constexpr (P::kPacked) c = P::pos_of(r);
-        else c = pos[s * kTile];
-    }
-    __device__ __forceinline__ void at(int b, int t, int &c, uint32_t &r) const { at_slot(b * bl + t, c, r); }
-    // largest non-empty band below b, or -1
-    __device__ __forceinline__ int prev_band(int b) const {
-        int s = -1;
-#pragma unroll
-        for (int u = 0; u < NB; ++u)
-            if (u < b && j[u] <= i[u]) s = u;
-        return s;
-    }
-    // smallest non-empty band above b, or -1
-    __device__ __forceinline__ int next_band(int b) const {
-        int s = -1;
-#pragma unroll
-        for (int u = NB - 1; u >= 0; --u)
-            if (u > b && j[u] <= i[u]) s = u;
-        return s;
-    }
-    // Bands are joined left to right by the junction repair: the current top T is
-    // popped while the entry S below it and the next band's first entry F dominate it,
-    // and F is dropped while T and the entry G above F dominate it.  The four entries'
-    // positions and h stay in registers, so each step loads one new entry.
-    // entry below (sb, si + 1): (sb, si) itself if inside band sb's kept range, else the
-    // top of the nearest earlier non-empty band; sb = -1 if there is none
-    __device__ __forceinline__ void below(int &sb, int &si) const {
-        if (si < pick<NB>(j, sb)) {
-            sb = prev_band(sb);
-            si = sb >= 0 ? pick<NB>(i, sb) : 0;
-        }
-    }
-    __device__ __forceinline__ int hat(const P &pol, int b, int t, int &c) const {
-        uint32_t r;
-        at(b, t, c, r);
-        return pol.h(r, c);
-    }
-    __device__ __forceinline__ void merge(const P &pol, const int (&k)[NB]) {
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            j[b] = 0;
-            i[b] = k[b] - 1;
-        }
-        int tb = -1;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            if (k[b] == 0) continue;
-            if (tb >= 0) {
-                int jb = 0;
-                const int ib = k[b] - 1;
-                for (;;) {
-                    const int ti = pick<NB>(i, tb), tj = pick<NB>(j, tb);
-                    int sb = tb, si = ti - 1;
-                    if (si < tj) {
-                        sb = prev_band(tb);
-                        si = sb >= 0 ? pick<NB>(i, sb) : 0;
-                    }
-                    int ca, cb, cc;
-                    uint32_t ra, rb, rc;
-                    at(tb, ti, cb, rb);
-                    at(b, jb, cc, rc);
-                    const int hb = pol.h(rb, cb), hc = pol.h(rc, cc);
-                    if (sb >= 0) {
-                        at(sb, si, ca, ra);
-                        if (dominated<typename P::Prod>(ca, pol.h(ra, ca), cb, hb, cc, hc)) {
-                            // pop the top; an emptied band hands the top to the band below
-#pragma unroll
-                            for (int u = 0; u < NB; ++u)
-                                if (u == tb) i[u] = ti - 1;
-                            if (ti - 1 < tj) tb = sb;
-                            continue;
-                        }
-                    }
-                    if (jb + 1 <= ib) {
-                        at(b, jb + 1, ca, ra);
-                        if (dominated<typename P::Prod>(cb, hb, cc, hc, ca, pol.h(ra, ca))) {
-                            ++jb;
-                            continue;
-                        }
-                    }
-                    break;
-                }
-                j[b] = jb;
-            }
-            tb = b;   // a band's last entry can only be dropped by a later band
-        }
-        last = tb;
-    }
-    // last non-empty band from the ranges
-    __device__ __forceinline__ void find_last() {
-        last = -1;
-#pragma unroll
-        for (int u = 0; u < NB; ++u)
-            if (j[u] <= i[u]) last = u;
-    }
-};
-
-// Position of the walk's first entry: band b, stack entry t.
-template <int NB, class P>
-struct Cursor {
-    int b, t;
-    __device__ __forceinline__ void set(const SmallMerged<NB, P> &, int bb, int tt) {
-        b = bb;
-        t = tt;
-    }
-};
-
-// Forward cursor of the walk over slots: the current band's kept range, then the later
-// non-empty bands' ranges queued in order (first slot | last slot << 16), so a step
-// needs no band search.
-template <int NB, class P>
-struct Walk {
-    static constexpr int kQ = NB > 1 ? NB - 1 : 1;
-    int s, se;
-    uint32_t q[kQ];
-    __device__ __forceinline__ void init(const SmallMerged<NB, P> &M, int b, int t) {
-        s = b * M.bl + t;
-        se = b * M.bl + pick<NB>(M.i, b);
-#pragma unroll
-        for (int k = 0; k < kQ; ++k) q[k] = ~0u;
-        int n = 0;
-#pragma unroll
-        for (int u = 1; u < NB; ++u) {
-            const bool take = u > b && M.j[u] <= M.i[u];
-            const uint32_t v = static_cast<uint32_t>(u * M.bl + M.j[u]) | (static_cast<uint32_t>(u * M.bl + M.i[u]) << 16);
-#pragma unroll
-            for (int k = 0; k < kQ; ++k)
-                if (take && k == n) q[k] = v;
-            n += take ? 1 : 0;
-        }
-    }
-    // next entry; false at the end of the envelope
-    __device__ __forceinline__ bool next() {
-        if (s < se) {
-            ++s;
-            return true;
-        }
-        if (q[0] == ~0u) return false;
-        s = static_cast<int>(q[0] & 0xFFFFu);
-        se = static_cast<int>(q[0] >> 16);
-#pragma unroll
-        for (int k = 0; k + 1 < kQ; ++k) q[k] = q[k + 1];
-        q[kQ - 1] = ~0u;
-        return true;
-    }
-};
-
-// Walks the merged envelope over voxels [lo, hi) of band `band`: emit.start(c, raw)
-// whenever the nearest proximate site changes (and at lo), emit.put(value) once per voxel.
-// Entry q+1 is strictly nearer to voxel j iff h1 - h0 < 2 j (c1 - c0), ties keeping the
-// lower site.  The walk starts at the band's first entry (or the next band's), steps down
-// while the entry below is no worse at lo (the values at lo are unimodal along the
-// envelope), then moves up as the voxels advance, one entry ahead.
-template <int NB, class P, class E>
-__device__ __forceinline__ void small_query(const P &pol, const SmallMerged<NB, P> &M, int lo, int hi, int band,
-                                            E &emit) {
-    if (lo >= hi) return;
-    int cb = (M.j[0] <= M.i[0] && band == 0) ? 0 : -1;
-    if (cb < 0) cb = (pick<NB>(M.j, band) <= pick<NB>(M.i, band)) ? band : M.next_band(band);
-    Cursor<NB, P> cur;
-    if (cb < 0) cur.set(M, M.last, pick<NB>(M.i, M.last));
-    else cur.set(M, cb, pick<NB>(M.j, cb));
-    int c0;
-    uint32_t r0;
-    M.at(cur.b, cur.t, c0, r0);
-    int h0 = pol.h(r0, c0);
-    for (;;) {
-        int pb = cur.b, pt = cur.t - 1;
-        if (pt < pick<NB>(M.j, cur.b)) {
-            pb = M.prev_band(cur.b);
-            if (pb < 0) break;
-            pt = pick<NB>(M.i, pb);
-        }
-        int c;
-        uint32_t r;
-        M.at(pb, pt, c, r);
-        const int hb = pol.h(r, c);
-        if (hb - 2 * lo * c > h0 - 2 * lo * c0) break;
-        cur.set(M, pb, pt);
-        c0 = c;
-        r0 = r;
-        h0 = hb;
-    }
-    Walk<NB, P> nxt;
-    nxt.init(M, cur.b, cur.t);
-    if constexpr (E::kValues) {
-        // Values at the current voxel j of the current entry (v0 = h0 - 2 j c0 + j^2, step
-        // i0) and of the next one (v1, i1; 2^30 when there is none, above any value reached
-        // here): the next entry is strictly nearer iff v1 < v0.  The emitter writes v0.
-        constexpr int kNone = 1 << 30;
-        int c1 = 0, v1 = kNone, i1 = 0;
-        uint32_t r1 = 0;
-        int v0 = h0 - 2 * lo * c0 + lo * lo, i0 = 2 * (lo - c0) + 1;
-        auto fetch = [&](int j) {
-            if (nxt.next()) {
-                M.at_slot(nxt.s, c1, r1);
-                const int d = j - c1;
-                v1 = pol.f(r1) + d * d;
-                i1 = 2 * d + 1;
-            } else {
-                v1 = kNone;
-                i1 = 0;
-            }
-        };
-        fetch(lo);
-        emit.start(c0, r0);
-        for (int j = lo; j < hi; ++j) {
-            if (v1 < v0) {
-                do {
-                    c0 = c1;
-                    r0 = r1;
-                    v0 = v1;
-                    i0 = i1;
-                    fetch(j);
-                } while (v1 < v0);
-                emit.start(c0, r0);
-            }
-            emit.put(v0);
-            v0 += i0;
-            i0 += 2;
-            v1 += i1;
-            i1 += 2;
-        }
-    } else {
-        // Only the nearest site is emitted: the next entry is strictly nearer to voxel j
-        // iff h1 - h0 < 2 j (c1 - c0), the right side kept incrementally.
-        int c1 = 0, h1 = 0, dc2 = 0, dh = INT_MAX;
-        uint32_t r1 = 0;
-        auto fetch = [&]() {
-            if (nxt.next()) {
-                M.at_slot(nxt.s, c1, r1);
-                h1 = pol.h(r1, c1);
-                dc2 = 2 * (c1 - c0);
-                dh = h1 - h0;
-            } else {
-                dh = INT_MAX;
-                dc2 = 0;
-            }
-        };
-        fetch();
-        int thr = lo * dc2;
-        emit.start(c0, r0);
-        for (int j = lo; j < hi; ++j) {
-            if (dh < thr) {
-                do {
-                    c0 = c1;
-                    r0 = r1;
-                    h0 = h1;
-                    fetch();
-                    thr = j * dc2;
-                } while (dh < thr);
-                emit.start(c0, r0);
-            }
-            emit.put(0);
-            thr += dc2;
-        }
-    }
-}
-
-__device__ __forceinline__ int align16(int n) { return (n + 15) & ~15; }
-
-// valid-position bitmask of band [lo, hi) from per-position flags (warp-uniform)
-template <int W>
-__device__ __forceinline__ void band_mask(const uint8_t *flags, int lo, int hi, int lane, uint32_t (&vm)[W]) {
-    uint8_t f[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        const int q = lo + 32 * w + lane;
-        f[w] = q < hi ? flags[q] : 0;
-    }
-#pragma unroll
-    for (int w = 0; w < W; ++w) vm[w] = __ballot_sync(0xffffffffu, f[w] != 0);
-}
-
-template <bool L>
-struct EmitYs {
-    using Site = typename std::conditional<L, uint32_t, uint16_t>::type;
-    static constexpr bool kValues = false;   // emits the 2-D site only
-    Site *s2;
-    uint32_t off, Xp;
-    Site v;
-    uint32_t lim;   // elements of s2 (debug bounds checks)
-    int32_t *err;
-    __device__ __forceinline__ void start(int c, uint32_t r) {
-        v = static_cast<Site>(r | (static_cast<uint32_t>(c) << (L ? 16 : 8)));
-    }
-    __device__ __forceinline__ void put(int) {
-        if (in_range(off, lim, err)) s2[off] = v;
-        off += Xp;
-    }
-};
-
-template <bool L>
-struct EmitZs {
-    static constexpr bool kValues = true;    // emits the squared distance too
-    int32_t *sq, *ix;
-    uint32_t off, plane;
-    int X, XY;
-    bool live;
-    int id;
-    uint32_t lim;   // voxels of the grid (debug bounds checks)
-    int32_t *err;
-    __device__ __forceinline__ void start(int c, uint32_t r) {
-        id = static_cast<int>(r & PolZ<L>::kMask) + X * static_cast<int>((r >> PolZ<L>::kShift) & PolZ<L>::kMask) +
-             XY * c;
-    }
-    __device__ __forceinline__ void put(int val) {
-        if (live && in_range(off, lim, err)) {
-            sq[off] = val;
-            ix[off] = id;
-        }
-        off += plane;
-    }
-};
-
-// Shared memory of an envelope tile over lines of n positions: the staged line tile
-// (whole TMA boxes of up to kBox positions x 32 columns), the position stacks, the stack
-// sizes and the published kept ranges.
-template <int NB, class P>
-__host__ __device__ constexpr int tile_in_bytes(int n) {
-    return ((n + kBox - 1) / kBox) * (n < kBox ? n : kBox) * kCols * static_cast<int>(sizeof(typename P::In));
-}
-template <int NB, class P>
-__host__ __device__ constexpr int tile_pos_bytes(int n) {
-    if (P::kPacked) return 0;
-    return Bands<NB, P::kMax>::len(n) * NB * kTile * static_cast<int>(sizeof(typename P::Pos));
-}
-// Stack sizes and kept ranges per (band, column): 8 bits while a band holds at most 255
-// positions.
-template <int NB, class P>
-using RangeIdx = typename std::conditional<(P::kMax / NB <= 255), uint8_t, uint16_t>::type;
-template <int NB, class P>
-__host__ __device__ constexpr int small_region_off(int n) {
-    return ((tile_in_bytes<NB, P>(n) + 15) & ~15) + ((tile_pos_bytes<NB, P>(n) + 15) & ~15);
-}
-// The range area (2 x NB x 32 indices, at least 64 bytes) also holds the standalone
-// kernels' TMA barrier in its first 8 bytes until the tile is staged.  A 256-long pass-Z
-// line tile then takes 24,832 bytes: nine CTAs per SM.
-template <int NB, class P>
-__host__ __device__ constexpr int small_smem(int n) {
-    return small_region_off<NB, P>(n) + 2 * NB * kTile * static_cast<int>(sizeof(RangeIdx<NB, P>));
-}
-
-constexpr int kNBY = 4;   // default bands per line in the standalone passes, dims <= 256
-constexpr int kNBL = 8;   // bands per line once some dim exceeds 256, lines over 256 long
-constexpr int kNBLs = 4;  // bands per line once some dim exceeds 256, lines up to 256 long
-
-// One envelope tile over the staged line tile `in` (n positions x 32 columns), after
-// its TMA loads were issued: builds the bands, merges, walks.  `flags` = validity of each
-// position; `emit` starts at the thread's first voxel; `region` = the range area.  With
-// kOwnBar the TMA barrier `bar` lies in the range area's first bytes and is invalidated
-// before the ranges overwrite it.  Returns 1 iff the line has a valid position (the same
-// for every column), else 0.
-template <int NB, class P, bool kOwnBar, class E>
-__device__ __forceinline__ int small_envelope(typename P::In *in, typename P::Pos *pos, uint8_t *region,
-                                              const uint8_t *flags, int n, const P &pol, E &emit, uint64_t *bar,
-                                              uint32_t phase, int32_t *err, bool &ok) {
-    using RIdx = RangeIdx<NB, P>;
-    const int tid = threadIdx.x, lane = tid & (kTile - 1), band = tid >> 5;
-    const int bl = Bands<NB, P::kMax>::len(n);
-    const int lo = band * bl, hi = min(n, lo + bl);
-    uint32_t vm[Bands<NB, P::kMax>::kWords];
-    band_mask(flags, lo, hi, lane, vm);
-    ok = mbar_wait_bounded(bar, phase, err);
-    if (!ok) return 0;
-    const int k = small_build<NB>(pol, in + lane, pos + lane, lo, vm, bl, err);
-    // [NB][32] first kept entry per band, then [NB][32] stack sizes, overwritten by the
-    // last kept entry + 1; the second half starts at byte 64 or later, past the barrier
-    RIdx *rj = reinterpret_cast<RIdx *>(region);
-    RIdx *ri = rj + NB * kTile;
-    ri[tid] = static_cast<RIdx>(k);
-    if (!__syncthreads_or(k)) return 0;   // no valid position: the same for every column
-    SmallMerged<NB, P> M;
-    M.in = in + lane;
-    M.pos = pos + lane;
-    M.bl = bl;
-    M.err = err;
-    if (band == 0) {   // one merge per column, published to the other bands
-        if constexpr (kOwnBar) {
-            if (tid == 0) mbar_inval(bar);   // every thread has passed its wait
-            __syncwarp();
-        }
-        int kk[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) kk[b] = ri[b * kTile + lane];
-        M.merge(pol, kk);
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            rj[b * kTile + lane] = static_cast<RIdx>(M.j[b]);
-            ri[b * kTile + lane] = static_cast<RIdx>(M.i[b] + 1);
-        }
-    }
-    __syncthreads();
-    if (band != 0) {
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            M.j[b] = rj[b * kTile + lane];
-            M.i[b] = static_cast<int>(ri[b * kTile + lane]) - 1;
-        }
-        M.find_last();
-    }
-    small_query<NB>(pol, M, lo, hi, band, emit);
-    return 1;
-}
-
-// Issues the TMA loads of a line tile: boxes of up to kBox positions along the line.
-template <class In>
-__device__ __forceinline__ void load_line_tile(In *in, const CUtensorMap *map, int n, int x0, int c1, bool along_y,
-                                               uint64_t *bar) {
-    const int bb = n < kBox ? n : kBox;
-    const int nbox = (n + bb - 1) / bb;
-    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(nbox * bb * kCols * sizeof(In)));
-    for (int b = 0; b < nbox; ++b) {
-        if (along_y) tma_load_3d(in + static_cast<size_t>(b) * bb * kCols, map, x0, b * bb, c1, bar);
-        else tma_load_3d(in + static_cast<size_t>(b) * bb * kCols, map, x0, c1, b * bb, bar);
-    }
-}
-
-// One pass-Y tile (grid g, slice z, columns x0..x0+31) with NB * 32 threads.  Same
-// contract as tile_y: `phase` is the barrier's current parity; ends with a CTA barrier
-// so the caller may reuse shared memory.  kOwnBar: `bar` lies in the tile's range area.
-template <int NB, bool L, bool kOwnBar>
-__device__ __forceinline__ bool tile_y_small(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
-                                             int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
-                                             int32_t *err) {
-    using P = PolY<L>;
-    using In = typename P::In;
-    const int tid = threadIdx.x, lane = tid & (kTile - 1);
-    const int Y = gd[g].Y, Xp = gd[g].Xp;
-    const int tiles_x = Xp / kCols;
-    const int z = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x));
-    const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * kCols;
-    In *in = reinterpret_cast<In *>(smem);                                        // [Y][32]
-    auto *pos = reinterpret_cast<typename P::Pos *>(smem + align16(tile_in_bytes<NB, P>(Y)));
-    uint8_t *region = smem + small_region_off<NB, P>(Y);
-    if (tid == 0) load_line_tile(in, &tm[2 * g], Y, x0, z, true, bar);
-    const int lo = (tid >> 5) * Bands<NB, P::kMax>::len(Y);
-    const P pol{x0 + lane};
-    EmitYs<L> e{static_cast<typename EmitYs<L>::Site *>(gd[g].s2),
-                static_cast<uint32_t>((static_cast<int64_t>(z) * Y + lo) * Xp + x0 + lane), static_cast<uint32_t>(Xp),
-                0, static_cast<uint32_t>(Xp * Y * gd[g].Z), err};
-    bool ok;
-    const int total = small_envelope<NB, P, kOwnBar>(in, pos, region, gd[g].row_has + static_cast<int64_t>(z) * Y, Y,
-                                                     pol, e, bar, phase, err, ok);
-    if (!ok) {
-        drain_after_timeout(bar, phase);
-        (void)__syncthreads_or(0);   // pairs with the first barrier of the others
-        return false;
-    }
-    // an empty slice (the same for every column) writes no sites: pass Z skips it
-    if (x0 == 0 && tid == 0) gd[g].slice_has[z] = total > 0 ? 1 : 0;
-    __syncthreads();
-    return true;
-}
-
-// One pass-Z tile (grid g, row y, columns x0..x0+31) with NB * 32 threads.
-template <int NB, bool L, bool kOwnBar, int PX>
-__device__ __forceinline__ bool tile_z_small(const GridDesc *__restrict__ gd, const CUtensorMap *__restrict__ tm,
-                                             int g, int64_t lt, uint8_t *smem, uint64_t *bar, uint32_t phase,
-                                             int32_t *err) {
-    using P = PolZ<L>;
-    using In = typename P::In;
-    static_assert(PX == 8 || PX == kCols, "pass-Z tiles are 8 x 4 or 32 x 1 columns");
-    constexpr int PY = kCols / PX;   // the tile is PX x PY columns (x, y); lane l owns (l % PX, l / PX)
-    const int tid = threadIdx.x, lane = tid & (kTile - 1);
-    const int X = gd[g].X, Y = gd[g].Y, Z = gd[g].Z, Xp = gd[g].Xp;
-    const int tiles_x = Xp / PX;
-    const int y0 = static_cast<int>(static_cast<uint32_t>(lt) / static_cast<uint32_t>(tiles_x)) * PY;
-    const int x0 = static_cast<int>(static_cast<uint32_t>(lt) % static_cast<uint32_t>(tiles_x)) * PX;
-    In *in = reinterpret_cast<In *>(smem);                                        // [Z][32]
-    auto *pos = reinterpret_cast<typename P::Pos *>(smem + align16(tile_in_bytes<NB, P>(Z)));
-    uint8_t *region = smem + small_region_off<NB, P>(Z);
-    if (tid == 0) load_line_tile(in, &tm[2 * g + 1], Z, x0, y0, false, bar);
-    const int bl = Bands<NB, P::kMax>::len(Z);
-    const int lo = (tid >> 5) * bl, hi = min(Z, lo + bl);
-    const int x = x0 + lane % PX, y = y0 + lane / PX;
-    const bool live = x < X && y < Y;   // a ragged last patch reads zero words past row Y - 1
-    const uint32_t plane = static_cast<uint32_t>(X * Y);
-    const P pol{x, y};
-    EmitZs<L> e{gd[g].sqdist, gd[g].idx,
-                static_cast<uint32_t>(lo) * plane + static_cast<uint32_t>(live ? y * X + x : 0), plane, X, X * Y,
-                live, 0, plane * static_cast<uint32_t>(Z), err};
-    bool ok;
-    const int total = small_envelope<NB, P, kOwnBar>(in, pos, region, gd[g].slice_has, Z, pol, e, bar, phase, err,
-                                                     ok);
-    if (!ok) {
-        drain_after_timeout(bar, phase);
-        (void)__syncthreads_or(0);   // pairs with the first barrier of the others
-        return false;
-    }
-    if (total == 0) {   // empty grid
-        for (int j = lo; j < hi; ++j) {
-            if (live) {
-                e.sq[e.off] = INT_MAX;
-                e.ix[e.off] = -1;
-            }
-            e.off += plane;
-        }
-    }
-    __syncthreads();
-    return true;
-}
-
-template <int NB, bool L>
-__global__ void __launch_bounds__(NB * kTile) k_pass_y_small(const GridDesc *__restrict__ gd,
-                                                             const CUtensorMap *__restrict__ tm, int ng,
-                                                             int32_t *err) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    pdl_trigger();
-    const int64_t t = blockIdx.x;
-    const int g = find_grid(gd, ng, t, 0);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + small_region_off<NB, PolY<L>>(gd[g].Y));
-    if (threadIdx.x == 0) mbar_init(bar, 1);
-    __syncthreads();
-    pdl_wait();   // the staged tile and the validity flags come from the previous pass
-    if (gd[g].changed && *gd[g].changed == 0) return;   // unchanged since its last EDT
-    tile_y_small<NB, L, true>(gd, tm, g, t - gd[g].ty_begin, smem, bar, 0, err);
-}
-
-template <int NB, bool L, int PX>
-__global__ void __launch_bounds__(NB * kTile) k_pass_z_small(const GridDesc *__restrict__ gd,
-                                                             const CUtensorMap *__restrict__ tm, int ng,
-                                                             int32_t *err) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    pdl_trigger();
-    const int64_t t = blockIdx.x;
-    const int g = find_grid(gd, ng, t, 1);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + small_region_off<NB, PolZ<L>>(gd[g].Z));
-    if (threadIdx.x == 0) mbar_init(bar, 1);
-    __syncthreads();
-    pdl_wait();   // the staged tile and the validity flags come from the previous pass
-    if (gd[g].changed && *gd[g].changed == 0) return;   // unchanged since its last EDT
-    tile_z_small<NB, L, true, PX>(gd, tm, g, t - gd[g].tz_begin, smem, bar, 0, err);
-}
+// Default bands per line (the m2 / m3 banding of Alg. 1).
+constexpr int kNBY = 4;   // grids with every dim <= 256
+constexpr int kNBL = 8;   // once some dim exceeds 256: lines over 256 long
+constexpr int kNBLs = 4;  // once some dim exceeds 256: lines up to 256 long
 
 // ------------------------------------------------------------------------------------
 // persistent EDT over a whole table: one launch, work items dequeued in order
@@ -1125,8 +430,7 @@ cudaError_t launch_wait_selftest(const unsigned *counter, uint32_t limit, int32_
 }
 
 // Persistent EDT for tables with a grid above 256: the large-grid pass X and two-band
-// large-grid tiles (tile_y_small / tile_z_small with 16-bit row sites and positions,
-// 32-bit 2-D sites, 32 x 1 pass-Z tiles).  The tile area of shared memory is reused from
+// tiles with the large word sizes (envelope.cuh, PolYL / PolZL; 32 x 1 pass-Z tiles).  The tile area of shared memory is reused from
 // tile to tile: every thread fences its generic accesses of a tile against the async
 // proxy before the CTA barrier that precedes the next tile's TMA load into the same bytes.
 template <int S>
@@ -1180,8 +484,13 @@ __global__ void __launch_bounds__(kLanes) k_edt_persistent(const GridDesc *__res
             }
             __syncthreads();
             if (ok_s) {
-                if (is_y) tile_y_small<2, true, false>(gd, tm, g, t - gd[g].ty_begin, smem, &bar, phase, err);
-                else tile_z_small<2, true, false, kCols>(gd, tm, g, t - gd[g].tz_begin, smem, &bar, phase, err);
+                if (is_y)
+                    lenv::tile_y<2, false, lenv::PolYL>(gd[g], &tm[2 * g], static_cast<int>(t - gd[g].ty_begin), smem,
+                                                        &bar, phase, err);
+                else
+                    lenv::tile_z<2, false, kCols, lenv::PolZL>(gd[g], &tm[2 * g + 1],
+                                                               static_cast<int>(t - gd[g].tz_begin), smem, &bar,
+                                                               phase, err);
                 phase ^= 1u;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1270,8 +579,8 @@ __global__ void __launch_bounds__(NB * 32) k_env_persistent(const GridDesc *__re
 template <int NB, int PX>
 static cudaError_t launch_env_persistent(const GridTable &t, const PersistCounters &c, int ctas_per_sm,
                                          int rows_per_item, cudaStream_t s) {
-    const size_t sy = static_cast<size_t>(lenv::Layout<NB, uint8_t>(t.maxY).bytes);
-    const size_t sz = static_cast<size_t>(lenv::Layout<NB, uint16_t>(t.maxZ).bytes);
+    const size_t sy = static_cast<size_t>(lenv::Layout<NB, lenv::PolY>(t.maxY).bytes);
+    const size_t sz = static_cast<size_t>(lenv::Layout<NB, lenv::PolZ>(t.maxZ).bytes);
     const size_t sm = sy > sz ? sy : sz;
     cudaError_t e = ensure_dyn_smem<k_env_persistent<NB, PX>>(sm);
     if (e != cudaSuccess) return e;
@@ -1349,7 +658,8 @@ cudaError_t launch_pass_x(const GridTable &t, cudaStream_t s, int8_t *logodds, c
 template <int S>
 static cudaError_t launch_persistent_impl(const GridTable &t, const PersistCounters &c, int ctas_per_sm,
                                           int rows_per_item, cudaStream_t s) {
-    const size_t sy = small_smem<2, PolY<true>>(t.maxY), sz = small_smem<2, PolZ<true>>(t.maxZ);
+    const size_t sy = static_cast<size_t>(lenv::Layout<2, lenv::PolYL>(t.maxY).bytes);
+    const size_t sz = static_cast<size_t>(lenv::Layout<2, lenv::PolZL>(t.maxZ).bytes);
     const size_t sm = sy > sz ? sy : sz;
     auto k = k_edt_persistent<S>;
     cudaError_t e = ensure_dyn_smem<k_edt_persistent<S>>(sm);
@@ -1389,14 +699,6 @@ cudaError_t launch_persistent(const GridTable &t, const PersistCounters &c, int 
     return launch_persistent_impl<32>(t, c, ctas_per_sm, rows_per_item, s);
 }
 
-template <int NB, auto K>
-static cudaError_t launch_small(int64_t tiles, int sm, const GridTable &t, cudaStream_t s) {
-    const cudaError_t e = ensure_dyn_smem<K>(static_cast<size_t>(sm));
-    if (e != cudaSuccess) return e;
-    return launch_pdl(K, dim3(static_cast<unsigned>(tiles)), dim3(NB * kTile), static_cast<size_t>(sm), s, t.desc,
-                      t.tmaps, t.n, t.err);
-}
-
 // Bands per line (the m2 / m3 banding of Alg. 1): the table's `bands` if set, else four
 // (small mode) or four / eight by line length (large mode).  Small mode takes 1, 2, 4 or
 // 8 bands, large mode 4 or 8; vedt_map_set_bands admits no other value.
@@ -1406,25 +708,8 @@ static int bands_for(const GridTable &t, int line) {
     return line <= 256 ? kNBLs : kNBL;
 }
 
-cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) {
-    if (t.tiles_y == 0) return cudaSuccess;
-    const int nb = bands_for(t, t.maxY);
-    if (!t.large) return launch_env_y(t, nb, s);
-    if (nb == 4) return launch_small<4, k_pass_y_small<4, true>>(t.tiles_y, small_smem<4, PolY<true>>(t.maxY), t, s);
-    return launch_small<8, k_pass_y_small<8, true>>(t.tiles_y, small_smem<8, PolY<true>>(t.maxY), t, s);
-}
+cudaError_t launch_pass_y(const GridTable &t, cudaStream_t s) { return launch_env_y(t, bands_for(t, t.maxY), s); }
 
-cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s) {
-    if (t.tiles_z == 0) return cudaSuccess;
-    const int nb = bands_for(t, t.maxZ);
-    if (!t.large) return launch_env_z(t, nb, s);
-    const size_t s4 = small_smem<4, PolZ<true>>(t.maxZ), s8 = small_smem<8, PolZ<true>>(t.maxZ);
-    if (t.pzx == 8)
-        return nb == 4 ? launch_small<4, k_pass_z_small<4, true, 8>>(t.tiles_z, s4, t, s)
-                       : launch_small<8, k_pass_z_small<8, true, 8>>(t.tiles_z, s8, t, s);
-    if (t.pzx != kCols) return cudaErrorInvalidValue;   // tiles counted for another shape
-    return nb == 4 ? launch_small<4, k_pass_z_small<4, true, kCols>>(t.tiles_z, s4, t, s)
-                   : launch_small<8, k_pass_z_small<8, true, kCols>>(t.tiles_z, s8, t, s);
-}
+cudaError_t launch_pass_z(const GridTable &t, cudaStream_t s) { return launch_env_z(t, bands_for(t, t.maxZ), s); }
 
 }  // namespace vedt

@@ -33,6 +33,7 @@
 // K + (x'^2 + y'^2) - 2 (x x' + y y') with K = x^2 + y^2: two byte dot products.
 #pragma once
 #include <climits>
+#include <type_traits>
 
 #include "vedt_internal.h"
 
@@ -51,9 +52,37 @@ __device__ __forceinline__ int find_tile_grid(const GridDesc *__restrict__ gd, i
     return lo;
 }
 
+// Word-size policies of the two passes.  Grids with every dim <= 256 (small): 8-bit row
+// sites, 16-bit 2-D sites x' | y' << 8, 8-bit stack positions, 32-bit products.  Grids
+// with a dim above 256 (large, up to 1024): 16-bit row sites, 32-bit 2-D sites
+// x' | y' << 16, 16-bit positions (pass Z keeps them in the free bits of its sites, so
+// its tile needs no position array), 64-bit products in the domination test.  h(r, p) =
+// f(p) + p^2 for input word r at position p stays below 2^22, and the walk's sums below
+// 2^31, for lines up to 1024.
+
 // Pass Y: input word = the row's nearest site x' (pass X); f(p) = (x - x')^2.
 struct PolY {
     using In = uint8_t;
+    using Pos = uint8_t;
+    using Prod = int;
+    using Out = uint16_t;   // the 2-D site x' | y' << 8
+    static constexpr int kMax = 256, kOutShift = 8, kBig = 1 << 20;
+    static constexpr bool kPacked = false;
+    int x;
+    __device__ __forceinline__ int g(uint32_t r) const {
+        const int d = x - static_cast<int>(r);
+        return d * d;
+    }
+    __device__ __forceinline__ int h(uint32_t r, int p) const { return g(r) + p * p; }
+};
+
+struct PolYL {
+    using In = uint16_t;
+    using Pos = uint16_t;
+    using Prod = long long;
+    using Out = uint32_t;   // x' | y' << 16
+    static constexpr int kMax = 1024, kOutShift = 16, kBig = 1 << 23;
+    static constexpr bool kPacked = false;
     int x;
     __device__ __forceinline__ int g(uint32_t r) const {
         const int d = x - static_cast<int>(r);
@@ -66,8 +95,15 @@ struct PolY {
 // f(p) = (x - x')^2 + (y - y')^2 = K + dp(r, r) - 2 dp(r, x | y << 8).
 struct PolZ {
     using In = uint16_t;
+    using Pos = uint8_t;
+    using Prod = int;
+    static constexpr int kMax = 256, kBig = 1 << 20;
+    static constexpr bool kPacked = false;
     uint32_t xy8;
     int K;
+    __device__ static PolZ at(int x, int y) {
+        return PolZ{static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 8), x * x + y * y};
+    }
     __device__ __forceinline__ int g(uint32_t r) const {
         return static_cast<int>(__dp4a(r, r, static_cast<unsigned>(K))) - 2 * static_cast<int>(__dp4a(r, xy8, 0u));
     }
@@ -75,34 +111,74 @@ struct PolZ {
         return static_cast<int>(__dp4a(r, r, static_cast<unsigned>(K + p * p))) -
                2 * static_cast<int>(__dp4a(r, xy8, 0u));
     }
+    // linear index x' + X y' + XY z' of the site as a 2-way dot product (coef = 1 | X << 16)
+    static __device__ __forceinline__ uint32_t coef(int X) { return 1u | (static_cast<uint32_t>(X) << 16); }
+    __device__ __forceinline__ int index(uint32_t r, int c, uint32_t coef, int XY) const {
+        return static_cast<int>(__dp2a_lo(coef, r, static_cast<unsigned>(XY * c)));
+    }
+};
+
+// Large pass Z: input word x' | y' << 16 (x', y' < 1024); a stack entry keeps its
+// position (< 1024) in bits 10-15 and 26-29, which the site leaves free.
+struct PolZL {
+    using In = uint32_t;
+    using Pos = uint16_t;
+    using Prod = long long;
+    static constexpr int kMax = 1024, kBig = 1 << 23;
+    static constexpr bool kPacked = true;
+    int x, y;
+    __device__ static PolZL at(int x, int y) { return PolZL{x, y}; }
+    __device__ __forceinline__ int g(uint32_t r) const {
+        const int dx = x - static_cast<int>(r & 0x3FFu), dy = y - static_cast<int>((r >> 16) & 0x3FFu);
+        return dx * dx + dy * dy;
+    }
+    __device__ __forceinline__ int h(uint32_t r, int p) const { return g(r) + p * p; }
+    // linear index x' + X y' + XY z' of the site (coef = X)
+    static __device__ __forceinline__ uint32_t coef(int X) { return static_cast<uint32_t>(X); }
+    __device__ __forceinline__ int index(uint32_t r, int c, uint32_t coef, int XY) const {
+        return static_cast<int>(r & 0x3FFu) + static_cast<int>(coef) * static_cast<int>((r >> 16) & 0x3FFu) + XY * c;
+    }
+    static __device__ __forceinline__ uint32_t pack(uint32_t r, int c) {
+        return r | (static_cast<uint32_t>(c & 63) << 10) | (static_cast<uint32_t>(c >> 6) << 26);
+    }
+    static __device__ __forceinline__ int pos_of(uint32_t r) {
+        return static_cast<int>(((r >> 10) & 63u) | ((r >> 26) << 6));
+    }
 };
 
 // b (between a and c) is dropped: c overtakes b no later than b overtakes a.
+template <class Prod>
 __device__ __forceinline__ bool dominated(int ca, int ha, int cb, int hb, int cc, int hc) {
-    return (hc - hb) * (cb - ca) <= (hb - ha) * (cc - cb);
+    return static_cast<Prod>(hc - hb) * (cb - ca) <= static_cast<Prod>(hb - ha) * (cc - cb);
 }
 
-template <int NB>
+template <int NB, int MAX = 256>
 struct Geo {
-    static constexpr int kWords = (256 / NB + 31) / 32;   // valid-mask words per band
+    static constexpr int kWords = (MAX / NB + 31) / 32;   // valid-mask words per band
     static __host__ __device__ constexpr int len(int n) { return (n + NB - 1) / NB; }
 };
 
-// Shared memory of one tile of n positions: the staged line tile [n][32], the stack
-// positions [NB * bl][32] (bytes) and the published kept ranges (j, then i + 1, NB x 32
-// bytes each).  The TMA barrier lives in the first 8 bytes of the j ranges, which are
-// written only after every thread has passed its wait and the barrier is invalidated.
-// A 256-long pass-Z tile with four bands takes 24,832 bytes (nine CTAs per SM), a pass-Y
-// tile 16,640 (thirteen).
-template <int NB, class In>
+// rows of the staged tile: whole TMA boxes of up to kBox positions
+__host__ __device__ constexpr int staged_rows(int n) { return n <= kBox ? n : (n + kBox - 1) / kBox * kBox; }
+
+// Shared memory of one tile of n positions: the staged line tile [rows][32], the stack
+// positions [NB * bl][32] (none where the policy packs them into the sites) and the
+// published kept ranges (j, then i + 1, NB x 32 each, bytes for small grids, 16-bit words
+// above).  The TMA barrier lives in the first 8 bytes of the j ranges, which are written
+// only after every thread has passed its wait and the barrier is invalidated.  A 256-long
+// small pass-Z tile with four bands takes 24,832 bytes (nine CTAs per SM), a pass-Y tile
+// 16,640 (thirteen).
+template <int NB, class P>
 struct Layout {
+    using Rng = typename std::conditional<(P::kMax > 256), uint16_t, uint8_t>::type;
     int pos_off, rng_off, bar_off, bytes;
     __host__ __device__ Layout(int n) {
-        const int in_b = n * kC * static_cast<int>(sizeof(In));
+        const int in_b = staged_rows(n) * kC * static_cast<int>(sizeof(typename P::In));
         pos_off = (in_b + 15) & ~15;
-        rng_off = pos_off + ((Geo<NB>::len(n) * NB * kC + 15) & ~15);
+        const int pos_b = P::kPacked ? 0 : Geo<NB>::len(n) * NB * kC * static_cast<int>(sizeof(typename P::Pos));
+        rng_off = pos_off + ((pos_b + 15) & ~15);
         bar_off = rng_off;
-        bytes = rng_off + 2 * NB * kC;
+        bytes = rng_off + 2 * NB * kC * static_cast<int>(sizeof(Rng));
     }
 };
 
@@ -127,31 +203,44 @@ __device__ __forceinline__ void band_mask(const uint8_t *__restrict__ flags, int
 // the top, clamped to the band's first slot, and replaces it by the sentinel when the
 // stack has become too small.
 template <int W, class P>
-__device__ __forceinline__ int build(const P &pol, typename P::In *col, uint8_t *cp, int lo, const uint32_t (&vm)[W],
-                                     int cap, int32_t *err) {
-    constexpr int kBig = 1 << 20;
-    typename P::In *const in0 = col + lo * kC;   // the band's first slot
-    uint8_t *const ps0 = cp + lo * kC;
+__device__ __forceinline__ int build(const P &pol, typename P::In *col, typename P::Pos *cp, int lo,
+                                     const uint32_t (&vm)[W], int cap, int32_t *err) {
+    constexpr int kBig = P::kBig;
+    using In = typename P::In;
+    using Pos = typename P::Pos;
+    In *const in0 = col + lo * kC;   // the band's first slot
+    Pos *const ps0 = cp + lo * kC;
     // before the first push: a fake b at position -1 with h = 0 and a sentinel a below it,
     // so that no candidate (position >= 0, h >= 0) can pop it
     int k = 0, cb = -1, hb = 0, ca = -2, ha = kBig;
     auto step = [&](int c) {
         const uint32_t r = col[c * kC];
         const int hc = pol.h(r, c);
-        while (dominated(ca, ha, cb, hb, c, hc)) {
+        while (dominated<typename P::Prod>(ca, ha, cb, hb, c, hc)) {
             --k;
             cb = ca;
             hb = ha;
             const int s = max(k - 2, 0) * kC;
-            const int c2 = ps0[s];
-            const int h2 = pol.h(in0[s], c2);
+            int c2, h2;
+            if constexpr (P::kPacked) {
+                const uint32_t w2 = in0[s];
+                c2 = P::pos_of(w2);
+                h2 = pol.h(w2, c2);
+            } else {
+                c2 = ps0[s];
+                h2 = pol.h(in0[s], c2);
+            }
             const bool real = k >= 2;
             ca = real ? c2 : cb - 1;
             ha = real ? h2 : hb + kBig;
         }
         if (in_range(k, cap, err)) {   // debug builds: the stack never outgrows its band
-            in0[k * kC] = static_cast<typename P::In>(r);
-            ps0[k * kC] = static_cast<uint8_t>(c);
+            if constexpr (P::kPacked) {
+                in0[k * kC] = static_cast<In>(P::pack(r, c));
+            } else {
+                in0[k * kC] = static_cast<In>(r);
+                ps0[k * kC] = static_cast<Pos>(c);
+            }
         }
         const bool first = k == 0;
         ca = first ? c - 1 : cb;
@@ -193,7 +282,7 @@ __device__ __forceinline__ int pick(const int (&a)[NB], int b) {
 template <int NB, class P>
 struct Joined {
     const typename P::In *col;   // this column's slots (stride kC)
-    const uint8_t *cp;
+    const typename P::Pos *cp;   // their positions (unused where the policy packs them)
     int bl;
     int j[NB], i[NB];
     int32_t *err;
@@ -204,7 +293,8 @@ struct Joined {
             return;
         }
         r = col[s * kC];
-        c = cp[s * kC];
+        if constexpr (P::kPacked) c = P::pos_of(r);
+        else c = cp[s * kC];
     }
     __device__ __forceinline__ bool nonempty(int b) const { return pick<NB>(j, b) <= pick<NB>(i, b); }
     // largest non-empty band below b, or -1
@@ -253,7 +343,7 @@ struct Joined {
                         int cS;
                         uint32_t rS;
                         at(sb * bl + si, cS, rS);
-                        if (dominated(cS, pol.h(rS, cS), cT, hT, cF, hF)) {
+                        if (dominated<typename P::Prod>(cS, pol.h(rS, cS), cT, hT, cF, hF)) {
 #pragma unroll
                             for (int u = 0; u < NB; ++u)
                                 if (u == tb) i[u] = ti - 1;
@@ -265,7 +355,7 @@ struct Joined {
                         int cG;
                         uint32_t rG;
                         at(b * bl + jb + 1, cG, rG);
-                        if (dominated(cT, hT, cF, hF, cG, pol.h(rG, cG))) {
+                        if (dominated<typename P::Prod>(cT, hT, cF, hF, cG, pol.h(rG, cG))) {
                             ++jb;
                             continue;
                         }
@@ -329,15 +419,22 @@ struct Joined {
     }
 };
 
-// Line tile staging: one TMA box of n positions x 32 columns.
+// Line tile staging: TMA boxes of up to kBox positions x 32 columns (one box for lines
+// up to 256; longer lines take whole boxes, the last one read past the line's end as
+// zeros that no sweep visits).
 template <class In>
 __device__ __forceinline__ void load_tile(In *in, const CUtensorMap *map, int n, int x0, int c1, bool along_y,
                                           uint64_t *bar) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
                  : "memory");
-    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(n * kC * sizeof(In)));
-    if (along_y) tma_load_3d(in, map, x0, 0, c1, bar);
-    else tma_load_3d(in, map, x0, c1, 0, bar);
+    const int bb = n < kBox ? n : kBox;
+    const int nbox = (n + bb - 1) / bb;
+    mbar_arrive_expect_tx(bar, static_cast<uint32_t>(nbox * bb * kC * sizeof(In)));
+    for (int b = 0; b < nbox; ++b) {
+        In *dst = in + static_cast<size_t>(b) * bb * kC;
+        if (along_y) tma_load_3d(dst, map, x0, b * bb, c1, bar);
+        else tma_load_3d(dst, map, x0, c1, b * bb, bar);
+    }
 }
 
 __device__ __forceinline__ void drain_after_timeout(uint64_t *bar, uint32_t phase) {
@@ -351,14 +448,15 @@ __device__ __forceinline__ void drain_after_timeout(uint64_t *bar, uint32_t phas
 // kernels, one tile per CTA) and is invalidated before the ranges overwrite it; else it
 // is a separate barrier that the caller reuses with alternating phases.
 template <int NB, bool kOwnBar, class P>
-__device__ __forceinline__ bool envelope(const P &pol, typename P::In *in, uint8_t *pos, uint8_t *rng,
+__device__ __forceinline__ bool envelope(const P &pol, typename P::In *in, typename P::Pos *pos, uint8_t *rng_bytes,
                                          const uint8_t *__restrict__ flags, int n, Joined<NB, P> &J, int &lo, int &hi,
                                          uint64_t *bar, uint32_t phase, int32_t *err, bool &ok) {
+    using Rng = typename Layout<NB, P>::Rng;
     const int tid = threadIdx.x, lane = tid & 31, band = tid >> 5;
     const int bl = Geo<NB>::len(n);
     lo = band * bl;
     hi = min(n, lo + bl);
-    uint32_t vm[Geo<NB>::kWords];
+    uint32_t vm[Geo<NB, P::kMax>::kWords];
     band_mask(flags, lo, hi, lane, vm);
     ok = mbar_wait_bounded(bar, phase, err);
     if (!ok) {
@@ -376,8 +474,10 @@ __device__ __forceinline__ bool envelope(const P &pol, typename P::In *in, uint8
         J.i[0] = k - 1;
         return __syncthreads_or(k) != 0;
     } else {
-        uint8_t *rj = rng, *ri = rng + NB * kC;   // first kept entry; stack size, then last kept + 1
-        ri[tid] = static_cast<uint8_t>(k);         // (ri starts at byte 64 or later, past the barrier)
+        // first kept entry; stack size, then last kept + 1 (ri starts at byte 64 or later,
+        // past the barrier)
+        Rng *rj = reinterpret_cast<Rng *>(rng_bytes), *ri = rj + NB * kC;
+        ri[tid] = static_cast<Rng>(k);
         if (!__syncthreads_or(k)) return false;
         if (band == 0) {
             if constexpr (kOwnBar) {
@@ -391,8 +491,8 @@ __device__ __forceinline__ bool envelope(const P &pol, typename P::In *in, uint8
             __syncwarp();   // every lane of warp 0 has read the sizes before they are overwritten
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                rj[b * kC + lane] = static_cast<uint8_t>(J.j[b]);
-                ri[b * kC + lane] = static_cast<uint8_t>(J.i[b] + 1);
+                rj[b * kC + lane] = static_cast<Rng>(J.j[b]);
+                ri[b * kC + lane] = static_cast<Rng>(J.i[b] + 1);
             }
         }
         __syncthreads();
@@ -412,22 +512,23 @@ __device__ __forceinline__ bool envelope(const P &pol, typename P::In *in, uint8
 // site x' | y' << 8 of every voxel and the slice's flag
 // ------------------------------------------------------------------------------------
 // One pass-Y tile (grid g, tile lt of that grid) with NB warps, staged into `smem` (layout
-// Layout<NB, uint8_t>(Y)) through `bar` (current parity `phase`).  Returns false if the
+// Layout<NB, P>(Y)) through `bar` (current parity `phase`).  Returns false if the
 // staging wait timed out (flagged in err).
-template <int NB, bool kOwnBar>
+template <int NB, bool kOwnBar, class P = PolY>
 __device__ __forceinline__ bool tile_y(const GridDesc &G, const CUtensorMap *tmap, int lt, uint8_t *smem,
                                        uint64_t *bar, uint32_t phase, int32_t *err) {
+    using Out = typename P::Out;
     const int tid = threadIdx.x, lane = tid & 31;
     const int Y = G.Y, Xp = G.Xp;
     const int tiles_x = Xp / kC;
     const int z = lt / tiles_x, x0 = (lt % tiles_x) * kC;
-    const Layout<NB, uint8_t> L(Y);
-    uint8_t *in = smem;
-    uint8_t *pos = smem + L.pos_off;
+    const Layout<NB, P> L(Y);
+    auto *in = reinterpret_cast<typename P::In *>(smem);
+    auto *pos = reinterpret_cast<typename P::Pos *>(smem + L.pos_off);
     uint8_t *rng = smem + L.rng_off;
     if (tid == 0) load_tile(in, tmap, Y, x0, z, true, bar);
-    const PolY pol{x0 + lane};
-    Joined<NB, PolY> J;
+    const P pol{x0 + lane};
+    Joined<NB, P> J;
     int lo, hi;
     bool ok;
     const bool any = envelope<NB, kOwnBar>(pol, in, pos, rng, G.row_has + static_cast<int64_t>(z) * Y, Y, J, lo, hi, bar,
@@ -456,8 +557,8 @@ __device__ __forceinline__ bool tile_y(const GridDesc &G, const CUtensorMap *tma
     };
     fetch();
     int thr = lo * dc2;
-    uint16_t site = static_cast<uint16_t>(r0 | (static_cast<uint32_t>(c0) << 8));
-    uint16_t *out = static_cast<uint16_t *>(G.s2);
+    Out site = static_cast<Out>(r0 | (static_cast<uint32_t>(c0) << P::kOutShift));
+    Out *out = static_cast<Out *>(G.s2);
     uint32_t off = static_cast<uint32_t>((z * Y + lo) * Xp + x0 + lane);
     const uint32_t lim = static_cast<uint32_t>(Xp * Y * G.Z);
     for (int jv = lo; jv < hi; ++jv) {
@@ -469,7 +570,7 @@ __device__ __forceinline__ bool tile_y(const GridDesc &G, const CUtensorMap *tma
                 fetch();
                 thr = jv * dc2;
             } while (dh < thr);
-            site = static_cast<uint16_t>(r0 | (static_cast<uint32_t>(c0) << 8));
+            site = static_cast<Out>(r0 | (static_cast<uint32_t>(c0) << P::kOutShift));
         }
         if (in_range(off, lim, err)) out[off] = site;
         off += Xp;
@@ -482,12 +583,12 @@ __device__ __forceinline__ bool tile_y(const GridDesc &G, const CUtensorMap *tma
 // pass Z: tile = (grid, patch of PX x (32 / PX) columns (x, y) at (x0, y0)), line along z;
 // writes sqdist and the nearest voxel's linear index
 // ------------------------------------------------------------------------------------
-// One pass-Z tile (grid g, tile lt of that grid), as tile_y (layout Layout<NB, uint16_t>(Z)).
+// One pass-Z tile (grid g, tile lt of that grid), as tile_y (layout Layout<NB, P>(Z)).
 // Lane l owns column (x0 + l % PX, y0 + l / PX); the TMA box (PX, 32 / PX, Z) lands as
 // [z][lane] for either shape.  The valid positions (slices holding a site) are the same
 // for every column, so the build stays warp-uniform; lanes past the grid's last row (a
 // ragged last patch, read as zero words) compute but store nothing.
-template <int NB, bool kOwnBar, int PX>
+template <int NB, bool kOwnBar, int PX, class P = PolZ>
 __device__ __forceinline__ bool tile_z(const GridDesc &G, const CUtensorMap *tmap, int lt, uint8_t *smem,
                                        uint64_t *bar, uint32_t phase, int32_t *err) {
     static_assert(PX == 8 || PX == 32, "pass-Z tiles are 8 x 4 or 32 x 1 columns");
@@ -496,14 +597,14 @@ __device__ __forceinline__ bool tile_z(const GridDesc &G, const CUtensorMap *tma
     const int X = G.X, Y = G.Y, Z = G.Z, Xp = G.Xp;
     const int tiles_x = Xp / PX;
     const int y0 = (lt / tiles_x) * PY, x0 = (lt % tiles_x) * PX;
-    const Layout<NB, uint16_t> L(Z);
-    uint16_t *in = reinterpret_cast<uint16_t *>(smem);
-    uint8_t *pos = smem + L.pos_off;
+    const Layout<NB, P> L(Z);
+    auto *in = reinterpret_cast<typename P::In *>(smem);
+    auto *pos = reinterpret_cast<typename P::Pos *>(smem + L.pos_off);
     uint8_t *rng = smem + L.rng_off;
     if (tid == 0) load_tile(in, tmap, Z, x0, y0, false, bar);
     const int x = x0 + lane % PX, y = y0 + lane / PX;
-    const PolZ pol{static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 8), x * x + y * y};
-    Joined<NB, PolZ> J;
+    const P pol = P::at(x, y);
+    Joined<NB, P> J;
     int lo, hi;
     bool ok;
     const bool any = envelope<NB, kOwnBar>(pol, in, pos, rng, G.slice_has, Z, J, lo, hi, bar, phase, err, ok);
@@ -524,7 +625,7 @@ __device__ __forceinline__ bool tile_z(const GridDesc &G, const CUtensorMap *tma
         return true;
     }
     if (lo >= hi) return true;
-    const uint32_t coef = 1u | (static_cast<uint32_t>(X) << 16);   // x' + X y' as a 2-way dot product
+    const uint32_t coef = P::coef(X);
     const int XY = X * Y;
     int s, sb, c0;
     uint32_t r0;
@@ -550,7 +651,7 @@ __device__ __forceinline__ bool tile_z(const GridDesc &G, const CUtensorMap *tma
     int d = lo - c0;
     int v = h0 - c0 * c0 + d * d;
     int inc = 2 * d + 1;
-    int id = static_cast<int>(__dp2a_lo(coef, r0, static_cast<unsigned>(XY * c0)));
+    int id = pol.index(r0, c0, coef, XY);
     for (int jv = lo; jv < hi; ++jv) {
         if (dh < thr) {
             do {
@@ -563,7 +664,7 @@ __device__ __forceinline__ bool tile_z(const GridDesc &G, const CUtensorMap *tma
             d = jv - c0;
             v = h0 - c0 * c0 + d * d;
             inc = 2 * d + 1;
-            id = static_cast<int>(__dp2a_lo(coef, r0, static_cast<unsigned>(XY * c0)));
+            id = pol.index(r0, c0, coef, XY);
         }
         if (live && in_range(off, lim, err)) {
             sq[off] = v;
