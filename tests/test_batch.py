@@ -60,6 +60,20 @@ def test_batch_mixed_small_and_large_matches_single_runs():
         sq1, ix1 = (t.cpu().numpy() for t in m.field(v.MAP_ENV))
         assert np.array_equal(sq, sq1) and np.array_equal(ix, ix1)
         assert np.array_equal(sq, oracle.edt(o)[0])
+    # both pass-Z tile shapes for the small grids (the large grids keep 32 x 1 rows), with
+    # the persistent launch and with three plain launches
+    for tz in (8, 32):
+        b.set_tile_z(tz)
+        assert b.tile_z() == tz
+        for persistent in (1, 0):
+            b.set_tuning(0, 32, persistent)
+            for m in maps:
+                m.field_view(v.MAP_ENV)[0].fill_(-5)
+            torch.cuda.synchronize()
+            b.compute_edt()
+            b.check()
+            for m, (sq, _) in zip(maps, batched):
+                assert np.array_equal(m.field(v.MAP_ENV)[0].cpu().numpy(), sq), (tz, persistent)
     b.close()
 
 
