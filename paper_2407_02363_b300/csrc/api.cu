@@ -757,15 +757,18 @@ vedt_status queue_host_frame(vedt_map *m, const float *xyz, int64_t n, const flo
             m->consumed[b] = ev[2 * b + 1];
         }
     }
-    if (n > m->stage_cap) {   // grow both buffers once nothing reads or writes them
-        VCHECK(cudaStreamSynchronize(m->copy_stream));
-        VCHECK(cudaStreamSynchronize(m->stream));
+    if (n > m->stage_cap) {
+        // Grow both buffers without synchronising the device (cudaFree would wait for every
+        // stream, other maps' frames included): the old buffers are released on the map's
+        // stream after the queued frames that read them, the new ones come from the
+        // stream-ordered allocator on the copy stream, ahead of the uploads into them.
         for (int b = 0; b < 2; ++b) {
-            cudaFree(m->stage[b]);
+            if (m->stage[b]) VCHECK(cudaFreeAsync(m->stage[b], m->stream));
             m->stage[b] = nullptr;
         }
         m->stage_cap = 0;
-        for (int b = 0; b < 2; ++b) VCHECK(cudaMalloc(&m->stage[b], sizeof(float) * 3 * n));
+        for (int b = 0; b < 2; ++b)
+            VCHECK(cudaMallocAsync(reinterpret_cast<void **>(&m->stage[b]), sizeof(float) * 3 * n, m->copy_stream));
         m->stage_cap = n;
     }
     const int b = m->parity;
