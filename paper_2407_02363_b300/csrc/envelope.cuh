@@ -327,10 +327,12 @@ struct Joined {
             if (tb >= 0) {
                 int jb = 0;
                 const int ib = k[b] - 1;
+                // the top band's kept range in scalars; the arrays are written back only
+                // when the top moves to another band and at the end of the junction
+                int ti = pick<NB>(i, tb), jt = pick<NB>(j, tb);
                 for (;;) {
-                    const int ti = pick<NB>(i, tb);
                     int sb = tb, si = ti - 1;   // entry below the top
-                    if (si < pick<NB>(j, tb)) {
+                    if (si < jt) {
                         sb = prev_band(tb);
                         si = sb >= 0 ? pick<NB>(i, sb) : 0;
                     }
@@ -344,10 +346,14 @@ struct Joined {
                         uint32_t rS;
                         at(sb * bl + si, cS, rS);
                         if (dominated<typename P::Prod>(cS, pol.h(rS, cS), cT, hT, cF, hF)) {
+                            if (--ti < jt) {   // the top band is used up: the band below takes over
 #pragma unroll
-                            for (int u = 0; u < NB; ++u)
-                                if (u == tb) i[u] = ti - 1;
-                            if (ti - 1 < pick<NB>(j, tb)) tb = sb;
+                                for (int u = 0; u < NB; ++u)
+                                    if (u == tb) i[u] = ti;
+                                tb = sb;
+                                ti = si;
+                                jt = pick<NB>(j, tb);
+                            }
                             continue;
                         }
                     }
@@ -363,8 +369,10 @@ struct Joined {
                     break;
                 }
 #pragma unroll
-                for (int u = 0; u < NB; ++u)
+                for (int u = 0; u < NB; ++u) {
+                    if (u == tb) i[u] = ti;
                     if (u == b) j[u] = jb;
+                }
             }
             tb = b;
         }
