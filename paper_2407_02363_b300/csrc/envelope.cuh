@@ -196,12 +196,13 @@ __device__ __forceinline__ void band_mask(const uint8_t *__restrict__ flags, int
 // Stack of proximate sites of one band over its valid positions lo + 32 w + (bit of
 // vm[w]), ascending; entry t ends in slot lo + t (input word in col, position in cp).
 //
-// The two top entries a (below) and b stay in registers.  While the stack holds fewer
-// than two entries, a is a sentinel that nothing dominates against (position b - 1,
-// h_b + 2^20: the right side of the test is then below -2^20, the left side above
-// -2^19), so the pop test needs no size check; a pop reloads a from the slot two below
-// the top, clamped to the band's first slot, and replaces it by the sentinel when the
-// stack has become too small.
+// The two top entries a (below) and b stay in registers.  The band's first valid site is
+// pushed before the sweep with a sentinel below it that nothing dominates against
+// (position b - 1, h_b + kBig, kBig above every h: the right side of the test is then
+// below -kBig, the left side above -kBig / 2), so the bottom entry is never popped,
+// every later push shifts b into a, and the pop test needs no size check; a pop reloads a
+// from the slot two below the top, clamped to the band's first slot, and takes the
+// sentinel again when one entry is left.
 template <int W, class P>
 __device__ __forceinline__ int build(const P &pol, typename P::In *col, typename P::Pos *cp, int lo,
                                      const uint32_t (&vm)[W], int cap, int32_t *err) {
@@ -210,9 +211,28 @@ __device__ __forceinline__ int build(const P &pol, typename P::In *col, typename
     using Pos = typename P::Pos;
     In *const in0 = col + lo * kC;   // the band's first slot
     Pos *const ps0 = cp + lo * kC;
-    // before the first push: a fake b at position -1 with h = 0 and a sentinel a below it,
-    // so that no candidate (position >= 0, h >= 0) can pop it
-    int k = 0, cb = -1, hb = 0, ca = -2, ha = kBig;
+    // the band's first valid site is pushed before the sweep, with the sentinel below it
+    uint32_t v[W];
+    int first = -1;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        v[w] = vm[w];
+        if (first < 0 && v[w]) {   // warp-uniform
+            first = lo + 32 * w + __ffs(v[w]) - 1;
+            v[w] &= v[w] - 1u;
+        }
+    }
+    if (first < 0) return 0;
+    const uint32_t r0 = col[first * kC];
+    int cb = first, hb = pol.h(r0, first);
+    const int cs = cb - 1, hs = hb + kBig;   // the sentinel below the bottom entry
+    int ca = cs, ha = hs, k = 1;
+    if constexpr (P::kPacked) {
+        in0[0] = static_cast<In>(P::pack(r0, first));
+    } else {
+        in0[0] = static_cast<In>(r0);
+        ps0[0] = static_cast<Pos>(first);
+    }
     auto step = [&](int c) {
         const uint32_t r = col[c * kC];
         const int hc = pol.h(r, c);
@@ -231,8 +251,8 @@ __device__ __forceinline__ int build(const P &pol, typename P::In *col, typename
                 h2 = pol.h(in0[s], c2);
             }
             const bool real = k >= 2;
-            ca = real ? c2 : cb - 1;
-            ha = real ? h2 : hb + kBig;
+            ca = real ? c2 : cs;
+            ha = real ? h2 : hs;
         }
         if (in_range(k, cap, err)) {   // debug builds: the stack never outgrows its band
             if constexpr (P::kPacked) {
@@ -242,20 +262,19 @@ __device__ __forceinline__ int build(const P &pol, typename P::In *col, typename
                 ps0[k * kC] = static_cast<Pos>(c);
             }
         }
-        const bool first = k == 0;
-        ca = first ? c - 1 : cb;
-        ha = first ? hc + kBig : hb;
+        ca = cb;
+        ha = hb;
         cb = c;
         hb = hc;
         ++k;
     };
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        uint32_t bits = vm[w];
+        uint32_t bits = v[w];
         const int base = lo + 32 * w;
-        if (bits == 0xFFFFFFFFu) {   // 32 valid positions in a row (warp-uniform)
+        if (bits != 0u && bits + (bits & (0u - bits)) == 0u) {   // one run of valid positions up to bit 31
 #pragma unroll 4
-            for (int c = base; c < base + 32; ++c) step(c);
+            for (int c = base + __ffs(bits) - 1; c < base + 32; ++c) step(c);
         } else {
             while (bits) {
                 const int c = base + __ffs(bits) - 1;
