@@ -142,3 +142,16 @@ def test_binding_refuses_to_load_without_the_library(tmp_path):
     r = subprocess.run([os.sys.executable, "-c", code], cwd=tmp_path, capture_output=True, text=True)
     assert r.returncode != 0
     assert "libvedt.so not built" in r.stderr
+
+def test_build_tracks_every_source_and_header():
+    """A change to any kernel source or header rebuilds the library: the up-to-date check
+    covers the .cu sources, the .h and .cuh headers beside them and the public header."""
+    import glob
+    import os
+    from paper_2407_02363_b300 import build
+    deps = set(build._deps())
+    csrc = os.path.join(os.path.dirname(build.__file__), "csrc")
+    for pattern in ("*.cu", "*.cuh", "*.h"):
+        files = glob.glob(os.path.join(csrc, pattern))
+        assert files and set(files) <= deps, pattern
+    assert any(p.endswith(os.path.join("include", "vedt.h")) for p in deps)
