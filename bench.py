@@ -46,7 +46,7 @@ WORKLOAD = ("frame256: 256^3 grid at 1 cm; 300k-point synthetic depth-camera clo
 # launches, one map per launch) with a hash of the kernel
 # sources it was taken from (comments and blank space excluded) and the algorithmic bytes
 # of the captured launch; reported only while both still match.
-NCU_TRAFFIC = {"edt_z": {"bytes": 111624960, "alg_bytes_per_launch": 167772160, "src": "2abdc1009827301c"}}
+NCU_TRAFFIC = {"edt_z": {"bytes": 111652736, "alg_bytes_per_launch": 167772160, "src": "8199909d7ba26ad2"}}
 KERNEL_SOURCES = ("paper_2407_02363_b300/csrc/envelope.cuh", "paper_2407_02363_b300/csrc/envelope.cu",
                   "paper_2407_02363_b300/csrc/vedt_internal.h")   # the code of k_env_z (pass Z)
 

@@ -58,7 +58,10 @@ __device__ __forceinline__ int find_tile_grid(const GridDesc *__restrict__ gd, i
 // x' | y' << 16, 16-bit positions (pass Z keeps them in the free bits of its sites, so
 // its tile needs no position array), 64-bit products in the domination test.  h(r, p) =
 // f(p) + p^2 for input word r at position p stays below 2^22, and the walk's sums below
-// 2^31, for lines up to 1024.
+// 2^31, for lines up to 1024.  kCachedRepair: the merge keeps its four entries in
+// registers (pass Z, where reloading an entry costs two dot products for h, or the
+// unpacking of a packed position) or reloads them (pass Y, where h is two operations and
+// the cache's bookkeeping costs as much as the reloads; both measured).
 
 // Pass Y: input word = the row's nearest site x' (pass X); f(p) = (x - x')^2.
 struct PolY {
@@ -67,6 +70,7 @@ struct PolY {
     using Prod = int;
     using Out = uint16_t;   // the 2-D site x' | y' << 8
     static constexpr int kMax = 256, kOutShift = 8, kBig = 1 << 20;
+    static constexpr bool kCachedRepair = false;
     static constexpr bool kPacked = false;
     int x;
     __device__ __forceinline__ int g(uint32_t r) const {
@@ -82,6 +86,7 @@ struct PolYL {
     using Prod = long long;
     using Out = uint32_t;   // x' | y' << 16
     static constexpr int kMax = 1024, kOutShift = 16, kBig = 1 << 23;
+    static constexpr bool kCachedRepair = false;
     static constexpr bool kPacked = false;
     int x;
     __device__ __forceinline__ int g(uint32_t r) const {
@@ -98,6 +103,7 @@ struct PolZ {
     using Pos = uint8_t;
     using Prod = int;
     static constexpr int kMax = 256, kBig = 1 << 20;
+    static constexpr bool kCachedRepair = true;
     static constexpr bool kPacked = false;
     uint32_t xy8;
     int K;
@@ -125,6 +131,7 @@ struct PolZL {
     using Pos = uint16_t;
     using Prod = long long;
     static constexpr int kMax = 1024, kBig = 1 << 23;
+    static constexpr bool kCachedRepair = true;
     static constexpr bool kPacked = true;
     int x, y;
     __device__ static PolZL at(int x, int y) { return PolZL{x, y}; }
@@ -332,6 +339,108 @@ struct Joined {
             if (u > b && j[u] <= i[u]) s = u;
         return s;
     }
+    // One junction of the merge: the joined prefix (top band tb, its kept entries jt .. ti)
+    // against band b (first kept entry jb of 0 .. ib).  Every step reloads T (the prefix's
+    // top), S (the entry below it) and F (band b's first kept entry), and G (the entry
+    // above F) where needed.
+    __device__ __forceinline__ void junction_reload(const P &pol, int b, int ib, int &tb, int &ti, int &jt, int &jb) {
+        for (;;) {
+            int sb = tb, si = ti - 1;   // entry below the top
+            if (si < jt) {
+                sb = prev_band(tb);
+                si = sb >= 0 ? pick<NB>(i, sb) : 0;
+            }
+            int cT, cF;
+            uint32_t rT, rF;
+            at(tb * bl + ti, cT, rT);
+            at(b * bl + jb, cF, rF);
+            const int hT = pol.h(rT, cT), hF = pol.h(rF, cF);
+            if (sb >= 0) {
+                int cS;
+                uint32_t rS;
+                at(sb * bl + si, cS, rS);
+                if (dominated<typename P::Prod>(cS, pol.h(rS, cS), cT, hT, cF, hF)) {
+                    if (--ti < jt) {   // the top band is used up: the band below takes over
+#pragma unroll
+                        for (int u = 0; u < NB; ++u)
+                            if (u == tb) i[u] = ti;
+                        tb = sb;
+                        ti = si;
+                        jt = pick<NB>(j, tb);
+                    }
+                    continue;
+                }
+            }
+            if (jb < ib) {
+                int cG;
+                uint32_t rG;
+                at(b * bl + jb + 1, cG, rG);
+                if (dominated<typename P::Prod>(cT, hT, cF, hF, cG, pol.h(rG, cG))) {
+                    ++jb;
+                    continue;
+                }
+            }
+            break;
+        }
+    }
+    // The same junction with T, S, F and G kept in registers: dropping T makes S the top
+    // and loads the next S, dropping F makes G the first entry and loads the next G, so a
+    // step loads one entry instead of three or four.
+    __device__ __forceinline__ void junction_cached(const P &pol, int b, int ib, int &tb, int &ti, int &jt, int &jb) {
+        int cT, cF, cS = 0, hS = 0, cG = 0, hG = 0;
+        uint32_t rT, rF;
+        at(tb * bl + ti, cT, rT);
+        at(b * bl + jb, cF, rF);
+        int hT = pol.h(rT, cT), hF = pol.h(rF, cF);
+        int sb, si;   // S's band (-1: no entry below T) and slot
+        auto below = [&]() {
+            sb = tb;
+            si = ti - 1;
+            if (si < jt) {
+                sb = prev_band(tb);
+                si = sb >= 0 ? pick<NB>(i, sb) : 0;
+            }
+            if (sb >= 0) {
+                uint32_t rS;
+                at(sb * bl + si, cS, rS);
+                hS = pol.h(rS, cS);
+            }
+        };
+        below();
+        bool g_ok = false;   // G loaded for the current F
+        for (;;) {
+            if (sb >= 0 && dominated<typename P::Prod>(cS, hS, cT, hT, cF, hF)) {
+                if (--ti < jt) {   // the top band is used up: the band below takes over
+#pragma unroll
+                    for (int u = 0; u < NB; ++u)
+                        if (u == tb) i[u] = ti;
+                    tb = sb;
+                    ti = si;
+                    jt = pick<NB>(j, tb);
+                }
+                cT = cS;
+                hT = hS;
+                below();
+                continue;
+            }
+            if (jb < ib) {
+                if (!g_ok) {
+                    uint32_t rG;
+                    at(b * bl + jb + 1, cG, rG);
+                    hG = pol.h(rG, cG);
+                    g_ok = true;
+                }
+                if (dominated<typename P::Prod>(cT, hT, cF, hF, cG, hG)) {
+                    ++jb;
+                    cF = cG;
+                    hF = hG;
+                    g_ok = false;
+                    continue;
+                }
+            }
+            break;
+        }
+    }
     // PBA-style merge of the band stacks of sizes k[b] (see the file comment)
     __device__ __forceinline__ void merge(const P &pol, const int (&k)[NB]) {
 #pragma unroll
@@ -345,48 +454,11 @@ struct Joined {
             if (k[b] == 0) continue;
             if (tb >= 0) {
                 int jb = 0;
-                const int ib = k[b] - 1;
                 // the top band's kept range in scalars; the arrays are written back only
                 // when the top moves to another band and at the end of the junction
                 int ti = pick<NB>(i, tb), jt = pick<NB>(j, tb);
-                for (;;) {
-                    int sb = tb, si = ti - 1;   // entry below the top
-                    if (si < jt) {
-                        sb = prev_band(tb);
-                        si = sb >= 0 ? pick<NB>(i, sb) : 0;
-                    }
-                    int cT, cF;
-                    uint32_t rT, rF;
-                    at(tb * bl + ti, cT, rT);
-                    at(b * bl + jb, cF, rF);
-                    const int hT = pol.h(rT, cT), hF = pol.h(rF, cF);
-                    if (sb >= 0) {
-                        int cS;
-                        uint32_t rS;
-                        at(sb * bl + si, cS, rS);
-                        if (dominated<typename P::Prod>(cS, pol.h(rS, cS), cT, hT, cF, hF)) {
-                            if (--ti < jt) {   // the top band is used up: the band below takes over
-#pragma unroll
-                                for (int u = 0; u < NB; ++u)
-                                    if (u == tb) i[u] = ti;
-                                tb = sb;
-                                ti = si;
-                                jt = pick<NB>(j, tb);
-                            }
-                            continue;
-                        }
-                    }
-                    if (jb < ib) {
-                        int cG;
-                        uint32_t rG;
-                        at(b * bl + jb + 1, cG, rG);
-                        if (dominated<typename P::Prod>(cT, hT, cF, hF, cG, pol.h(rG, cG))) {
-                            ++jb;
-                            continue;
-                        }
-                    }
-                    break;
-                }
+                if constexpr (P::kCachedRepair) junction_cached(pol, b, k[b] - 1, tb, ti, jt, jb);
+                else junction_reload(pol, b, k[b] - 1, tb, ti, jt, jb);
 #pragma unroll
                 for (int u = 0; u < NB; ++u) {
                     if (u == tb) i[u] = ti;
