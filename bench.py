@@ -905,7 +905,7 @@ def run_serving(args, v, dev):
 def run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream):
     """Frames end to end through the public host-buffer API: every step uploads its cloud
     from pinned host memory and reads its 2m sphere results back on the host.  Frames are
-    queued with vedt_frame_host_async two deep (the library uploads the next cloud while
+    queued with vedt_frame_host_async three deep (the library uploads the next cloud while
     the current frame computes); the host reads a frame's results as soon as its event
     completes."""
     import torch
@@ -914,7 +914,7 @@ def run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream):
     m_sph = len(spheres.radius)
     pinned = [torch.from_numpy(c).pin_memory() for c in W["clouds"]]
     lib_chain = v.make_chain(chain)
-    depth = 2
+    depth = 3   # two would leave one frame's time for the host's turnaround plus the upload
     item = v.SPHERE_DTYPE.itemsize
     outs = [torch.zeros(2 * m_sph * item, dtype=torch.uint8).pin_memory() for _ in range(depth)]
     evs = [torch.cuda.Event() for _ in range(depth)]
@@ -952,7 +952,7 @@ def run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream):
     e2e = {"value": 2 * N * args.e2e_steps * world / e2e_s / 1e9, "unit": "Gvoxel/s",
            "h2d_bytes_per_step": N_POINTS * 12 + m_sph * 16, "d2h_bytes_per_step": 2 * m_sph * item,
            "steps": args.e2e_steps, "ms_per_step": e2e_s / args.e2e_steps * 1e3,
-           "api": "vedt_sphere_centres + vedt_frame_host_async per step, two frames in flight (pinned host "
+           "api": "vedt_sphere_centres + vedt_frame_host_async per step, three frames in flight (pinned host "
                   "cloud in, sphere results read on the host every step)"}
     return e2e
 

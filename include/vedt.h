@@ -257,8 +257,10 @@ vedt_status vedt_frame(vedt_map *map, const float *xyz_dev, int64_t n_points,
 
 /* The same cycle from host buffers: copies xyz_host (n_points x 3 fp32; page-locked memory
  * makes the copy asynchronous) into one of the map's two device staging buffers (grown on
- * demand, ENOMEM if that fails) on the map's own copy stream, and centres/radii into
- * device scratch; runs vedt_frame on the map's stream once the upload has landed, delivers
+ * demand, ENOMEM if that fails) on the map's own copy stream, and centres/radii into one
+ * of four page-locked slots of the map that the query kernel reads in place (the call
+ * waits for the frame four back if that one still reads the slot); runs vedt_frame on the
+ * map's stream once the upload has landed, delivers
  * the 2m results (ENV block first) to out_host and synchronises the stream, reporting any
  * pending in-kernel error.  If out_host is page-locked memory the device can address (for
  * instance from cudaHostAlloc), the query kernel writes the results into it directly;
@@ -347,7 +349,8 @@ vedt_status vedt_batch_check(vedt_batch *batch);
  * last read that buffer has finished; so a frame queued behind a running one uploads while
  * the earlier one computes.  xyz_host and out_host must stay valid until vedt_frame_done
  * reports completion (page-locked memory keeps the copies asynchronous); centres/radii are
- * copied before the call returns. */
+ * copied (into the map's page-locked slot of this frame) before the call returns, which
+ * waits only if the frame queued four calls earlier is still running. */
 vedt_status vedt_frame_host_async(vedt_map *map, const float *xyz_host, int64_t n_points,
                                   const float *T_world_sensor_host, const vedt_chain *chain, const double *q,
                                   uint32_t link_mask, const float *centres_host, const float *radii_host,

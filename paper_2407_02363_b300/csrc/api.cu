@@ -197,9 +197,11 @@ void free_map(vedt_map *m) {
     for (int b = 0; b < 2; ++b) {
         cudaFree(m->stage[b]);
         if (m->copied[b]) cudaEventDestroy(m->copied[b]);
-        if (m->consumed[b]) cudaEventDestroy(m->consumed[b]);
     }
+    for (int s = 0; s < kQRing; ++s)
+        if (m->fdone[s]) cudaEventDestroy(m->fdone[s]);
     if (m->copy_stream) cudaStreamDestroy(m->copy_stream);
+    if (m->pin_q) cudaFreeHost(m->pin_q);
     if (m->side_stream) cudaStreamDestroy(m->side_stream);
     if (m->links_done) cudaEventDestroy(m->links_done);
     if (m->self_done) cudaEventDestroy(m->self_done);
@@ -309,8 +311,8 @@ vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float
     const size_t desc_bytes = sizeof(GridDesc) * 4, tm_bytes = sizeof(CUtensorMap) * 8;
     if (e == cudaSuccess) e = cudaMalloc(&m->tab_mem, desc_bytes + tm_bytes + 256);
     if (e == cudaSuccess) e = cudaMalloc(&m->qgrids, sizeof(QueryGrid) * 4);
-    // three query input areas: vedt_query_spheres, then one per host-frame staging parity
-    if (e == cudaSuccess) e = cudaMalloc(&m->q_in, sizeof(float) * 3 * 4 * kMaxQuery);
+    // query input area of vedt_query_spheres (host frames read page-locked slots in place)
+    if (e == cudaSuccess) e = cudaMalloc(&m->q_in, sizeof(float) * 4 * kMaxQuery);
     if (e == cudaSuccess) e = cudaMalloc(&m->q_out, sizeof(vedt_sphere_result) * 2 * kMaxQuery);
     if (e != cudaSuccess) {
         free_map(m);
@@ -337,6 +339,8 @@ vedt_status vedt_map_create(const int32_t dims[3], float voxel_size, const float
 vedt_status vedt_map_destroy(vedt_map *m) {
     if (!m) return VEDT_OK;
     cudaStreamSynchronize(m->stream);
+    for (cudaStream_t x : {m->side_stream, m->copy_stream})
+        if (x) cudaStreamSynchronize(x);
     free_map(m);
     return VEDT_OK;
 }
@@ -734,28 +738,36 @@ vedt_status vedt_frame(vedt_map *m, const float *xyz, int64_t n, const float *T,
 namespace {
 
 // Queues one cycle from host buffers on the map's stream.  The cloud goes to staging
-// buffer `parity` on the copy stream, after the frame that last read that buffer has
-// finished, so the upload overlaps the previous frame's kernels; the map's stream waits
-// for the upload before the frame's kernels.
+// buffer h % 2 on the copy stream once the frame that last read that buffer (h - 2) has
+// finished, so the upload overlaps the previous frame's kernels, and the map's stream
+// waits for it before the frame's kernels; the sphere centres and radii go to page-locked
+// slot h % kQRing, which the frame's query reads in place.
 vedt_status queue_host_frame(vedt_map *m, const float *xyz, int64_t n, const float *T, const vedt_chain *chain,
                              const double *q, uint32_t mask, const float *centres, const float *radii, int nq,
                              vedt_sphere_result *out) {
     if (!m->copy_stream) {   // created together, or not at all
+        constexpr int kEv = 2 + kQRing;
         cudaStream_t cs = nullptr;
-        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+        cudaEvent_t ev[kEv] = {};
+        float *pin = nullptr;
+        void *pin_dev = nullptr;
         cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-        for (int j = 0; j < 4 && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
+        for (int j = 0; j < kEv && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(reinterpret_cast<void **>(&pin), sizeof(float) * kQRing * 4 * kMaxQuery, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&pin_dev, pin, 0);
         if (e != cudaSuccess) {
+            if (pin) cudaFreeHost(pin);
             for (cudaEvent_t x : ev)
                 if (x) cudaEventDestroy(x);
             if (cs) cudaStreamDestroy(cs);
             return from_cuda(e);
         }
         m->copy_stream = cs;
-        for (int b = 0; b < 2; ++b) {
-            m->copied[b] = ev[2 * b];
-            m->consumed[b] = ev[2 * b + 1];
-        }
+        m->pin_q = pin;
+        m->pin_q_dev = static_cast<const float *>(pin_dev);
+        for (int b = 0; b < 2; ++b) m->copied[b] = ev[b];
+        for (int r = 0; r < kQRing; ++r) m->fdone[r] = ev[2 + r];
     }
     if (n > m->stage_cap) {
         // Grow both buffers without synchronising the device (cudaFree would wait for every
@@ -771,23 +783,26 @@ vedt_status queue_host_frame(vedt_map *m, const float *xyz, int64_t n, const flo
             VCHECK(cudaMallocAsync(reinterpret_cast<void **>(&m->stage[b]), sizeof(float) * 3 * n, m->copy_stream));
         m->stage_cap = n;
     }
-    const int b = m->parity;
-    m->parity ^= 1;
-    // the cloud and the sphere inputs go up on the copy stream (the map's stream then has
-    // one event wait between frames instead of copies, which would end the programmatic
-    // overlap of one frame's last kernel with the next frame's first)
-    float *qin = m->q_in + (1 + b) * 4 * kMaxQuery;
-    if (n > 0 || nq > 0) {
-        VCHECK(cudaStreamWaitEvent(m->copy_stream, m->consumed[b], 0));
-        if (n > 0)
-            VCHECK(cudaMemcpyAsync(m->stage[b], xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->copy_stream));
-        if (nq > 0) {
-            VCHECK(cudaMemcpyAsync(qin, centres, sizeof(float) * 3 * nq, cudaMemcpyHostToDevice, m->copy_stream));
-            VCHECK(cudaMemcpyAsync(qin + 3 * kMaxQuery, radii, sizeof(float) * nq, cudaMemcpyHostToDevice,
-                                   m->copy_stream));
-        }
+    const int64_t h = m->hframes++;
+    const int b = static_cast<int>(h & 1), r = static_cast<int>(h % kQRing);
+    // the upload goes on the copy stream (the map's stream then has an event wait between
+    // frames instead of a copy, which would end the programmatic overlap of one frame's
+    // last kernel with the next frame's first); fdone[x] holds its latest record, the end
+    // of the last frame queued in slot x
+    if (n > 0) {
+        if (h >= 2) VCHECK(cudaStreamWaitEvent(m->copy_stream, m->fdone[(h - 2) % kQRing], 0));
+        VCHECK(cudaMemcpyAsync(m->stage[b], xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->copy_stream));
         VCHECK(cudaEventRecord(m->copied[b], m->copy_stream));
         VCHECK(cudaStreamWaitEvent(m->stream, m->copied[b], 0));
+    }
+    const float *qin = m->pin_q_dev + static_cast<size_t>(r) * 4 * kMaxQuery;
+    if (nq > 0) {
+        // slot r was last read by the query of the frame kQRing back: wait for it on the
+        // host (at once unless the caller runs kQRing frames ahead of the device)
+        if (h >= kQRing) VCHECK(cudaEventSynchronize(m->fdone[r]));
+        float *pq = m->pin_q + static_cast<size_t>(r) * 4 * kMaxQuery;
+        std::memcpy(pq, centres, sizeof(float) * 3 * nq);
+        std::memcpy(pq + 3 * kMaxQuery, radii, sizeof(float) * nq);
     }
     // The results go straight into the caller's buffer when it is page-locked host memory
     // the device can address: the query kernel's stores then reach the host with the
@@ -806,7 +821,7 @@ vedt_status queue_host_frame(vedt_map *m, const float *xyz, int64_t n, const flo
     vedt_status st =
         vedt_frame(m, m->stage[b], n, T, chain, q, mask, qin, qin + 3 * kMaxQuery, nq, direct ? direct : m->q_out);
     if (st != VEDT_OK) return st;
-    VCHECK(cudaEventRecord(m->consumed[b], m->stream));
+    VCHECK(cudaEventRecord(m->fdone[r], m->stream));
     if (nq > 0 && !direct)
         VCHECK(cudaMemcpyAsync(out, m->q_out, sizeof(vedt_sphere_result) * 2 * nq, cudaMemcpyDeviceToHost,
                                m->stream));
