@@ -88,6 +88,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=("vedt", "reference"), default="vedt")
     p.add_argument("--e2e-steps", type=int, default=200)
+    p.add_argument("--e2e-depth", type=int, default=3, help="host frames in flight in the e2e leg")
     p.add_argument("--bands", type=int, default=0,
                    help="bands per line for the frame workload (0: the autotuner's pick; fixed for profiling runs)")
     p.add_argument("--tile-z", type=int, default=0,
@@ -914,7 +915,7 @@ def run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream):
     m_sph = len(spheres.radius)
     pinned = [torch.from_numpy(c).pin_memory() for c in W["clouds"]]
     lib_chain = v.make_chain(chain)
-    depth = 3   # two would leave one frame's time for the host's turnaround plus the upload
+    depth = max(1, args.e2e_depth)   # two leave one frame's time for the host's turnaround plus the upload
     item = v.SPHERE_DTYPE.itemsize
     outs = [torch.zeros(2 * m_sph * item, dtype=torch.uint8).pin_memory() for _ in range(depth)]
     evs = [torch.cuda.Event() for _ in range(depth)]
@@ -952,7 +953,8 @@ def run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream):
     e2e = {"value": 2 * N * args.e2e_steps * world / e2e_s / 1e9, "unit": "Gvoxel/s",
            "h2d_bytes_per_step": N_POINTS * 12 + m_sph * 16, "d2h_bytes_per_step": 2 * m_sph * item,
            "steps": args.e2e_steps, "ms_per_step": e2e_s / args.e2e_steps * 1e3,
-           "api": "vedt_sphere_centres + vedt_frame_host_async per step, three frames in flight (pinned host "
+           "frames_in_flight": depth,
+           "api": "vedt_sphere_centres + vedt_frame_host_async per step, frames_in_flight frames queued (pinned host "
                   "cloud in, sphere results read on the host every step)"}
     return e2e
 
