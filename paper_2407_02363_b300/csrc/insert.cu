@@ -162,15 +162,20 @@ __global__ void __launch_bounds__(128) k_query(const QueryGrid *__restrict__ gri
                                                const float *__restrict__ radii, int m,
                                                vedt_sphere_result *__restrict__ out) {
     pdl_trigger();
-    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m * ng) return;
     const int g = t / m, i = t - g * m;
+    // The sphere inputs and the grids' descriptors are written by the host (or by the
+    // caller's work before the frame's first kernel, which cannot start until that work
+    // has finished), not by the kernels this one waits for: read them before the wait,
+    // so that only the field loads follow it.
+    const float cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2], rad = radii[i];
+    const int32_t *sqp = grids[g].sqdist, *ixp = grids[g].idx;
     vedt_sphere_result r;
     int v[3];
-    const bool inside = voxel_coord(centres[3 * i], org.o[0], vs, X, v[0]) &&
-                        voxel_coord(centres[3 * i + 1], org.o[1], vs, Y, v[1]) &&
-                        voxel_coord(centres[3 * i + 2], org.o[2], vs, Z, v[2]);
+    const bool inside = voxel_coord(cx, org.o[0], vs, X, v[0]) && voxel_coord(cy, org.o[1], vs, Y, v[1]) &&
+                        voxel_coord(cz, org.o[2], vs, Z, v[2]);
+    pdl_wait();   // the fields come from the EDT passes; the results buffer may have been read before
     if (!inside) {
         r.sqdist = -1;
         r.idx = -1;
@@ -182,8 +187,8 @@ __global__ void __launch_bounds__(128) k_query(const QueryGrid *__restrict__ gri
         return;
     }
     const int64_t id = v[0] + static_cast<int64_t>(X) * (v[1] + static_cast<int64_t>(Y) * v[2]);
-    r.sqdist = grids[g].sqdist[id];
-    r.idx = grids[g].idx[id];
+    r.sqdist = sqp[id];
+    r.idx = ixp[id];
     if (r.idx < 0) {
         r.dist = __int_as_float(0x7f800000);
         r.clearance = r.dist;
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(128) k_query(const QueryGrid *__restrict__ gri
         return;
     }
     r.dist = __fmul_rn(vs, __fsqrt_rn(static_cast<float>(r.sqdist)));
-    r.clearance = __fsub_rn(r.dist, radii[i]);
+    r.clearance = __fsub_rn(r.dist, rad);
     const int j = r.idx;
     const int nv[3] = {j % X, (j / X) % Y, j / (X * Y)};
     for (int a = 0; a < 3; ++a)
