@@ -155,6 +155,8 @@ def gpu_preroll(stream, frames, ms_per_frame=0.25):
     over 200 us per frame); the host-inclusive rate is the e2e leg's.  The spin ends on its
     own after a fixed number of cycles and sits before the first timing event."""
     import torch
+    if not hasattr(torch.cuda, "_sleep"):   # a torch without the spin kernel: no pre-roll
+        return
     cycles = int(min(frames, 100) * ms_per_frame * 1e-3 * 2.032e9)
     with torch.cuda.stream(stream):
         torch.cuda._sleep(cycles)
