@@ -147,12 +147,13 @@ def reduce_max(x, world, device="cpu"):
 # ------------------------------------------------------------------------------------
 # workload
 # ------------------------------------------------------------------------------------
-def gpu_preroll(stream, frames, ms_per_frame=0.25):
+def gpu_preroll(stream, frames, ms_per_frame=0.5):
     """Keeps `stream` busy for about `frames` x `ms_per_frame` (at most 100 frames' worth)
     with a clock-spin kernel, so that the host can queue the frames that follow before the
     GPU reaches them.  The device timings of those frames then hold no gap from the host's
     submission (on a shared box the Python loop and the launch calls vary from about 40 to
-    over 200 us per frame); the host-inclusive rate is the e2e leg's.  The spin ends on its
+    over 200 us per frame, so the default leaves 500 us per frame); the host-inclusive rate
+    is the e2e leg's.  The spin ends on its
     own after a fixed number of cycles and sits before the first timing event."""
     import torch
     if not hasattr(torch.cuda, "_sleep"):   # a torch without the spin kernel: no pre-roll
