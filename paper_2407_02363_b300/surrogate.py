@@ -105,18 +105,30 @@ class EvalResult:
 
 def evaluate(pred, exact, valid, margin=0.05):
     """Errors (mm) over valid entries; a configuration falls back to the exact path if any
-    valid predicted distance is below `margin`; it is missed if it does not fall back but
-    some valid exact distance is below 5 cm."""
+    valid predicted distance is below its sphere's margin (`margin`: one value for every
+    sphere, or one per sphere); it is missed if it does not fall back but some valid exact
+    distance is below 5 cm.  margin_m reports the largest margin."""
     err = np.abs(pred - exact)[valid] * 1000.0
     big = np.where(valid, pred, np.inf)
-    fallback = (big < margin).any(axis=1)
+    fallback = (big < np.asarray(margin)).any(axis=1)
     near = (np.where(valid, exact, np.inf) < 0.05).any(axis=1)
     missed = near & ~fallback
     return EvalResult(max_err_mm=float(err.max()) if err.size else 0.0,
                       p99_err_mm=float(np.percentile(err, 99)) if err.size else 0.0,
                       mean_err_mm=float(err.mean()) if err.size else 0.0,
                       fallback_rate=float(fallback.mean()), missed_rate=float(missed.mean()),
-                      margin_m=float(margin), n=int(pred.shape[0]))
+                      margin_m=float(np.max(margin)), n=int(pred.shape[0]))
+
+
+def sphere_margins(pred, exact, valid, base=0.05):
+    """Per-sphere safety margins from a calibration set: base + the largest |error| of that
+    sphere over its valid entries (base alone for a sphere with none).  If every error of a
+    sphere stays within its calibration maximum, a prediction at or above the margin means
+    an exact distance of at least `base`: pred < exact + e_max < base + e_max whenever
+    exact < base.  A single margin (base + the largest error of any sphere) is the special
+    case of the worst sphere; spheres whose network is more accurate fall back less."""
+    err = np.where(valid, np.abs(pred - exact), 0.0)
+    return base + err.max(axis=0)
 
 
 def train(net, q, y, mask, steps, batch=8192, lr=2e-3, wd=1e-4, seed=0, log_every=0):
@@ -185,7 +197,8 @@ def fit(lab, net, n_train, n_val, seed, steps, batch=8192, lr=2e-3, near_weight=
     """Labels n_train + n_val seeded configurations on the exact path, trains `net` on
     the clipped valid distances (weighted toward small distances, `near_weights`) and
     returns (history, validation EvalResult, the safety margin = 5 cm + validation max
-    error, label throughput in configurations/s)."""
+    error, label throughput in configurations/s, the per-sphere margins of
+    `sphere_margins` on the validation set)."""
     import torch
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
     q_tr = synth.joint_states(seed, n_train)
@@ -198,8 +211,9 @@ def fit(lab, net, n_train, n_val, seed, steps, batch=8192, lr=2e-3, near_weight=
     hist = train(net, dev(q_tr), dev(y_tr), dev(w_tr), steps=steps, batch=batch, lr=lr, log_every=log_every)
     q_va = synth.joint_states(seed + 1, n_val)
     d_va, s_va = lab(q_va)
-    r_va = evaluate(clip(predict(net, dev(q_va)).cpu().numpy()), clip(d_va), lab.valid_mask(s_va))
-    return hist, r_va, 0.05 + r_va.max_err_mm / 1000.0, label_qps
+    p_va, y_va, m_va = clip(predict(net, dev(q_va)).cpu().numpy()), clip(d_va), lab.valid_mask(s_va)
+    r_va = evaluate(p_va, y_va, m_va)
+    return hist, r_va, 0.05 + r_va.max_err_mm / 1000.0, label_qps, sphere_margins(p_va, y_va, m_va)
 
 
 def throughput(fn, n_items, reps=5, warmup=2):

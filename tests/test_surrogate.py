@@ -22,6 +22,37 @@ def test_evaluate_fallback_and_missed_bookkeeping():
     assert np.isclose(r.max_err_mm, 30.0)
 
 
+def test_sphere_margins_are_safe_on_their_calibration_set_and_fall_back_less():
+    """Per-sphere margins (5 cm + each sphere's largest validation error) never miss a
+    near configuration of the set they were calibrated on, equal the single margin for the
+    worst sphere, and send fewer configurations to the exact path when the other spheres
+    are more accurate.  A margin set from the wrong sphere's errors does miss."""
+    from paper_2407_02363_b300.surrogate import evaluate, sphere_margins
+    rng = np.random.default_rng(7)
+    n, m = 20000, 6
+    exact = rng.uniform(0.0, 0.35, size=(n, m))
+    scale = np.array([0.002, 0.004, 0.008, 0.016, 0.03, 0.06])      # sphere 5 is the worst
+    pred = exact + rng.normal(0.0, 1.0, size=(n, m)) * scale
+    valid = rng.random((n, m)) > 0.1
+    margins = sphere_margins(pred, exact, valid)
+    one = 0.05 + np.abs(pred - exact)[valid].max()
+    assert np.isclose(margins.max(), one) and int(np.argmax(margins)) == 5
+    err = np.where(valid, np.abs(pred - exact), 0.0).max(axis=0)
+    assert np.allclose(margins, 0.05 + err)
+    r_sph, r_one = evaluate(pred, exact, valid, margins), evaluate(pred, exact, valid, one)
+    assert r_sph.missed_rate == 0.0 and r_one.missed_rate == 0.0
+    assert r_sph.fallback_rate < r_one.fallback_rate
+    assert np.isclose(r_sph.margin_m, one)
+    # the worst sphere's margin taken from the best sphere's errors: its near entries slip
+    wrong = margins.copy()
+    wrong[5] = margins[0]
+    assert evaluate(pred, exact, valid, wrong).missed_rate > 0.0
+    # a sphere with no valid entry keeps the base margin
+    v2 = valid.copy()
+    v2[:, 2] = False
+    assert np.isclose(sphere_margins(pred, exact, v2)[2], 0.05)
+
+
 def _setup():
     chain = synth.make_chain(1234 + 4000, (1.28, 1.28, 1.28))
     spheres = synth.sphere_model(chain)
@@ -82,7 +113,9 @@ def test_surrogate_trains_and_hybrid_beats_exact_safely():
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
     net = v.MLP(65536)
     net.set_params(omlp.init_params(0).astype(np.float32))
-    hist, r_va, margin, _ = sg.fit(lab, net, n_train=262144, n_val=8192, seed=1, steps=12000, log_every=4000)
+    hist, r_va, margin, _, margins = sg.fit(lab, net, n_train=262144, n_val=8192, seed=1, steps=12000,
+                                            log_every=4000)
+    assert margins.shape == (24,) and np.all(margins <= margin + 1e-7) and np.all(margins >= 0.05)
     assert hist[-1][1] < 0.2 * hist[0][1], hist
     q_te = synth.joint_states(3, 8192)
     d_te, s_te = lab(q_te)
@@ -90,6 +123,8 @@ def test_surrogate_trains_and_hybrid_beats_exact_safely():
     r_te = sg.evaluate(p_te, sg.clip(d_te), lab.valid_mask(s_te), margin=margin)
     assert r_te.p99_err_mm < 45.0, r_te
     assert r_te.missed_rate == 0.0, r_te
+    r_sph = sg.evaluate(p_te, sg.clip(d_te), lab.valid_mask(s_te), margin=margins)
+    assert r_sph.missed_rate == 0.0 and r_sph.fallback_rate <= r_te.fallback_rate, (r_sph, r_te)
     # throughput: exact labels vs surrogate + exact fallback on the flagged fraction
     qd = dev(synth.joint_states(4, 65536))
     out = torch.empty((65536, 24), device="cuda")
