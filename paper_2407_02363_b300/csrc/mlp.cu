@@ -489,6 +489,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     const int T = static_cast<int>(blockIdx.x) < n_tiles ? (n_tiles - 1 - static_cast<int>(blockIdx.x)) / gridDim.x + 1 : 0;
     const int pairs = (T + 1) / 2;
     auto tile_row0 = [&](int i) { return (static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x)) * 128; };
+    // A forward launched right after another starts placing its CTAs as the previous grid's
+    // leave their SMs; everything up to the dependency wait below touches only on-chip
+    // state (tensor memory, shared-memory barriers; the biases are launch parameters).
+    pdl_trigger();
     if (warp == 0) tmem_alloc(&tmem_base, 512);
     if (tid == 0) {
         for (int k = 0; k < kStages; ++k) {
@@ -505,6 +509,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = tmem_base;
+    pdl_wait();   // weights, joint angles and outputs may belong to the previous kernels
 
     if (warp == 0 && lane == 0) {
         // ---- weight producer: one thread fills the ring in consumption order (chunk it goes
@@ -884,8 +889,8 @@ bool check_rows(const vedt_mlp *n, int B) { return n && B >= 1 && B <= n->cap; }
 // persistent grid: one CTA per SM, capped by the number of 128-row tiles
 cudaError_t launch_fused(const vedt_mlp *n, const float *q, int B, const FusedArgs &a, float *out) {
     const int tiles = (B + 127) / 128;
-    k_mlp_fused<<<std::min(tiles, n->sms), kFusedThreads, kFusedSmem, n->stream>>>(q, B, a, out, n->err);
-    return cudaGetLastError();
+    return launch_pdl(k_mlp_fused, dim3(std::min(tiles, n->sms)), dim3(kFusedThreads), kFusedSmem, n->stream, q, B,
+                      a, out, n->err);
 }
 
 }  // namespace
