@@ -952,6 +952,7 @@ def run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream):
     m_sph = len(spheres.radius)
     pinned = [torch.from_numpy(c).pin_memory() for c in W["clouds"]]
     lib_chain = v.make_chain(chain)
+    centres_of = v.SphereCentres(lib_chain, spheres)
     depth = max(1, args.e2e_depth)   # two leave one frame's time for the host's turnaround plus the upload
     item = v.SPHERE_DTYPE.itemsize
     outs = [torch.zeros(2 * m_sph * item, dtype=torch.uint8).pin_memory() for _ in range(depth)]
@@ -969,7 +970,7 @@ def run_e2e(args, v, m, W, n_frames, cchain, world, dev, stream):
                 evs[slot].synchronize()
                 read(slot)
             # C_i <- FK(q) on the host for every step (Alg. 2 line 8), inside the timed loop
-            cen = v.sphere_centres(lib_chain, spheres, W["traj"][k])
+            cen = centres_of(W["traj"][k])
             m.frame_host_async(pinned[k], cchain, W["traj"][k], SELF_MASK, cen, spheres.radius, outs[slot])
             evs[slot].record(stream)
         for i in range(max(0, steps - depth), steps):

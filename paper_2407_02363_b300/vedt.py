@@ -141,7 +141,9 @@ def _chk(st, where):
 
 
 def _np_ptr(a):
-    return a.ctypes.data_as(ctypes.c_void_p)
+    """Address of a numpy array's data for a C call.  Every caller binds the array to a name
+    that outlives the call (the integer keeps no reference to it)."""
+    return a.__array_interface__["data"][0]
 
 
 def dev_ptr(x):
@@ -235,6 +237,27 @@ def sphere_centres(chain, spheres, q) -> np.ndarray:
     _chk(_lib.vedt_sphere_centres(ctypes.byref(c), _np_ptr(qa), lk.shape[0], _np_ptr(lk), _np_ptr(lc),
                                   _np_ptr(out)), "vedt_sphere_centres")
     return out
+
+
+class SphereCentres:
+    """sphere_centres for one chain and sphere set, called once per control cycle: the
+    sphere arrays and the (m, 3) result buffer are set up once and their addresses kept,
+    so a call converts only the joint vector.  Each call returns the same buffer,
+    overwritten; copy it to keep a cycle's centres."""
+
+    def __init__(self, chain, spheres):
+        self._chain = chain if isinstance(chain, Chain) else make_chain(chain)
+        self._lk = np.ascontiguousarray(spheres.link, dtype=np.int32)
+        self._lc = np.ascontiguousarray(spheres.local, dtype=np.float64).reshape(-1, 3)
+        self.out = np.zeros((self._lk.shape[0], 3), dtype=np.float32)
+        self._args = (ctypes.byref(self._chain), self._lk.shape[0], _np_ptr(self._lk), _np_ptr(self._lc),
+                      _np_ptr(self.out))
+
+    def __call__(self, q) -> np.ndarray:
+        qa = np.ascontiguousarray(q, dtype=np.float64)
+        cref, m, lk, lc, out = self._args
+        _chk(_lib.vedt_sphere_centres(cref, _np_ptr(qa), m, lk, lc, out), "vedt_sphere_centres")
+        return self.out
 
 
 def sphere_centres_batch(chain, spheres, q) -> np.ndarray:

@@ -102,11 +102,14 @@ def test_sphere_centres_bitequal_to_oracle(v, oracle_mod):
     qs = synth.joint_states(6, 12)
     for sph in (spheres, off_axis):
         batch = v.sphere_centres_batch(chain, sph, qs)
+        per_cycle = v.SphereCentres(chain, sph)   # the cached per-cycle form
         for i, q in enumerate(qs):
             want = oracle_mod.sphere_centres(chain, sph, q)
             got = v.sphere_centres(chain, sph, q)
             assert got.dtype == np.float32 and np.array_equal(got, want)
             assert np.array_equal(batch[i], want)
+            cyc = per_cycle(q)
+            assert cyc is per_cycle.out and np.array_equal(cyc, want)   # one buffer, overwritten
 
 
 def test_sphere_centres_rejects_bad_arguments(v):
