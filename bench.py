@@ -87,7 +87,9 @@ def parse():
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=("vedt", "reference"), default="vedt")
-    p.add_argument("--e2e-steps", type=int, default=200)
+    p.add_argument("--e2e-steps", type=int, default=1000,
+                   help="end-to-end steps timed (1000: 0.2 s, so that filling and draining the frames in flight "
+                        "weighs little)")
     p.add_argument("--e2e-depth", type=int, default=3, help="host frames in flight in the e2e leg")
     p.add_argument("--bands", type=int, default=0,
                    help="bands per line for the frame workload (0: the autotuner's pick; fixed for profiling runs)")
