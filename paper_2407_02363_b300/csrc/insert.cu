@@ -135,24 +135,38 @@ __global__ void __launch_bounds__(256) k_insert_points(uint8_t *__restrict__ env
 }
 
 // UpdateLinks + Insert(O_Lk) (Alg. 2 lines 5-6): every registered link point is moved by
-// its link's pose and marked in the self map if its link is in the mask.
+// its link's pose and marked in the self map if its link is in the mask.  The link points
+// and their link indices are copied to the device when the links are registered, before
+// any frame, and the poses are launch parameters: a thread loads and places its first
+// point before the dependency wait (overlapping the tail of the clear before it) and only
+// the store into the self map follows the wait.
+__device__ __forceinline__ int64_t link_voxel(const float *__restrict__ pts, const uint8_t *__restrict__ link_of,
+                                              int64_t i, const LinkPose &poses, uint32_t mask, int X, int Y, int Z,
+                                              float vs, const Origin &org) {
+    const int k = link_of[i];
+    if (!((mask >> k) & 1u)) return -1;
+    float wx, wy, wz;
+    rigid(poses.T[k], __ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2), wx, wy, wz);
+    int vx, vy, vz;
+    if (!voxel_coord(wx, org.o[0], vs, X, vx) || !voxel_coord(wy, org.o[1], vs, Y, vy) ||
+        !voxel_coord(wz, org.o[2], vs, Z, vz))
+        return -1;
+    return vx + static_cast<int64_t>(X) * (vy + static_cast<int64_t>(Y) * vz);
+}
+
 __global__ void __launch_bounds__(256) k_insert_links(uint8_t *__restrict__ self, int X, int Y, int Z, float vs,
                                                       Origin org, const float *__restrict__ pts,
                                                       const uint8_t *__restrict__ link_of, int64_t n,
                                                       LinkPose poses, uint32_t mask) {
     pdl_trigger();
-    pdl_wait();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int k = link_of[i];
-        if (!((mask >> k) & 1u)) continue;
-        float wx, wy, wz;
-        rigid(poses.T[k], __ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2), wx, wy, wz);
-        int vx, vy, vz;
-        if (!voxel_coord(wx, org.o[0], vs, X, vx) || !voxel_coord(wy, org.o[1], vs, Y, vy) ||
-            !voxel_coord(wz, org.o[2], vs, Z, vz))
-            continue;
-        self[vx + static_cast<int64_t>(X) * (vy + static_cast<int64_t>(Y) * vz)] = 1;
+    int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t first = i < n ? link_voxel(pts, link_of, i, poses, mask, X, Y, Z, vs, org) : -1;
+    pdl_wait();   // the self map is cleared by the previous kernel
+    if (first >= 0) self[first] = 1;
+    for (i += stride; i < n; i += stride) {
+        const int64_t id = link_voxel(pts, link_of, i, poses, mask, X, Y, Z, vs, org);
+        if (id >= 0) self[id] = 1;
     }
 }
 
