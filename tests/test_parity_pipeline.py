@@ -173,6 +173,68 @@ def test_frame_api_full_size_on_two_streams(timing):
     m.close()
 
 
+def test_frame_api_back_to_back_without_host_syncs():
+    """Frames queued back to back on the map's stream, as the bench times them: no host
+    synchronisation between frames, so each frame's first kernels overlap the previous
+    frame's last ones.  Every frame writes its sphere results to a buffer of its own; each
+    frame's results, and the last frame's fields, against the oracle."""
+    v = lib()
+    grid = synth.GridSpec((256, 256, 256), 0.01)
+    scene = synth.CameraScene(1234 + 2000, grid)
+    chain = synth.make_chain(1234 + 2000, (1.28, 1.28, 1.28))
+    links = synth.link_models(chain, grid.voxel_size)
+    spheres = synth.sphere_model(chain)
+    traj = synth.joint_trajectory(1234 + 2000, 40)
+    m = v.Map(grid.dims, grid.voxel_size, grid.origin, stream=torch.cuda.Stream())
+    m.register_links(links)
+    cchain = v.make_chain(chain)
+    nm = len(spheres.radius)
+    radii = torch.from_numpy(spheres.radius).cuda()
+    frames = (20, 21, 22, 23)
+    clouds = {f: scene.frame(f) for f in frames}
+    cl = {f: torch.from_numpy(clouds[f]).cuda() for f in frames}
+    cen_np = {f: oracle.sphere_centres(chain, spheres, traj[f]) for f in frames}
+    cen = {f: torch.from_numpy(cen_np[f]).cuda() for f in frames}
+    outs = {f: torch.empty(2 * nm * 32, dtype=torch.uint8, device="cuda") for f in frames}
+    torch.cuda.synchronize()
+    for f in frames:
+        m.frame(cl[f], cl[f].shape[0], cchain, traj[f], SELF_MASK, cen[f], radii, nm, outs[f])
+    m.check()
+    X, Y, Z = grid.dims
+    for f in frames:
+        poses = v.fk(chain, traj[f]).astype(np.float32)
+        o_self = np.zeros((Z, Y, X), np.uint8)
+        oracle.insert_links(o_self, grid.dims, grid.voxel_size, grid.origin, links, poses, SELF_MASK)
+        o_env = np.zeros((Z, Y, X), np.uint8)
+        oracle.insert_points(o_env, o_self, grid.dims, grid.voxel_size, grid.origin, clouds[f], filter_self=True)
+        res = outs[f].cpu().numpy().view(v.SPHERE_DTYPE)
+        for k, (g, occ) in enumerate(((v.MAP_ENV, o_env), (v.MAP_SELF, o_self))):
+            osq, oix = oracle.edt(occ)
+            if f == frames[-1]:
+                sq, ix = (t.cpu().numpy() for t in m.field(g))
+                assert np.array_equal(sq, osq)
+                check_idx_valid(occ, sq, ix)
+            expect = oracle.query_spheres(osq, oix, grid.dims, grid.voxel_size, grid.origin, cen_np[f],
+                                          spheres.radius)
+            got = res[k * nm:(k + 1) * nm].copy()
+            exp = np.zeros(nm, dtype=got.dtype)
+            for name in exp.dtype.names:
+                exp[name] = expect[name]
+            # the nearest voxel may be any occupied voxel at that distance: compare what is
+            # unique bit for bit, and check that the returned voxel is one of them
+            assert np.array_equal(got["sqdist"], exp["sqdist"]) and np.array_equal(got["status"], exp["status"])
+            for name in ("dist", "clearance"):
+                assert np.array_equal(got[name].view(np.uint32), exp[name].view(np.uint32)), (f, name)
+            vox = np.floor((cen_np[f].astype(np.float32) - np.asarray(grid.origin, np.float32))
+                           / np.float32(grid.voxel_size)).astype(np.int64)
+            for i in np.nonzero(got["status"] == v.SPHERE_OK)[0]:
+                j = int(got["idx"][i])
+                nx, ny, nz = j % X, (j // X) % Y, j // (X * Y)
+                assert occ[nz, ny, nx] != 0
+                assert (nx - vox[i, 0]) ** 2 + (ny - vox[i, 1]) ** 2 + (nz - vox[i, 2]) ** 2 == got["sqdist"][i]
+    m.close()
+
+
 def test_async_host_frames_back_to_back_match_sync_frames():
     """Frames queued back to back with vedt_frame_host_async alternate the two staging
     buffers, each upload running on the copy stream while the previous frame computes;
