@@ -175,9 +175,10 @@ def test_frame_api_full_size_on_two_streams(timing):
 
 def test_frame_api_back_to_back_without_host_syncs():
     """Frames queued back to back on the map's stream, as the bench times them: no host
-    synchronisation between frames, so each frame's first kernels overlap the previous
-    frame's last ones.  Every frame writes its sphere results to a buffer of its own; each
-    frame's results, and the last frame's fields, against the oracle."""
+    synchronisation between frames, so each frame's first kernel is launched while the
+    previous frame's query still runs (and waits for it).  Every frame writes its sphere
+    results to a buffer of its own; each frame's results, and the last frame's fields,
+    against the oracle."""
     v = lib()
     grid = synth.GridSpec((256, 256, 256), 0.01)
     scene = synth.CameraScene(1234 + 2000, grid)
